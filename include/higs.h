@@ -1,0 +1,215 @@
+/*
+ * higs.h - C ABI of the hierarchically tiled 3D Gaussian Splatting renderer
+ * (HiGS, arxiv 2606.00352) for sm_103a GPUs.
+ *
+ * One call renders V views of a device-resident gaussian scene through the
+ * paper's pipeline (Fig. 2; Sec. 3-4):
+ *   projection + SH colour (Sec. 4.2) -> macro-tile count / two-level scan /
+ *   fill (Sec. 3.2, 4.3) -> segmented depth sort (Sec. 3.3, 4.4) -> batch split
+ *   (Sec. 3.1) -> macro-tile rasterisation (Alg. 1, Alg. 2, Sec. 4.5) ->
+ *   ordered merge of the batch partials (Eq. 1, Sec. 3.4).
+ * A plain one-block-per-8x8-tile path with a global 64-bit radix sort (the
+ * baseline of Sec. 5) renders the same image for comparison.
+ *
+ * Conventions for every function below:
+ *  - Pointers named d_* or documented as "device" are CUDA device pointers of
+ *    the context's device; all other pointers are host pointers.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Render calls are stream-ordered: they enqueue work and,
+ *    unless stated otherwise, return before the GPU finishes.
+ *  - Every function returns an hg_status; nothing aborts.  Device-side
+ *    failures (capacity exceeded, a bounded wait that gave up) are written to
+ *    a device status word and reported by the call that synchronises
+ *    (hg_render in synchronous mode, hg_state_sync, hg_graph_launch with a
+ *    check).  hg_last_error() returns a thread-local message for the last
+ *    failure of the calling thread.
+ *  - Image outputs of a multi-view call are packed back to back: view v
+ *    starts at pixel offset sum_{u<v} W_u H_u; RGB is [H][W][3] float32 per
+ *    view and transmittance [H][W] float32.
+ */
+#ifndef HIGS_H
+#define HIGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HG_OK = 0,
+  HG_ERR_INVALID_ARG = -1,
+  HG_ERR_OOM = -2,
+  HG_ERR_CUDA = -3,
+  HG_ERR_CAPACITY = -4,       /* a preallocated buffer was too small (frame invalid) */
+  HG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait gave up (frame invalid) */
+  HG_ERR_BUSY = -6,
+  HG_ERR_NOT_FOUND = -7,
+  HG_ERR_CANCELLED = -8,
+  HG_ERR_UNSUPPORTED = -9
+} hg_status;
+
+typedef struct hg_ctx hg_ctx;
+typedef struct hg_scene hg_scene;
+typedef struct hg_state hg_state;
+typedef struct hg_graph hg_graph;
+typedef struct hg_server hg_server;
+
+/* Device memory provider.  alloc returns a device pointer of at least
+ * `bytes` (aligned to 256 bytes) or NULL; free releases it.  When the
+ * allocator passed to hg_ctx_create is NULL the library uses cudaMalloc /
+ * cudaFree.  Workspace buffers are requested only when a frame needs more
+ * than the buffers it already holds. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} hg_allocator;
+
+/* Gaussian scene, structure of arrays, float32, device pointers:
+ *   means [n][3], log_scales [n][3], quats [n][4] (w, x, y, z, any norm),
+ *   opacity_logits [n], sh [n][(sh_degree+1)^2][3] (coefficient k = l*l+l+m).
+ * borrow = 0: the library copies the arrays into memory it owns.
+ * borrow = 1: the library keeps the pointers; the caller keeps them alive
+ * and unchanged while the scene exists. */
+typedef struct {
+  int64_t n;
+  int32_t sh_degree; /* 0..3 */
+  int32_t borrow;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+} hg_scene_desc;
+
+/* Pinhole camera: world->camera 4x4 row-major (x right, y down, z forward),
+ * focal lengths and principal point in pixels; pixel (i, j) has its centre
+ * at (i, j) + (0.5, 0.5) in the (cx, cy) frame. */
+typedef struct {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} hg_camera;
+
+/* Projected gaussian ("splat"), the record the projection front end hands to
+ * partitioning and rasterisation (Sec. 4.2 outputs).  48 bytes. */
+typedef struct {
+  float mean2d[2];   /* pixel-centre convention: centre of pixel (i, j) is (i, j) */
+  float conic[3];    /* (A, B, C): q = A dx^2 + 2 B dx dy + C dy^2 */
+  float opacity;     /* sigmoid(logit) */
+  float rgb[3];      /* max(0, SH + 0.5) */
+  uint32_t depth_key;/* float32 bits of the camera-space depth */
+  int32_t radius;    /* ceil(3 sqrt(lambda_max)), 0 = culled */
+  float depth;
+} hg_splat;
+
+enum { HG_PATH_HIGS = 0, HG_PATH_PLAIN = 1 };
+enum { HG_BIN_RECT = 0 };
+enum {
+  HG_FLAG_ASYNC = 1,       /* do not synchronise or check the status word */
+  HG_FLAG_TIMING = 2,      /* record per-stage CUDA events (hg_render_stats) */
+  HG_FLAG_KEEP_SPLATS = 4  /* also write hg_splat records (hg_state_read) */
+};
+
+typedef struct {
+  int32_t path;        /* HG_PATH_HIGS or HG_PATH_PLAIN */
+  int32_t macro_w;     /* render tiles per macro-tile in x: 4 or 8 (default 8) */
+  int32_t macro_h;     /* render tiles per macro-tile in y: 4 or 8 (default 4) */
+  int32_t batch_cap;   /* B_r, 32..2048 multiple of 32 (default 1024) */
+  int32_t bin_test;    /* HG_BIN_RECT */
+  float bg[3];         /* background colour added as C + T bg */
+  int32_t save_for_backward;
+  int32_t flags;       /* HG_FLAG_* */
+} hg_render_opts;
+
+/* Per-frame statistics (filled after the frame completed). */
+typedef struct {
+  int64_t n_views, n_gaussians, n_visible;
+  int64_t n_pairs;        /* macro-tile pairs (HiGS) or tile pairs (plain) */
+  int64_t n_segments;     /* macro-tiles over all views */
+  int64_t n_batches;      /* N_R */
+  int64_t max_segment;    /* largest segment */
+  int64_t seg_by_tier[5]; /* segments sorted by tier: <=1K, <=4K, <=16K, onesweep, empty/1 */
+  int64_t n_sort_tiles;   /* onesweep tiles */
+  int64_t n_replays;      /* merge replays (exact termination across batches) */
+  int64_t raster_evals;   /* (gaussian, pixel) evaluations in the rasteriser */
+  int32_t status;         /* device status word (hg_status) */
+  int32_t pad;
+  float ms_project, ms_partition, ms_sort, ms_raster, ms_merge, ms_total;
+} hg_frame_stats;
+
+/* ---------------------------------------------------------------- context */
+const char* hg_status_str(hg_status s);
+const char* hg_last_error(void);
+const char* hg_version(void);
+
+/* Create a context on `device`; `alloc` may be NULL (cudaMalloc). */
+hg_status hg_ctx_create(int device, const hg_allocator* alloc, hg_ctx** out);
+void hg_ctx_destroy(hg_ctx* ctx);
+
+/* ------------------------------------------------------------------ scene */
+/* Sec. 4.2 inputs.  Copies (borrow = 0) are enqueued on the legacy stream and
+ * complete before the call returns. */
+hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* desc, hg_scene** out);
+void hg_destroy_scene(hg_scene* scene);
+int64_t hg_scene_size(const hg_scene* scene);
+
+/* ----------------------------------------------------------------- render */
+/* Render `n_views` cameras of `scene` (the whole pipeline of Sec. 3-4).
+ *  out_rgb: device, sum_v W_v H_v * 3 floats; out_T: device, sum_v W_v H_v
+ *  floats or NULL.
+ *  state: NULL -> the context's internal workspace is used (calls on the
+ *  same context must then be stream-serialised); non-NULL -> *state (created
+ *  on first use when *state == NULL) holds this frame's workspace, its
+ *  statistics and, with save_for_backward, what hg_render_backward needs.
+ *  Unless HG_FLAG_ASYNC is set the call synchronises `stream` and returns
+ *  the device status; when a workspace buffer was too small it grows it and
+ *  renders again, so HG_ERR_CAPACITY is only seen in asynchronous use.
+ * Errors: HG_ERR_INVALID_ARG (bad sizes or options), HG_ERR_OOM,
+ *  HG_ERR_CUDA, HG_ERR_DEVICE_TIMEOUT. */
+hg_status hg_render(hg_scene* scene, const hg_camera* cams, int n_views,
+                    const hg_render_opts* opts, float* out_rgb, float* out_T,
+                    hg_state** state, void* stream);
+
+/* Same pipeline starting from precomputed splats (skips the projection):
+ * d_splats is device [n_views][n] hg_splat.  Used to run the discrete stages
+ * on records computed elsewhere. */
+hg_status hg_render_splats(hg_ctx* ctx, const hg_splat* d_splats, int64_t n,
+                           const hg_camera* cams, int n_views, const hg_render_opts* opts,
+                           float* out_rgb, float* out_T, hg_state** state, void* stream);
+
+/* Backward of 0.5 ||C - C*||^2-style losses: given dL/dC (device, same layout
+ * as out_rgb) of the frame saved in `state` (rendered with
+ * save_for_backward), write dL/d(parameter) into the device arrays (same
+ * shapes as the scene arrays; they are overwritten, not accumulated).  The
+ * per-batch partials become a prefix scan (Sec. 6) and every batch is
+ * replayed back to front from its per-(pixel, batch) stop position. */
+hg_status hg_render_backward(hg_state* state, const float* dL_drgb,
+                             float* d_means, float* d_log_scales, float* d_quats,
+                             float* d_opacity_logits, float* d_sh, void* stream);
+
+void hg_state_free(hg_state* state);
+
+/* Wait for the frame of `state` and return its device status. */
+hg_status hg_state_sync(hg_state* state);
+
+/* Statistics of the last frame rendered into `state` (synchronises). */
+hg_status hg_render_stats(hg_state* state, hg_frame_stats* out);
+
+/* Copy an intermediate buffer of the last frame to host memory (synchronises).
+ * which: HG_BUF_SEG_OFF (uint32 [S+1]), HG_BUF_PAIR_KEYS (uint32 [P]),
+ * HG_BUF_PAIR_IDS (uint32 [P]), HG_BUF_BATCHES (uint32 [N_R][3]: segment,
+ * start, count), HG_BUF_SPLATS (hg_splat [V][n], needs HG_FLAG_KEEP_SPLATS),
+ * HG_BUF_VIEW_SEG_BASE (uint32 [V+1]).  *bytes_needed receives the size; dst
+ * may be NULL to query it. */
+enum { HG_BUF_SEG_OFF = 0, HG_BUF_PAIR_KEYS = 1, HG_BUF_PAIR_IDS = 2, HG_BUF_BATCHES = 3,
+       HG_BUF_SPLATS = 4, HG_BUF_VIEW_SEG_BASE = 5 };
+hg_status hg_state_read(hg_state* state, int which, void* dst, size_t dst_bytes,
+                        size_t* bytes_needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HIGS_H */

@@ -1,0 +1,67 @@
+// Per-pixel front-to-back blend step (Sec. 3.4 rules of 3DGS): support
+// q <= 9, alpha = min(0.99, o exp(-q/2)), skip alpha < 1/255, stop before
+// T (1 - alpha) < 1e-4.  q is evaluated as the sum of squares of the
+// prescaled Cholesky factors (Sec. 3.5), e = (l0 dx + l1 dy)^2 + (l2 dy)^2 =
+// q log2(e) / 2, so alpha = o exp2(-e).
+#pragma once
+#include "common.cuh"
+
+namespace hg {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct PixelAcc {
+  float r, g, b, T;
+  bool done;      // stopped (or outside the image)
+  bool stopped;   // stopped by the termination rule
+};
+
+__device__ __forceinline__ void pixel_init(PixelAcc& p, bool inside, float t_in = 1.f) {
+  p.r = p.g = p.b = 0.f;
+  p.T = t_in;
+  p.done = !inside;
+  p.stopped = false;
+}
+
+// One gaussian (g0 = {mx, my, l0', l1'}, g1 = {l2', o, ., .}, g2 = {r, g, b, .})
+// at pixel offset (dx, dy) from its centre.  Returns true if the pixel
+// stopped at this gaussian.
+__device__ __forceinline__ bool blend_one(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
+                                          const float4& g2) {
+  if (p.done) return false;
+  const float u = fmaf(g0.w, dy, ubase);
+  const float w = g1.x * dy;
+  const float e = fmaf(u, u, w * w);
+  if (e > SUPPORT_E) return false;
+  const float al = fminf(ALPHA_MAX, g1.y * ex2_approx(-e));
+  if (al < ALPHA_MIN) return false;
+  const float tn = p.T * (1.f - al);
+  if (tn < T_EPS) {
+    p.done = true;
+    p.stopped = true;
+    return true;
+  }
+  const float wt = al * p.T;
+  p.r = fmaf(g2.x, wt, p.r);
+  p.g = fmaf(g2.y, wt, p.g);
+  p.b = fmaf(g2.z, wt, p.b);
+  p.T = tn;
+  return false;
+}
+
+// Conservative test of a gaussian's 3-sigma rectangle against render tile
+// (tx, ty) (same integer rule as the macro binning, at 8x8 granularity).
+__device__ __forceinline__ void tile_rect(const float4& g0, const float4& g1, int& x0, int& x1, int& y0, int& y1) {
+  const int rad = __float_as_int(g1.z);
+  const int px = (int)floorf(g0.x), py = (int)floorf(g0.y);
+  x0 = floordiv(px - rad, TILE);
+  x1 = floordiv(px + rad, TILE);
+  y0 = floordiv(py - rad, TILE);
+  y1 = floordiv(py + rad, TILE);
+}
+
+}  // namespace hg

@@ -1,0 +1,85 @@
+// Host-side objects behind the opaque C ABI handles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "kernels.cuh"
+
+struct hg_ctx {
+  int device = 0;
+  hg_allocator alloc{};
+  bool has_alloc = false;
+  int sms = 0;
+  hg_state* internal = nullptr;  // workspace used when the caller passes no state
+};
+
+struct hg_scene {
+  hg_ctx* ctx = nullptr;
+  int64_t n = 0;
+  int deg = 0;
+  bool owned = true;
+  float* arr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // means, log_scales, quats, logits, sh
+  size_t bytes[5] = {0, 0, 0, 0, 0};
+};
+
+namespace hg {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+enum BufId {
+  B_FC, B_VIEWS, B_BIN, B_REC, B_VIS, B_SPLATS,
+  B_HIST, B_COLPRE, B_SEGTOT, B_SEGOFF, B_FIRSTB, B_TIERLIST, B_BIGTILES, B_BIGSEGS, B_BIGTF,
+  B_KEYS, B_VALS, B_KEYS2, B_VALS2, B_BATCHES, B_BORDER, B_RANKC,
+  B_PARTIAL, B_ACTIVE, B_TILESAT, B_STOPPOS, B_PREFIX, B_SEGHIST, B_LOOKBACK,
+  P_COUNTS, P_OFFS, P_SCAN, P_KEYS, P_KEYS2, P_VALS, P_VALS2, P_RANGES, P_LOOKBACK, P_DHIST,
+  G_DMEANS2, G_AUX,
+  BUF_COUNT
+};
+
+struct FrameGeom {
+  int V = 0;
+  int S = 0;
+  int total_tiles = 0;
+  long long pixels = 0;
+  int max_nm = 0;
+};
+
+struct FrameInputs {
+  const hg_scene* scene;
+  const hg_splat* splats;
+  long long n;
+};
+
+constexpr int N_EVENTS = 8;
+
+}  // namespace hg
+
+struct hg_state {
+  hg_ctx* ctx = nullptr;
+  hg::Buf bufs[hg::BUF_COUNT];
+  hg::FrameCounters* fc_host = nullptr;  // pinned
+  hg::ViewDesc* views_host = nullptr;    // pinned, MAX_VIEWS entries
+  cudaEvent_t ev[hg::N_EVENTS] = {};
+  cudaStream_t last_stream = nullptr;
+  bool has_frame = false;
+  hg::FrameGeom geom;
+  hg_render_opts opts{};
+  long long n = 0;
+  const hg_scene* scene = nullptr;
+  size_t cap_pairs = 0, cap_batches = 0, cap_tiles = 0, cap_big_segs = 0;
+  size_t cap_plain_pairs = 0, cap_plain_tiles = 0;
+};
+
+void hg_set_error(const std::string& s);
+hg_status hg_cuda_status(cudaError_t e, const char* where);
+void* ctx_alloc(hg_ctx* ctx, size_t bytes, cudaStream_t st);
+void ctx_free(hg_ctx* ctx, void* p, size_t bytes, cudaStream_t st);
+hg_status ws_ensure(hg_state* s, int id, size_t bytes, cudaStream_t st);
+hg_status state_create(hg_ctx* ctx, hg_state** out);
+hg_status build_views(hg_state* s, const hg_camera* cams, int V, const hg_render_opts* o, hg::FrameGeom& g);
+hg_status run_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg_camera* cams, int V,
+                    float* out_rgb, float* out_T, cudaStream_t st);

@@ -1,0 +1,175 @@
+// Launch interface of the render kernels (host <-> device layouts).
+#pragma once
+#include "common.cuh"
+
+namespace hg {
+
+struct ProjectArgs {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  long long n;
+  const ViewDesc* views;  // device
+  int n_views;
+  long long vis_words;    // ceil(n / 32)
+  uint4* bin;             // [V][n]
+  float4* rec;            // [V][n][3]
+  uint32_t* vis;          // [V][vis_words]
+  hg_splat* splats;       // optional [V][n]
+  FrameCounters* fc;
+};
+
+// Partition (count -> scan -> fill) and batch split of one frame.
+struct PartitionArgs {
+  const uint4* bin;
+  const uint32_t* vis;
+  long long n;
+  long long vis_words;
+  const ViewDesc* views;
+  int n_views;
+  int n_seg;              // S = sum of macro-tiles
+  int n_pb;               // N_B = ceil(n / B_p)
+  int macro_w, macro_h;   // render tiles per macro-tile
+  int max_nm;             // largest per-view macro-tile count
+  uint16_t* hist;         // [N_B][S] (view v occupies columns [seg_base_v, seg_base_v + N_M_v))
+  uint32_t* colpre;       // [N_B][S] exclusive prefix over partition batches
+  uint32_t* seg_tot;      // [S]
+  uint32_t* seg_off;      // [S + 1]
+  uint32_t* first_batch;  // [S + 1]
+  uint32_t* tier_list;    // [5][S] segment ids per sort tier
+  uint4* big_tiles;       // onesweep tiles {seg, start, count, tile index in segment}
+  uint32_t* big_segs;     // [S] big segment ids
+  uint32_t* big_tile_first; // [S] first tile of each big segment
+  uint32_t* keys;         // pair keys [cap_pairs]
+  uint32_t* vals;         // pair ids  [cap_pairs]
+  uint4* batches;         // [cap_batches] {seg, start, count, j}
+  uint32_t* batch_order;  // [cap_batches] raster schedule: batch ids, batch rank major
+  uint32_t* rank_count;   // [MAX_RANKS + 1] scratch for the schedule
+  int batch_cap;
+  uint32_t cap_pairs, cap_batches, cap_tiles, cap_big_segs;
+  FrameCounters* fc;
+};
+
+// Sort tiers: segment-size limits handled by one CTA in shared memory.
+constexpr int TIER0_MAX = 1024;    // 128 threads x 8
+constexpr int TIER1_MAX = 4096;    // 256 threads x 16
+constexpr int TIER2_MAX = 16384;   // 1024 threads x 16
+constexpr int OS_THREADS = 512;    // onesweep tile: 512 threads x 16 items
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
+constexpr int MAX_RANKS = 4096;    // batch ranks tracked by the raster schedule
+
+struct SortArgs {
+  uint32_t* keys;
+  uint32_t* vals;
+  uint32_t* keys_alt;
+  uint32_t* vals_alt;
+  const uint32_t* seg_off;
+  const uint32_t* tier_list;  // [5][S]
+  int n_seg;
+  const uint4* big_tiles;
+  const uint32_t* big_segs;
+  const uint32_t* big_tile_first;
+  uint32_t* seg_hist;         // [cap_big_segs][4][256]
+  uint32_t* lookback;         // [4][cap_tiles][256]
+  uint32_t cap_tiles, cap_big_segs;
+  FrameCounters* fc;
+};
+
+struct RasterArgs {
+  const float4* rec;          // [V][n][3]
+  long long n;
+  const ViewDesc* views;
+  int n_views;
+  int n_seg;
+  const uint32_t* keys;       // sorted pair keys
+  const uint32_t* vals;       // sorted pair ids
+  const uint4* batches;       // {seg, start, count, j}
+  const uint32_t* batch_order;
+  uint32_t cap_batches;
+  int batch_cap;              // B_r
+  int macro_w, macro_h;
+  float4* partial;            // [cap_batches][M][64] (r, g, b, +-T)
+  unsigned long long* active; // [cap_batches] tile bits
+  uint32_t* tile_sat;         // [total render tiles] first batch rank that saturated the tile (+1), 0 = none
+  uint16_t* stop_pos;         // optional [cap_batches][M][64]: local stop position (backward)
+  int persistent_ctas;
+  FrameCounters* fc;
+};
+
+struct MergeArgs {
+  const float4* partial;
+  const unsigned long long* active;
+  const uint32_t* first_batch;
+  const uint4* batches;
+  const uint32_t* vals;
+  const float4* rec;
+  long long n;
+  const ViewDesc* views;
+  int n_views;
+  int total_tiles;
+  int macro_w, macro_h;
+  float bg[3];
+  float* out_rgb;
+  float* out_T;
+  float4* prefix;             // optional [cap_batches][M][64]: (C, T) entering each batch (backward)
+  FrameCounters* fc;
+};
+
+struct PlainArgs {
+  const uint4* bin;
+  const float4* rec;
+  long long n;
+  const ViewDesc* views;
+  int n_views;
+  int total_tiles;
+  uint32_t* counts;           // [V n]
+  uint32_t* offsets;          // [V n + 1]
+  uint32_t* scan_tmp;
+  unsigned long long* keys;   // [cap] (global tile << 32) | depth key
+  uint32_t* vals;             // [cap] record index v n + i
+  unsigned long long* keys_alt;
+  uint32_t* vals_alt;
+  uint2* ranges;              // [total tiles]
+  uint32_t* lookback;
+  uint32_t* digit_hist;       // [8][256]
+  uint32_t cap_pairs, cap_tiles;
+  float bg[3];
+  float* out_rgb;
+  float* out_T;
+  FrameCounters* fc;
+};
+
+// Tiles of the segments sorted by the onesweep: {big segment index, start,
+// count, tile index inside the segment}; a segment's tiles are consecutive.
+struct OsTileView {
+  const uint4* tiles;
+  const uint32_t* tile_count;     // device
+  const uint32_t* seg_hist;       // [big segments][npass][256]
+  const uint32_t* seg_off;        // segment offsets, or NULL for one segment at 0
+  const uint32_t* big_segs;       // big segment index -> segment id
+  const uint32_t* big_tile_first;
+};
+
+// Onesweep LSD radix sort of the tiles' segments over digit passes
+// [first_pass, first_pass + npass) of K keys with uint32 values; the result
+// is in (keys, vals) for an even pass count, else in the alternates.
+template <typename K, int NPASS>
+cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt,
+                            uint32_t* seg_hist, size_t seg_hist_words, uint32_t* lookback, size_t lookback_words,
+                            uint32_t* claims, int first_pass, int npass, FrameCounters* fc, cudaStream_t st,
+                            bool* result_in_alt);
+
+cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
+cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words, uint4* bin,
+                                     float4* rec, uint32_t* vis, cudaStream_t st);
+cudaError_t launch_partition(const PartitionArgs& a, cudaStream_t st);
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
+cudaError_t launch_raster(const RasterArgs& a, cudaStream_t st);
+cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
+// returns the key pointer that holds the sorted result through *sorted_keys / *sorted_vals
+cudaError_t launch_plain(PlainArgs& a, cudaStream_t st, unsigned long long** sorted_keys, uint32_t** sorted_vals);
+
+}  // namespace hg

@@ -1,0 +1,374 @@
+// Segmented depth sort (Sec. 3.3, 4.4).  Every (view, macro-tile) segment of
+// (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
+//   * segments of <= 16K pairs: one CTA sorts the segment in shared memory
+//     (tiers <= 1K / 4K / 16K pairs), skipping digit passes whose byte is
+//     constant over the segment;
+//   * larger segments: a segment-local onesweep (one kernel per 8-bit digit
+//     pass, decoupled look-back across the segment's tiles, tiles claimed in
+//     order through an atomic counter so every awaited predecessor is
+//     running), preceded by one histogram kernel for all four digits.
+// The fill pass writes a segment in a data-dependent order, so runs of equal
+// keys are re-sorted by id at the end (the id tie-break).
+#include "kernels.cuh"
+#include "radix.cuh"
+
+namespace hg {
+
+namespace {
+
+// ------------------------------------------------------------ tier sorts
+template <int NT, int IPT>
+struct BlockSortSmem {
+  uint32_t keys[NT * IPT];
+  uint32_t vals[NT * IPT];
+  RankSmem<NT> rank;
+  uint32_t red[2][NT / 32];
+};
+
+__device__ __forceinline__ void sort_run_by_val(uint32_t* vals, int a, int b) {
+  for (int i = a + 1; i < b; ++i) {
+    uint32_t v = vals[i];
+    int j = i - 1;
+    while (j >= a && vals[j] > v) {
+      vals[j + 1] = vals[j];
+      --j;
+    }
+    vals[j + 1] = v;
+  }
+}
+
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
+  constexpr int CAP = NT * IPT;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BlockSortSmem<NT, IPT>& s = *reinterpret_cast<BlockSortSmem<NT, IPT>*>(smem_raw);
+  if (read_status(a.fc)) return;
+  const uint32_t count = a.fc->tier_count[tier];
+  const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const uint32_t seg = list[idx];
+    const uint32_t start = a.seg_off[seg];
+    const int n = (int)(a.seg_off[seg + 1] - start);
+    uint32_t orv = 0, andv = 0xffffffffu;
+    for (int j = tid; j < CAP; j += NT) {
+      uint32_t k = 0xffffffffu, v = 0xffffffffu;
+      if (j < n) {
+        k = a.keys[start + j];
+        v = a.vals[start + j];
+        orv |= k;
+        andv &= k;
+      }
+      s.keys[j] = k;
+      s.vals[j] = v;
+    }
+    // bits that vary over the segment's keys
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      orv |= __shfl_xor_sync(0xffffffffu, orv, o);
+      andv &= __shfl_xor_sync(0xffffffffu, andv, o);
+    }
+    if (lane == 0) {
+      s.red[0][warp] = orv;
+      s.red[1][warp] = andv;
+    }
+    __syncthreads();
+    orv = 0;
+    andv = 0xffffffffu;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      orv |= s.red[0][w];
+      andv &= s.red[1][w];
+    }
+    const uint32_t vary = orv ^ andv;
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 8 * pass;
+      if (((vary >> shift) & 0xffu) == 0) continue;
+      uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        int e = striped_index<IPT>(i);
+        k[i] = s.keys[e];
+        v[i] = s.vals[e];
+        d[i] = (k[i] >> shift) & 0xffu;
+      }
+      block_rank<NT, IPT>(d, p, s.rank);
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        s.keys[p[i]] = k[i];
+        s.vals[p[i]] = v[i];
+      }
+      __syncthreads();
+    }
+    // equal keys: order by id
+    for (int j = tid; j < n; j += NT) {
+      uint32_t kk = s.keys[j];
+      if ((j == 0 || s.keys[j - 1] != kk) && j + 1 < n && s.keys[j + 1] == kk) {
+        int e = j + 1;
+        while (e < n && s.keys[e] == kk) ++e;
+        sort_run_by_val(s.vals, j, e);
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += NT) {
+      a.keys[start + j] = s.keys[j];
+      a.vals[start + j] = s.vals[j];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ onesweep
+// Look-back words: bits 30-31 flag, bits 0-29 count.
+constexpr uint32_t LB_AGG = 1u << 30;
+constexpr uint32_t LB_INC = 2u << 30;
+constexpr uint32_t LB_MASK = (1u << 30) - 1;
+
+template <typename K>
+struct OneSweepSmem {
+  K keys[OS_TILE];
+  uint32_t vals[OS_TILE];
+  RankSmem<OS_THREADS> rank;
+  uint32_t gbase[256];
+  uint32_t tile_claim;
+};
+
+
+
+template <typename K, int NPASS>
+__global__ void __launch_bounds__(OS_THREADS) k_os_hist(OsTileView tv, const K* keys, uint32_t* seg_hist,
+                                                        FrameCounters* fc) {
+  __shared__ uint32_t h[NPASS][256];
+  if (read_status(fc)) return;
+  const uint32_t nt = *tv.tile_count;
+  for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    for (int j = threadIdx.x; j < NPASS * 256; j += OS_THREADS) (&h[0][0])[j] = 0;
+    __syncthreads();
+    const uint4 td = tv.tiles[t];
+    for (uint32_t j = threadIdx.x; j < td.z; j += OS_THREADS) {
+      K k = keys[td.y + j];
+#pragma unroll
+      for (int p = 0; p < NPASS; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    uint32_t* dst = seg_hist + (size_t)td.x * NPASS * 256;
+    for (int j = threadIdx.x; j < NPASS * 256; j += OS_THREADS) {
+      uint32_t c = (&h[0][0])[j];
+      if (c) atomicAdd(dst + j, c);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K, int NPASS>
+__global__ void __launch_bounds__(OS_THREADS) k_os_pass(OsTileView tv, const K* src_k, const uint32_t* src_v,
+                                                        K* dst_k, uint32_t* dst_v, uint32_t* lookback,
+                                                        uint32_t* claim, int pass, FrameCounters* fc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  OneSweepSmem<K>& s = *reinterpret_cast<OneSweepSmem<K>*>(smem_raw);
+  if (read_status(fc)) return;
+  const uint32_t nt = *tv.tile_count;
+  const int shift = 8 * pass;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) s.tile_claim = atomicAdd(claim, 1u);
+    __syncthreads();
+    const uint32_t t = s.tile_claim;
+    __syncthreads();
+    if (t >= nt) return;
+    const uint4 td = tv.tiles[t];
+    const uint32_t bseg = td.x, start = td.y, cnt = td.z, ti = td.w;
+    K k[OS_ITEMS];
+    uint32_t v[OS_ITEMS], d[OS_ITEMS], p[OS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+      int e = striped_index<OS_ITEMS>(i);
+      if ((uint32_t)e < cnt) {
+        k[i] = src_k[start + e];
+        v[i] = src_v[start + e];
+        d[i] = (uint32_t)(k[i] >> shift) & 0xffu;
+      } else {
+        k[i] = 0;
+        v[i] = 0;
+        d[i] = NO_DIGIT;
+      }
+    }
+    block_rank<OS_THREADS, OS_ITEMS>(d, p, s.rank);
+    // publish this tile's digit counts, then look back over the segment's
+    // earlier tiles for the exclusive prefix of every digit
+    uint32_t* lb = lookback + (size_t)t * 256;
+    if (tid < 256) {
+      const uint32_t c = s.rank.digit_count[tid];
+      volatile uint32_t* me = lb + tid;
+      if (ti == 0) {
+        *me = LB_INC | c;
+      } else {
+        *me = LB_AGG | c;
+        uint32_t excl = 0;
+        uint32_t j = t - 1;
+        bool ok = true;
+        while (true) {
+          volatile uint32_t* w = lookback + (size_t)j * 256 + tid;
+          uint32_t val = *w;
+          uint32_t it = 0;
+          while ((val & ~LB_MASK) == 0) {
+            if (++it > SPIN_LIMIT) {
+              ok = false;
+              break;
+            }
+            val = *w;
+          }
+          if (!ok) break;
+          excl += val & LB_MASK;
+          if ((val & ~LB_MASK) == LB_INC) break;
+          --j;
+        }
+        if (!ok) {
+          set_status(fc, HG_ERR_DEVICE_TIMEOUT);
+          atomicOr(&fc->timeout_where, 1u);
+        }
+        *me = LB_INC | ((excl + c) & LB_MASK);
+        s.gbase[tid] = excl;
+      }
+      if (ti == 0) s.gbase[tid] = 0;
+    }
+    // segment-level digit offsets for this pass
+    __syncthreads();
+    if (tid < 32) {
+      const uint32_t* hh = tv.seg_hist + ((size_t)bseg * NPASS + pass) * 256;
+      uint32_t vv[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        vv[q] = hh[tid * 8 + q];
+        sum += vv[q];
+      }
+      uint32_t inc = warp_incl_scan(sum), run = inc - sum;
+      const uint32_t seg_start = tv.seg_off ? tv.seg_off[tv.big_segs[bseg]] : 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int dd = tid * 8 + q;
+        // destination of local sorted index j with digit dd: gbase[dd] + j
+        s.gbase[dd] = seg_start + run + s.gbase[dd] - s.rank.digit_start[dd];
+        run += vv[q];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+      if (d[i] != NO_DIGIT) {
+        s.keys[p[i]] = k[i];
+        s.vals[p[i]] = v[i];
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < cnt; j += OS_THREADS) {
+      K kk = s.keys[j];
+      uint32_t dd = (uint32_t)(kk >> shift) & 0xffu;
+      uint32_t dst = s.gbase[dd] + j;
+      dst_k[dst] = kk;
+      dst_v[dst] = s.vals[j];
+    }
+    __syncthreads();
+  }
+}
+
+// equal keys inside big segments: order by id (runs may cross tiles)
+__global__ void k_os_fixup(OsTileView tv, uint32_t* keys, uint32_t* vals, FrameCounters* fc) {
+  if (read_status(fc)) return;
+  const uint32_t nt = *tv.tile_count;
+  for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    const uint4 td = tv.tiles[t];
+    const uint32_t seg = tv.big_segs[td.x];
+    const uint32_t s0 = tv.seg_off[seg], s1 = tv.seg_off[seg + 1];
+    for (uint32_t j = threadIdx.x; j < td.z; j += blockDim.x) {
+      uint32_t g = td.y + j;
+      uint32_t kk = keys[g];
+      if ((g == s0 || keys[g - 1] != kk) && g + 1 < s1 && keys[g + 1] == kk) {
+        uint32_t e = g + 1;
+        while (e < s1 && keys[e] == kk) ++e;
+        sort_run_by_val(vals, (int)g, (int)e);
+      }
+    }
+  }
+}
+
+static int g_sms = 0;
+static int num_sms() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 148;
+  }
+  return g_sms;
+}
+
+template <int NT, int IPT>
+static cudaError_t launch_tier(const SortArgs& a, int tier, int blocks_per_sm, cudaStream_t st) {
+  size_t sm = sizeof(BlockSortSmem<NT, IPT>);
+  cudaError_t e = cudaFuncSetAttribute(k_block_sort<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_block_sort<NT, IPT><<<num_sms() * blocks_per_sm, NT, sm, st>>>(a, tier);
+  return cudaGetLastError();
+}
+
+template <typename K, int NPASS>
+cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt,
+                            uint32_t* seg_hist, size_t seg_hist_words, uint32_t* lookback, size_t lookback_words,
+                            uint32_t* claims, int first_pass, int npass, FrameCounters* fc, cudaStream_t st,
+                            bool* result_in_alt) {
+  cudaError_t e = cudaMemsetAsync(seg_hist, 0, seg_hist_words * 4, st);
+  if (e != cudaSuccess) return e;
+  const int grid = num_sms() * 2;
+  k_os_hist<K, NPASS><<<grid, OS_THREADS, 0, st>>>(tv, keys, seg_hist, fc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  size_t sm = sizeof(OneSweepSmem<K>);
+  e = cudaFuncSetAttribute(k_os_pass<K, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_os_pass<K, NPASS>, OS_THREADS, sm);
+  if (occ < 1) occ = 1;
+  K* sk = keys;
+  uint32_t* sv = vals;
+  K* dk = keys_alt;
+  uint32_t* dv = vals_alt;
+  for (int p = first_pass; p < first_pass + npass; ++p) {
+    e = cudaMemsetAsync(lookback, 0, lookback_words * 4, st);
+    if (e != cudaSuccess) return e;
+    k_os_pass<K, NPASS><<<num_sms() * occ, OS_THREADS, sm, st>>>(tv, sk, sv, dk, dv, lookback, claims + p, p, fc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    K* tk = sk;
+    sk = dk;
+    dk = tk;
+    uint32_t* tvv = sv;
+    sv = dv;
+    dv = tvv;
+  }
+  *result_in_alt = (npass & 1) != 0;
+  return cudaSuccess;
+}
+
+template cudaError_t launch_onesweep<unsigned long long, 8>(const OsTileView&, unsigned long long*, uint32_t*,
+                                                            unsigned long long*, uint32_t*, uint32_t*, size_t,
+                                                            uint32_t*, size_t, uint32_t*, int, int,
+                                                            FrameCounters*, cudaStream_t, bool*);
+
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
+  if ((e = launch_tier<256, 16>(a, 1, 4, st)) != cudaSuccess) return e;
+  if ((e = launch_tier<1024, 16>(a, 2, 1, st)) != cudaSuccess) return e;
+  OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
+  bool alt = false;
+  e = launch_onesweep<uint32_t, 4>(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist,
+                                   (size_t)a.cap_big_segs * 4 * 256, a.lookback, (size_t)a.cap_tiles * 256,
+                                   a.fc->os_claim, 0, 4, a.fc, st, &alt);
+  if (e != cudaSuccess) return e;
+  k_os_fixup<<<num_sms() * 4, 256, 0, st>>>(tv, a.keys, a.vals, a.fc);
+  return cudaGetLastError();
+}
+
+}  // namespace hg

@@ -1,0 +1,317 @@
+"""Python binding of libhigs.so (argument marshalling only).
+
+Every step of the render path runs in the library's CUDA kernels; this module
+only converts torch tensors / numpy arrays into the C ABI's pointers and
+structs (include/higs.h).  It fails loudly when the library cannot be loaded:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhigs.so")
+
+HG_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "capacity",
+          -5: "device timeout", -6: "busy", -7: "not found", -8: "cancelled", -9: "unsupported"}
+PATH_HIGS, PATH_PLAIN = 0, 1
+FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS = 1, 2, 4
+BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE = range(6)
+
+EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",
+           "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",
+           "hg_state_free", "hg_state_sync", "hg_render_stats", "hg_state_read"]
+
+
+class HgError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("borrow", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class CameraC(C.Structure):
+    _fields_ = [("viewmat", C.c_float * 16), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("path", C.c_int32), ("macro_w", C.c_int32), ("macro_h", C.c_int32),
+                ("batch_cap", C.c_int32), ("bin_test", C.c_int32), ("bg", C.c_float * 3),
+                ("save_for_backward", C.c_int32), ("flags", C.c_int32)]
+
+
+class FrameStats(C.Structure):
+    _fields_ = [("n_views", C.c_int64), ("n_gaussians", C.c_int64), ("n_visible", C.c_int64),
+                ("n_pairs", C.c_int64), ("n_segments", C.c_int64), ("n_batches", C.c_int64),
+                ("max_segment", C.c_int64), ("seg_by_tier", C.c_int64 * 5), ("n_sort_tiles", C.c_int64),
+                ("n_replays", C.c_int64), ("raster_evals", C.c_int64), ("status", C.c_int32),
+                ("pad", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
+                ("ms_sort", C.c_float), ("ms_raster", C.c_float), ("ms_merge", C.c_float),
+                ("ms_total", C.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "seg_by_tier")}
+        d["seg_by_tier"] = list(self.seg_by_tier)
+        return d
+
+
+SPLAT_DTYPE = np.dtype([("mean2d", "<f4", 2), ("conic", "<f4", 3), ("opacity", "<f4"), ("rgb", "<f4", 3),
+                        ("depth_key", "<u4"), ("radius", "<i4"), ("depth", "<f4")])
+assert SPLAT_DTYPE.itemsize == 48
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhigs.so (raises if it is missing or lacks an exported symbol)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhigs.so not built ({path}); run paper_2606_00352_gb300/build.py")
+    lib = C.CDLL(path)
+    for name in EXPORTS:
+        if not hasattr(lib, name):
+            raise RuntimeError(f"libhigs.so does not export {name}")
+    lib.hg_status_str.restype = C.c_char_p
+    lib.hg_last_error.restype = C.c_char_p
+    lib.hg_version.restype = C.c_char_p
+    lib.hg_scene_size.restype = C.c_int64
+    for name in ("hg_ctx_create", "hg_create_scene", "hg_render", "hg_render_splats",
+                 "hg_state_sync", "hg_render_stats", "hg_state_read"):
+        getattr(lib, name).restype = C.c_int
+    lib.hg_ctx_create.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.hg_ctx_destroy.argtypes = [C.c_void_p]
+    lib.hg_create_scene.argtypes = [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(C.c_void_p)]
+    lib.hg_destroy_scene.argtypes = [C.c_void_p]
+    lib.hg_scene_size.argtypes = [C.c_void_p]
+    lib.hg_render.argtypes = [C.c_void_p, C.POINTER(CameraC), C.c_int, C.POINTER(RenderOpts), C.c_void_p,
+                              C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p]
+    lib.hg_render_splats.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(CameraC), C.c_int,
+                                     C.POINTER(RenderOpts), C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p),
+                                     C.c_void_p]
+    lib.hg_state_free.argtypes = [C.c_void_p]
+    lib.hg_state_sync.argtypes = [C.c_void_p]
+    lib.hg_render_stats.argtypes = [C.c_void_p, C.POINTER(FrameStats)]
+    lib.hg_state_read.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != HG_OK:
+        raise HgError(status, load().hg_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> CameraC:
+    c = CameraC()
+    vm = np.asarray(cam.viewmat, np.float32).reshape(16)
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def cameras_array(cams):
+    arr = (CameraC * len(cams))()
+    for i, cam in enumerate(cams):
+        arr[i] = camera_struct(cam)
+    return arr
+
+
+@dataclass
+class Options:
+    path: int = PATH_HIGS
+    macro_w: int = 8
+    macro_h: int = 4
+    batch_cap: int = 1024
+    bg: tuple = (0.0, 0.0, 0.0)
+    save_for_backward: bool = False
+    flags: int = 0
+
+    def struct(self) -> RenderOpts:
+        o = RenderOpts()
+        o.path, o.macro_w, o.macro_h, o.batch_cap, o.bin_test = (self.path, self.macro_w, self.macro_h,
+                                                                 self.batch_cap, 0)
+        for i in range(3):
+            o.bg[i] = float(self.bg[i])
+        o.save_for_backward = int(self.save_for_backward)
+        o.flags = int(self.flags)
+        return o
+
+
+class Context:
+    """hg_ctx on one CUDA device (workspace from cudaMalloc)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        check(self.lib.hg_ctx_create(device, None, C.byref(h)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.hg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GpuScene:
+    """Device-resident scene (hg_create_scene).  Arrays are torch CUDA tensors
+    (float32, contiguous); borrow=True keeps references instead of copying."""
+
+    def __init__(self, ctx: Context, means, log_scales, quats, opacity_logits, sh, sh_degree: int,
+                 borrow: bool = False):
+        import torch
+        dev = torch.device("cuda", ctx.device)
+
+        def t(x):
+            x = torch.as_tensor(x, dtype=torch.float32, device=dev)
+            return x.contiguous()
+        self.tensors = [t(means), t(log_scales), t(quats), t(opacity_logits), t(sh)]
+        n = self.tensors[0].shape[0]
+        d = SceneDesc(n, sh_degree, int(borrow), *[x.data_ptr() for x in self.tensors])
+        h = C.c_void_p()
+        torch.cuda.synchronize(dev)
+        check(ctx.lib.hg_create_scene(ctx.h, C.byref(d), C.byref(h)))
+        self.h, self.ctx, self.n, self.sh_degree, self.borrow = h, ctx, n, sh_degree, borrow
+        if not borrow:
+            self.tensors = None
+
+    @classmethod
+    def from_scene(cls, ctx: Context, scene, borrow: bool = False):
+        return cls(ctx, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
+                   scene.sh_degree, borrow)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.hg_destroy_scene(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """hg_state: a frame workspace plus what the last frame saved."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+
+    def stats(self) -> dict:
+        s = FrameStats()
+        check(self.ctx.lib.hg_render_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def read(self, which: int, dtype=np.uint32) -> np.ndarray:
+        need = C.c_size_t()
+        check(self.ctx.lib.hg_state_read(self.h, which, None, 0, C.byref(need)))
+        out = np.empty(need.value // np.dtype(dtype).itemsize, dtype)
+        check(self.ctx.lib.hg_state_read(self.h, which, out.ctypes.data_as(C.c_void_p), out.nbytes,
+                                         C.byref(need)))
+        return out
+
+    def sync(self) -> int:
+        return self.ctx.lib.hg_state_sync(self.h)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.hg_state_free(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _out_tensors(cams, device, out_rgb=None, out_T=None, with_T=True):
+    import torch
+    pix = sum(int(c.width) * int(c.height) for c in cams)
+    if out_rgb is None:
+        out_rgb = torch.empty(pix * 3, dtype=torch.float32, device=device)
+    if out_T is None and with_T:
+        out_T = torch.empty(pix, dtype=torch.float32, device=device)
+    return out_rgb, out_T
+
+
+def split_views(flat, cams, channels):
+    out, o = [], 0
+    for c in cams:
+        k = int(c.width) * int(c.height)
+        out.append(flat[o * channels:(o + k) * channels].view(int(c.height), int(c.width), *([channels] if channels > 1 else [])))
+        o += k
+    return out
+
+
+def render(scene: GpuScene, cams, opts: Options | None = None, state: State | None = None, stream=None,
+           out_rgb=None, out_T=None, with_T=True):
+    """Render `cams` (list of scenes.Camera) of `scene`.  Returns the packed
+    (rgb, T) device tensors (views back to back)."""
+    import torch
+    opts = opts or Options()
+    dev = torch.device("cuda", scene.ctx.device)
+    out_rgb, out_T = _out_tensors(cams, dev, out_rgb, out_T, with_T)
+    cam_arr = cameras_array(cams)
+    o = opts.struct()
+    sp = C.byref(state.h) if state is not None else None
+    check(scene.ctx.lib.hg_render(scene.h, cam_arr, len(cams), C.byref(o), C.c_void_p(out_rgb.data_ptr()),
+                                  C.c_void_p(out_T.data_ptr()) if out_T is not None else None, sp,
+                                  _stream_ptr(stream)))
+    return out_rgb, out_T
+
+
+def render_splats(ctx: Context, splats, n: int, cams, opts: Options | None = None, state: State | None = None,
+                  stream=None):
+    """Render precomputed splats (device uint8 tensor of [V][n] hg_splat)."""
+    import torch
+    opts = opts or Options()
+    dev = torch.device("cuda", ctx.device)
+    out_rgb, out_T = _out_tensors(cams, dev)
+    cam_arr = cameras_array(cams)
+    o = opts.struct()
+    sp = C.byref(state.h) if state is not None else None
+    check(ctx.lib.hg_render_splats(ctx.h, C.c_void_p(splats.data_ptr()), n, cam_arr, len(cams), C.byref(o),
+                                   C.c_void_p(out_rgb.data_ptr()), C.c_void_p(out_T.data_ptr()), sp,
+                                   _stream_ptr(stream)))
+    return out_rgb, out_T
+
+
+def splats_to_device(rec: np.ndarray, device=0):
+    """numpy structured array (SPLAT_DTYPE) -> device byte tensor."""
+    import torch
+    assert rec.dtype == SPLAT_DTYPE
+    return torch.from_numpy(rec.view(np.uint8).copy()).to(torch.device("cuda", device))
+
+
+def version() -> str:
+    return load().hg_version().decode()

@@ -1,0 +1,246 @@
+"""GPU parity of the forward render path against the FP64 oracle, through
+the C ABI.  Discrete stages (pairs, keys, batch boundaries) are compared
+bit-exactly on identical float32 records; images within 2e-4 outside
+decision-ambiguous pixels."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2606_00352_gb300 import scenes
+from oracle import binning as BN
+from oracle import composite as C
+from oracle import project as P
+from tests.helpers import compare_image, splat_records, sample_tiles, tiles_mask
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    return lib.Context(0)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def render_np(lib, gs, cams, **kw):
+    import torch
+    st = kw.pop("state", None)
+    rgb, T = lib.render(gs, cams, lib.Options(**kw), state=st)
+    torch.cuda.synchronize()
+    imgs = [_np(x) for x in lib.split_views(rgb, cams, 3)]
+    ts = [_np(x) for x in lib.split_views(T, cams, 1)]
+    return imgs, ts
+
+
+# ------------------------------------------------------------ projection
+def test_projection_records_match_oracle(lib, ctx):
+    scene, cams = scenes.tiny_workload()
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    st = lib.State(ctx)
+    lib.render(gs, cams, lib.Options(flags=lib.FLAG_KEEP_SPLATS), state=st)
+    sp = st.read(lib.BUF_SPLATS, np.uint8).view(lib.SPLAT_DTYPE)
+    pr = P.project(scene, cams[0])
+    mx, my, r, key = BN.records_f32(pr)
+    on = BN.rect_ranges(mx, my, r, 256, 256, 8, 8)[4] > 0
+    amb = pr["ambiguous"]
+    gvis = sp["radius"] > 0
+    assert np.array_equal(gvis[~amb], on[~amb])
+    both = gvis & on & ~amb
+    assert both.sum() > 5000
+    assert np.array_equal(sp["depth_key"][both], pr["depth_key"][both])
+    assert np.array_equal(sp["radius"][both], pr["radius"][both])
+    np.testing.assert_allclose(sp["mean2d"][both], pr["mean2d"][both], atol=1e-3)
+    cn = pr["conic"][both]
+    scale = np.maximum(np.abs(cn[:, 0]), np.abs(cn[:, 2]))[:, None]
+    assert np.all(np.abs(sp["conic"][both] - cn) <= 1e-4 * scale)
+    np.testing.assert_allclose(sp["rgb"][both], pr["rgb"][both], atol=1e-5)
+    np.testing.assert_allclose(sp["opacity"][both], pr["opacity"][both], atol=1e-6)
+
+
+def test_projection_sh3_colour(lib, ctx):
+    """Degree-3 SH colour of the cluster scene against the Legendre-based
+    oracle basis (view-dependent colour)."""
+    scene = scenes.cluster_scene(4096 + 77, 8, 1.2, seed=3, sigma_range=scenes.CLUSTER_SIGMA,
+                                 extent=scenes.EXTENT)
+    cams = scenes.scene_orbit(2, 320, 200)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    st = lib.State(ctx)
+    lib.render(gs, cams, lib.Options(flags=lib.FLAG_KEEP_SPLATS), state=st)
+    sp = st.read(lib.BUF_SPLATS, np.uint8).view(lib.SPLAT_DTYPE).reshape(2, -1)
+    for v, cam in enumerate(cams):
+        pr = P.project(scene, cam)
+        ok = (sp[v]["radius"] > 0) & pr["visible"] & ~pr["ambiguous"]
+        assert ok.sum() > 1000
+        np.testing.assert_allclose(sp[v]["rgb"][ok], pr["rgb"][ok], atol=2e-5)
+        assert np.array_equal(sp[v]["depth_key"][ok], pr["depth_key"][ok])
+
+
+# ------------------------------------------------------------ discrete stages
+def _gate(lib, ctx, projs, cams, macro=(8, 4), cap=1024):
+    """Render oracle records through hg_render_splats and compare pairs, keys
+    and batch boundaries bit-exactly with the oracle's stages."""
+    import torch
+    n = projs[0]["n"]
+    rec = splat_records(projs, lib.SPLAT_DTYPE)
+    d = lib.splats_to_device(rec)
+    st = lib.State(ctx)
+    lib.render_splats(ctx, d, n, cams, lib.Options(macro_w=macro[0], macro_h=macro[1], batch_cap=cap), state=st)
+    torch.cuda.synchronize()
+    seg_off = st.read(lib.BUF_SEG_OFF).astype(np.int64)
+    keys = st.read(lib.BUF_PAIR_KEYS)
+    ids = st.read(lib.BUF_PAIR_IDS).astype(np.int64)
+    bt = st.read(lib.BUF_BATCHES).reshape(-1, 3).astype(np.int64)
+    ref = BN.segments([BN.records_f32(p) for p in projs], [(c.width, c.height) for c in cams],
+                      macro[0] * 8, macro[1] * 8)
+    assert np.array_equal(seg_off, ref["seg_off"])
+    assert np.array_equal(keys, ref["keys"])
+    assert np.array_equal(ids, ref["ids"])
+    tab, first = BN.batches(ref["seg_off"], cap)
+    assert np.array_equal(bt, tab)
+    return st.stats()
+
+
+@pytest.mark.parametrize("macro", [(8, 4), (4, 4), (8, 8)])
+@pytest.mark.parametrize("cap", [32, 256, 1024])
+def test_discrete_stages_tiny(lib, ctx, macro, cap):
+    scene, cams = scenes.tiny_workload()
+    _gate(lib, ctx, [P.project(scene, cams[0])], cams, macro, cap)
+
+
+def test_discrete_stages_multiview_mixed_resolution(lib, ctx):
+    scene = scenes.uniform_scene(20_000, seed=4)
+    cams = [scenes.look_at((3, 0, 0), width=256, height=256),
+            scenes.look_at((0, 3, 0.5), width=200, height=120),
+            scenes.look_at((-2, -2, 1), width=97, height=61)]
+    _gate(lib, ctx, [P.project(scene, c) for c in cams], cams)
+
+
+def _synthetic_records(n, w, h, n_keys, seed, rad_max=3):
+    """Hand-made records: dense screen positions, few distinct depth keys
+    (ties), so segments exceed the shared-memory tiers."""
+    g = np.random.default_rng(seed)
+    keys = np.sort(g.uniform(2.0, 3.0, n_keys)).astype(np.float32).view(np.uint32)
+    pr = {"n": n, "mean2d": np.stack([g.uniform(0, w, n), g.uniform(0, h, n)], 1),
+          "conic": np.tile([0.5, 0.0, 0.5], (n, 1)), "opacity": np.full(n, 0.5), "rgb": np.full((n, 3), 0.5),
+          "depth_key": keys[g.integers(0, n_keys, n)], "radius": g.integers(1, rad_max + 1, n),
+          "depth": np.full(n, 2.5)}
+    pr["radius"][g.random(n) < 0.01] = 0  # some culled
+    return pr
+
+
+def test_discrete_stages_onesweep_and_ties(lib, ctx):
+    """Segments of 20K-100K pairs (onesweep path) and 1K-16K (tier sorts),
+    depth keys drawn from 3,000 values so equal keys are common."""
+    cam = scenes.look_at((3, 0, 0), width=130, height=70)
+    pr = _synthetic_records(300_000, 130, 70, 3000, seed=0)
+    st = _gate(lib, ctx, [pr], [cam])
+    assert st["seg_by_tier"][3] > 0 and st["n_sort_tiles"] > 1
+    st2 = _gate(lib, ctx, [pr], [cam], macro=(4, 4), cap=2048)
+    assert st2["seg_by_tier"][3] > 0
+
+
+def test_discrete_stages_all_tiers(lib, ctx):
+    cam = scenes.look_at((3, 0, 0), width=640, height=96)
+    g = np.random.default_rng(5)
+    parts = []
+    for n, w in ((400, 64), (3000, 128), (12000, 256), (40000, 512)):
+        p = _synthetic_records(n, 64, 32, 500, seed=int(g.integers(1 << 30)))
+        p["mean2d"][:, 0] += w - 64  # one macro column per density
+        parts.append(p)
+    pr = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if k != "n"}
+    pr["n"] = len(pr["radius"])
+    st = _gate(lib, ctx, [pr], [cam])
+    assert all(st["seg_by_tier"][t] > 0 for t in range(4))
+
+
+# ------------------------------------------------------------ images
+@pytest.mark.parametrize("path", ["higs", "plain"])
+def test_image_tiny(lib, ctx, path):
+    scene, cams = scenes.tiny_workload()
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    p = lib.PATH_HIGS if path == "higs" else lib.PATH_PLAIN
+    imgs, ts = render_np(lib, gs, cams, path=p)
+    ref = C.render(P.project(scene, cams[0]))
+    compare_image(imgs[0], ts[0], ref)
+
+
+@pytest.mark.parametrize("macro,cap", [((8, 4), 32), ((4, 4), 64), ((8, 8), 256), ((8, 4), 2048)])
+def test_image_invariant_to_macro_shape_and_cap(lib, ctx, macro, cap):
+    """Small caps force many batches per macro-tile and exercise the
+    exact-termination replay of the merge."""
+    scene = scenes.uniform_scene(30_000, seed=2)
+    scene.log_scales += np.float32(0.7)
+    cam = scenes.look_at((3, 0, 0), width=192, height=136)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    st = lib.State(ctx)
+    imgs, ts = render_np(lib, gs, [cam], macro_w=macro[0], macro_h=macro[1], batch_cap=cap, state=st)
+    ref = C.render(P.project(scene, cam))
+    compare_image(imgs[0], ts[0], ref)
+    if cap <= 64:
+        assert st.stats()["n_replays"] > 0
+
+
+def test_image_background_and_multiview(lib, ctx):
+    scene = scenes.uniform_scene(8000, seed=6)
+    cams = [scenes.look_at((3, 0, 0), width=128, height=128),
+            scenes.look_at((0, 3, 1), width=100, height=75),
+            scenes.look_at((-3, 0.5, -1), width=33, height=17)]
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    bg = (0.2, 0.5, 0.9)
+    for path in (lib.PATH_HIGS, lib.PATH_PLAIN):
+        imgs, ts = render_np(lib, gs, cams, path=path, bg=bg)
+        for v, cam in enumerate(cams):
+            ref = C.render(P.project(scene, cam), bg=bg)
+            compare_image(imgs[v], ts[v], ref)
+
+
+def test_edge_cases_empty_culled_single(lib, ctx):
+    cam = scenes.look_at((3, 0, 0), width=40, height=24)
+    bg = (0.25, 0.5, 0.75)
+    # empty scene
+    empty = scenes.uniform_scene(1, seed=0).subset(slice(0, 0))
+    gs = lib.GpuScene.from_scene(ctx, empty)
+    for path in (lib.PATH_HIGS, lib.PATH_PLAIN):
+        imgs, ts = render_np(lib, gs, [cam], path=path, bg=bg)
+        assert np.all(imgs[0] == np.float32(bg)) and np.all(ts[0] == 1.0)
+    # everything behind the camera
+    behind = scenes.uniform_scene(333, seed=1)
+    behind.means[:, 0] += np.float32(10.0)
+    gs = lib.GpuScene.from_scene(ctx, behind)
+    imgs, ts = render_np(lib, gs, [cam], bg=bg)
+    assert np.all(imgs[0] == np.float32(bg))
+    # one gaussian, and 33 (not a multiple of the warp)
+    for n in (1, 33):
+        sc = scenes.uniform_scene(n, seed=7)
+        sc.means[:] = sc.means * np.float32(0.2)
+        sc.log_scales[:] = np.float32(-1.5)
+        gs = lib.GpuScene.from_scene(ctx, sc)
+        for path in (lib.PATH_HIGS, lib.PATH_PLAIN):
+            imgs, ts = render_np(lib, gs, [cam], path=path)
+            compare_image(imgs[0], ts[0], C.render(P.project(sc, cam)))
+
+
+def test_deterministic(lib, ctx):
+    scene = scenes.uniform_scene(30_000, seed=2)
+    cam = scenes.look_at((3, 0, 0), width=192, height=136)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    a = render_np(lib, gs, [cam], batch_cap=64)
+    b = render_np(lib, gs, [cam], batch_cap=64)
+    assert np.array_equal(a[0][0], b[0][0]) and np.array_equal(a[1][0], b[1][0])
+
+
+def test_image_1m_scene_sampled_tiles(lib, ctx):
+    """1M-gaussian SH3 cluster scene at 1080p, two orbit views, HiGS and the
+    plain path, on sampled tiles the oracle computes one by one."""
+    scene = scenes.scene_1m()
+    cams = scenes.scene_orbit(32, 1920, 1080)[:2]
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    for path in (lib.PATH_HIGS, lib.PATH_PLAIN):
+        imgs, ts = render_np(lib, gs, cams, path=path)
+        for v, cam in enumerate(cams):
+            tiles = sample_tiles(1920, 1080, 48, seed=v)
+            ref = C.render(P.project(scene, cam), tiles=tiles)
+            compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles))
