@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the hierarchically tiled 3DGS render path on one node.
+
+One step = one pass of the whole forward path (projection + SH, macro-tile
+binning, segmented sort, batch split, raster, ordered merge) over one batch of
+4 views of the 5.8M-gaussian SH-3 cluster scene at 1920x1080, replayed from a
+captured CUDA graph with the next 4 poses of a 64-pose orbit.  The value is
+frames (views) per second over all ranks; the plain one-CTA-per-8x8-tile path
+with a global 64-bit sort is timed the same way on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank renders its own poses of its own replica of
+the scene (weak scaling, no data-path collective).  `--impl reference` times
+the FP64 CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s at 5.8M gaussians, HiGS vs per-tile path; serving p99 ms"
+UNIT = "frames/s"
+VIEWS = 4
+N_POSES = 64
+WIDTH, HEIGHT = 1920, 1080
+# Sample of one oracle step: 1/ORACLE_FRACTION of the projection plus
+# ORACLE_TILES tiles of one view; a frame is ORACLE_FRACTION such steps.
+ORACLE_FRACTION = 1024
+ORACLE_TILES = 32
+# FP32-pipe instructions per (pixel, gaussian) evaluation of the blend step
+# (dy, u, w, w^2, e, support test, o*2^-e, min, alpha test, 1-alpha, T',
+# stop test, alpha*T, three colour FMAs)
+RASTER_OPS_PER_EVAL = 16
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "sm_max_mhz": d.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def workload_config():
+    from paper_2606_00352_gb300 import scenes
+    return {"workload": "5.8M-gaussian SH-3 cluster scene (256 clusters, Zipf 1.4), 1920x1080, "
+                        "4 views per captured CUDA graph, 64-pose orbit",
+            "n_gaussians": 5_800_000, "resolution": f"{WIDTH}x{HEIGHT}", "views_per_step": VIEWS,
+            "sh_degree": 3, "macro_tile": "8x4", "batch_cap": 1024, "scene_extent": scenes.EXTENT,
+            "orbit_radius": scenes.ORBIT_RADIUS,
+            "l2": "inputs larger than L2 (scene arrays 1.37 GB, records 1.5 GB per step)"}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample_steps(steps: int, warmup: int, seed: int = 0):
+    """Times the FP64 oracle on bounded samples of the workload (this
+    process; numpy single-threaded).  Returns per-step seconds."""
+    import numpy as np
+    from paper_2606_00352_gb300 import scenes
+    from oracle import project as P, composite as Cmp
+    scene = scenes.scene_5m8()
+    cam = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)[0]
+    full = P.project(scene, cam)  # full projection for the sampled tiles (not timed)
+    cand = Cmp.tile_candidates(full)
+    n = scene.n
+    sl = n // ORACLE_FRACTION
+    gw, gh = -(-WIDTH // 8), -(-HEIGHT // 8)
+    g = np.random.default_rng(seed)
+    times = []
+    for k in range(warmup + steps):
+        lo = (k * sl) % (n - sl)
+        part = scene.subset(slice(lo, lo + sl))
+        tiles = g.choice(gw * gh, ORACLE_TILES, replace=False)
+        t0 = time.perf_counter()
+        Cmp.tile_candidates(P.project(part, cam))   # 1/ORACLE_FRACTION of projection + binning
+        Cmp.render(full, tiles=tiles, cand=cand)     # ORACLE_TILES tiles of compositing
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+    return times
+
+
+def run_oracle_subprocess(steps: int, warmup: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-steps", str(steps),
+                          "--warmup", str(warmup)], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_desc(steps):
+    return (f"per step: FP64 projection + tile binning of 1/{ORACLE_FRACTION} of the 5.8M gaussians + {ORACLE_TILES} "
+            f"sampled 8x8 tiles of one 1080p view; {steps} steps; frame time = mean step x {ORACLE_FRACTION} "
+            f"({ORACLE_FRACTION * ORACLE_TILES} tiles ~ the 32,400 of a frame)")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait(timeout=5)
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def pose_batch(cams, step, rank):
+    base = (step * VIEWS + rank * 7 * VIEWS) % N_POSES
+    return [cams[(base + i) % N_POSES] for i in range(VIEWS)]
+
+
+def time_graph(lib, gs, cams, opts, steps, warmup, rank, world, stream, collect_stats=True):
+    """Replays the captured frame; per step: new poses, launch, wait.
+    Returns (ms for the timed steps, per-step stage stats)."""
+    import torch
+    pix = sum(c.width * c.height for c in cams[:VIEWS])
+    rgb = torch.empty(pix * 3, device="cuda", dtype=torch.float32)
+    T = torch.empty(pix, device="cuda", dtype=torch.float32)
+    state = lib.State(gs.ctx)
+    graph = lib.Graph(gs, pose_batch(cams, 0, rank), opts, rgb, T, state, stream)
+    for w in range(warmup):
+        graph.set_cameras(pose_batch(cams, w + 1, rank))
+        graph.launch()
+        graph.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    ev0.record(stream)
+    for k in range(steps):
+        graph.set_cameras(pose_batch(cams, warmup + 1 + k, rank))
+        graph.launch()
+        graph.sync()
+        if collect_stats:
+            stats.append(state.stats())
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    kernels = graph.kernels
+    graph.close()
+    state.close()
+    return ms, stats, kernels
+
+
+def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
+    """Public-API frames: hg_render with host cameras (uploaded by the call)
+    and the rendered images read back into pinned host memory every step."""
+    import torch
+    pix = sum(c.width * c.height for c in cams[:VIEWS])
+    rgb = torch.empty(pix * 3, device="cuda", dtype=torch.float32)
+    host = torch.empty(pix * 3, dtype=torch.float32, pin_memory=True)
+    state = lib.State(gs.ctx)
+    with torch.cuda.stream(stream):
+        for w in range(warmup):
+            lib.render(gs, pose_batch(cams, w, rank), opts, state=state, stream=stream, out_rgb=rgb, with_T=False)
+            host.copy_(rgb, non_blocking=True)
+            stream.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            lib.render(gs, pose_batch(cams, warmup + k, rank), opts, state=state, stream=stream, out_rgb=rgb,
+                       with_T=False)
+            host.copy_(rgb, non_blocking=True)
+            stream.synchronize()
+        dt = time.perf_counter() - t0
+    state.close()
+    view_desc_bytes = 144  # camera table entry uploaded per view by hg_render
+    return {"seconds": dt, "h2d": VIEWS * view_desc_bytes, "d2h": pix * 3 * 4}
+
+
+def roofline(stage_ms, stats0, n, pk, clock_mhz):
+    """Roofline of the stage that takes the most time per step."""
+    hbm_peak = pk["hbm_gbs"]
+    K = 16
+    proj_bytes = n * (44 + 12 * K) + VIEWS * n * (16 + 48) + VIEWS * ((n + 31) // 32) * 4
+    pairs = statistics.mean(s["n_pairs"] for s in stats0)
+    evals = statistics.mean(s["raster_evals"] for s in stats0)
+    alu_peak = 152 * FP32_LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12  # T FP32-pipe ops/s
+    table = {
+        "project": {"bound": "hbm", "units": proj_bytes, "peak": hbm_peak, "unit": "GB/s",
+                    "per_unit": "bytes: 236 read + 4 x 64 written + vis bits per gaussian"},
+        "partition": {"bound": "hbm", "units": VIEWS * n * 16 * 2 + pairs * 8, "peak": hbm_peak, "unit": "GB/s",
+                      "per_unit": "bytes: 16 per (view, gaussian) read by count and by fill + 8 per pair"},
+        "sort": {"bound": "hbm", "units": pairs * 16, "peak": hbm_peak, "unit": "GB/s",
+                 "per_unit": "bytes: 8 read + 8 written per pair"},
+        "raster": {"bound": "alu", "units": evals * RASTER_OPS_PER_EVAL, "peak": alu_peak, "unit": "Tops/s",
+                   "per_unit": f"{RASTER_OPS_PER_EVAL} FP32-pipe ops per (pixel, gaussian) evaluation"},
+    }
+    out = {}
+    for name, d in table.items():
+        ms = stage_ms[name]
+        if d["unit"] == "GB/s":
+            ach = d["units"] / (ms * 1e-3) / 1e9
+        else:
+            ach = d["units"] / (ms * 1e-3) / 1e12
+        out[name] = {"bound": d["bound"], "achieved": round(ach, 2), "peak": round(d["peak"], 1),
+                     "unit": d["unit"], "frac": round(ach / d["peak"], 4), "ms": round(ms, 4),
+                     "per_unit": d["per_unit"]}
+    top = max(("project", "partition", "sort", "raster"), key=lambda k: stage_ms[k])
+    return top, out
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    from paper_2606_00352_gb300 import higs, scenes
+    rank, world, local = dist_setup(args.gpus)
+    higs.load()
+    scene = scenes.scene_5m8()
+    cams = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)
+    ctx = higs.Context(torch.cuda.current_device())
+    gs = higs.GpuScene.from_scene(ctx, scene)
+    del scene
+    stream = torch.cuda.Stream()
+    pk = peaks()
+    opts = higs.Options(path=higs.PATH_HIGS, macro_w=8, macro_h=4, batch_cap=1024, flags=higs.FLAG_TIMING)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, stats, kernels = time_graph(higs, gs, cams, opts, args.steps, args.warmup, rank, world, stream)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms, world)
+    frames = sum_over_ranks(args.steps * VIEWS, world)
+    value = frames / (ms * 1e-3)
+
+    stage_ms = {k: statistics.mean(s["ms_" + k] for s in stats) for k in
+                ("project", "partition", "sort", "raster", "merge")}
+    top, rl = roofline(stage_ms, stats, gs.n, pk, clocks.get("sm_mhz") or pk["sm_max_mhz"])
+
+    plain = None
+    if not args.skip_plain:
+        popts = higs.Options(path=higs.PATH_PLAIN, flags=higs.FLAG_TIMING)
+        psteps = max(3, min(args.steps, 10))
+        pms, pstats, _ = time_graph(higs, gs, cams, popts, psteps, min(args.warmup, 3), rank, world, stream)
+        pms = max_over_ranks(pms, world)
+        plain = {"value": round(sum_over_ranks(psteps * VIEWS, world) / (pms * 1e-3), 2), "unit": UNIT,
+                 "ms_per_step": round(pms / psteps, 3),
+                 "tile_pairs_per_step": int(statistics.mean(s["n_pairs"] for s in pstats))}
+
+    e2e_opts = higs.Options(path=higs.PATH_HIGS)
+    e2e_steps = max(3, min(args.steps, 10))
+    e = time_e2e(higs, gs, cams, e2e_opts, e2e_steps, min(args.warmup, 3), rank, stream)
+    e2e_t = max_over_ranks(e["seconds"], world)
+    e2e = {"value": round(sum_over_ranks(e2e_steps * VIEWS, world) / e2e_t, 2), "unit": UNIT,
+           "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        r = run_oracle_subprocess(steps=8, warmup=1)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": oracle_sample_desc(8)}
+    s0 = stats
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(),
+        "roofline": {k: v for k, v in rl[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
+        | {"kernel": top, "traffic": None, "peak_source": pk["source"]},
+        "stages": rl | {"merge": {"ms": round(stage_ms["merge"], 4)}},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(kernels * args.steps),
+        "clocks": clocks,
+        "plain_path": plain,
+        "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
+        "frame_stats": {
+            "pairs_per_step": int(statistics.mean(s["n_pairs"] for s in s0)),
+            "batches_per_step": int(statistics.mean(s["n_batches"] for s in s0)),
+            "max_segment": int(max(s["max_segment"] for s in s0)),
+            "segments_by_tier": s0[-1]["seg_by_tier"],
+            "replays_per_step": int(statistics.mean(s["n_replays"] for s in s0)),
+            "raster_evals_per_step": int(statistics.mean(s["raster_evals"] for s in s0)),
+            "visible_per_step": int(statistics.mean(s["n_visible"] for s in s0)),
+        },
+        "serving_p99_ms": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    r = run_oracle_subprocess(steps=args.steps, warmup=args.warmup)
+    fps = r["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": int(args.gpus),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": fps, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": oracle_sample_desc(args.steps)},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.oracle_steps:
+        args.warmup = 3
+    if args.oracle_steps:
+        times = oracle_sample_steps(args.oracle_steps, args.warmup)
+        ms = statistics.mean(times) * 1e3
+        print(json.dumps({"value": 1.0 / (statistics.mean(times) * ORACLE_FRACTION), "ms_per_step": ms,
+                          "times": times}))
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

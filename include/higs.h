@@ -209,6 +209,31 @@ enum { HG_BUF_SEG_OFF = 0, HG_BUF_PAIR_KEYS = 1, HG_BUF_PAIR_IDS = 2, HG_BUF_BAT
 hg_status hg_state_read(hg_state* state, int which, void* dst, size_t dst_bytes,
                         size_t* bytes_needed);
 
+/* ------------------------------------------------------------ CUDA graphs */
+/* Multi-view frames in one captured CUDA graph (the batching of several
+ * views per launch).  hg_graph_create renders one sizing frame
+ * synchronously on `stream` (non-default stream required), grows `state`'s
+ * workspace with headroom, then captures the whole pipeline for these views
+ * into a graph that writes out_rgb / out_T.  `state` must stay alive and must
+ * not be used by other calls while the graph exists. */
+hg_status hg_graph_create(hg_scene* scene, const hg_camera* cams, int n_views, const hg_render_opts* opts,
+                          float* out_rgb, float* out_T, hg_state* state, void* stream, hg_graph** out);
+/* Enqueue one replay on `stream` (NULL = the capture stream). */
+hg_status hg_graph_launch(hg_graph* graph, void* stream);
+/* New poses with the captured count and resolutions for the next replay;
+ * call only when no replay is pending (after hg_graph_sync). */
+hg_status hg_graph_set_cameras(hg_graph* graph, const hg_camera* cams, int n_views);
+/* Wait for the last replay and return its device status; HG_ERR_CAPACITY
+ * means a pose binned more pairs than the capture allows: create the graph
+ * again from that pose. */
+hg_status hg_graph_sync(hg_graph* graph);
+/* Kernels one replay launches. */
+int64_t hg_graph_kernels(const hg_graph* graph);
+void hg_graph_destroy(hg_graph* graph);
+
+/* Kernel launches issued by the library so far (all contexts). */
+int64_t hg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -152,10 +152,11 @@ def _tile_pixels(tx, ty, tile, w, h):
     return px.ravel(), py.ravel()
 
 
-def render(proj: dict, bg=(0.0, 0.0, 0.0), tiles=None, tile: int = 8):
+def render(proj: dict, bg=(0.0, 0.0, 0.0), tiles=None, tile: int = 8, cand=None):
     """Full image (or only the listed tile indices) in float64.
 
-    Returns dict: rgb [H, W, 3], T [H, W], stopped [H, W], margins
+    `cand` may hold the result of ``tile_candidates(proj, tile)`` computed
+    earlier.  Returns dict: rgb [H, W, 3], T [H, W], stopped [H, W], margins
     (q, alpha, T) [H, W] and a boolean `done` mask of evaluated pixels.
     """
     w, h = proj["width"], proj["height"]
@@ -164,7 +165,7 @@ def render(proj: dict, bg=(0.0, 0.0, 0.0), tiles=None, tile: int = 8):
            "stopped": np.zeros((h, w), bool), "done": np.zeros((h, w), bool)}
     for k in ("q", "alpha", "T"):
         out["m_" + k] = np.full((h, w), np.inf)
-    gw, gh, off, gid = tile_candidates(proj, tile)
+    gw, gh, off, gid = tile_candidates(proj, tile) if cand is None else cand
     todo = range(gw * gh) if tiles is None else tiles
     rgb_all, op_all = proj["rgb"], proj["opacity"]
     for t in todo:

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,12 @@
 using namespace hg;
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+namespace hg {
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hg
 
 void hg_set_error(const std::string& s) { g_last_error = s; }
 
@@ -48,6 +55,7 @@ extern "C" const char* hg_status_str(hg_status s) {
 
 extern "C" const char* hg_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char* hg_version(void) { return "higs-gb300 0.1 (sm_103a)"; }
+extern "C" int64_t hg_kernel_launches(void) { return hg::launches_issued(); }
 
 // ---------------------------------------------------------------- memory
 void* ctx_alloc(hg_ctx* ctx, size_t bytes, cudaStream_t st) {
@@ -282,7 +290,7 @@ static void sizes_from_counters(hg_state* s, const FrameGeom& g, const hg_render
   (void)g;
 }
 
-static hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o, const FrameGeom& g,
+hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o, const FrameGeom& g,
                                float* out_rgb, float* out_T, cudaStream_t st) {
   const long long n = in.n;
   const int V = g.V;

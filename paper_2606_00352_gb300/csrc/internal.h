@@ -81,5 +81,7 @@ void ctx_free(hg_ctx* ctx, void* p, size_t bytes, cudaStream_t st);
 hg_status ws_ensure(hg_state* s, int id, size_t bytes, cudaStream_t st);
 hg_status state_create(hg_ctx* ctx, hg_state** out);
 hg_status build_views(hg_state* s, const hg_camera* cams, int V, const hg_render_opts* o, hg::FrameGeom& g);
+hg_status enqueue_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg::FrameGeom& g,
+                        float* out_rgb, float* out_T, cudaStream_t st);
 hg_status run_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg_camera* cams, int V,
                     float* out_rgb, float* out_T, cudaStream_t st);

@@ -162,6 +162,10 @@ cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* ke
                             uint32_t* claims, int first_pass, int npass, FrameCounters* fc, cudaStream_t st,
                             bool* result_in_alt);
 
+// Host-side count of kernel launches issued by this library (all threads).
+void note_launch(int n = 1);
+long long launches_issued();
+
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words, uint4* bin,
                                      float4* rec, uint32_t* vis, cudaStream_t st);

@@ -162,6 +162,7 @@ cudaError_t launch_merge_shape(const MergeArgs& a, cudaStream_t st) {
   int blocks = min((a.total_tiles + 7) / 8, sms * 8);
   if (blocks < 1) blocks = 1;
   k_merge<MW, MH><<<blocks, 256, 0, st>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -260,14 +260,19 @@ cudaError_t launch_partition(const PartitionArgs& a, cudaStream_t st) {
   if (a.n_pb == 0 || a.n_seg == 0) return cudaSuccess;
   dim3 g(a.n_pb, a.n_views);
   k_count<<<g, PART_THREADS, sm, st>>>(a);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_colscan<<<(a.n_seg + 31) / 32, dim3(32, 32), 0, st>>>(a);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_segscan<<<1, 1024, 0, st>>>(a);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_fill<<<g, PART_THREADS, sm, st>>>(a);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_batches<<<(a.n_seg + 255) / 256, 256, 0, st>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 

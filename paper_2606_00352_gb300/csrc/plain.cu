@@ -178,17 +178,24 @@ cudaError_t launch_plain(PlainArgs& a, cudaStream_t st, unsigned long long** sor
     *sorted_vals = a.vals;
     if ((e = cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * a.total_tiles, st)) != cudaSuccess) return e;
     k_plain_raster<<<a.total_tiles, TILE_PX, 0, st>>>(a, a.vals);
+    note_launch();
     return cudaGetLastError();
   }
   const unsigned g = (unsigned)((total + 255) / 256);
   k_plain_count<<<g, 256, 0, st>>>(a);
+  note_launch();
   const int nblk = (int)((total + SCAN_B - 1) / SCAN_B);
   k_scan_blocks<<<nblk, SCAN_T, 0, st>>>(a.counts, a.offsets, a.scan_tmp, total);
+  note_launch();
   k_scan_sums<<<1, SCAN_T, 0, st>>>(a.scan_tmp, nblk, a.offsets, total, a);
+  note_launch();
   k_scan_add<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a.offsets, a.scan_tmp, total);
+  note_launch();
   uint4* tiles = reinterpret_cast<uint4*>(a.scan_tmp + ((nblk + 3) & ~3));
   k_plain_tiles<<<256, 256, 0, st>>>(a, tiles);
+  note_launch();
   k_plain_dup<<<g, 256, 0, st>>>(a);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // passes: the depth bytes plus the bytes of the global tile index
   int tile_bits = 1;
@@ -206,7 +213,9 @@ cudaError_t launch_plain(PlainArgs& a, cudaStream_t st, unsigned long long** sor
   *sorted_vals = sv;
   if ((e = cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * a.total_tiles, st)) != cudaSuccess) return e;
   k_plain_ranges<<<1024, 256, 0, st>>>(a, sk);
+  note_launch();
   k_plain_raster<<<a.total_tiles, TILE_PX, 0, st>>>(a, sv);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -292,6 +292,7 @@ static cudaError_t launch_project_deg(const ProjectArgs& a, cudaStream_t st) {
   long long blocks = (a.n + PROJ_THREADS - 1) / PROJ_THREADS;
   if (blocks == 0) return cudaSuccess;
   k_project<DEG><<<(unsigned)blocks, PROJ_THREADS, sm, st>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -310,6 +311,7 @@ cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_view
   cudaError_t e = cudaMemsetAsync(vis, 0, sizeof(uint32_t) * vis_words * n_views, st);
   if (e != cudaSuccess || total == 0) return e;
   k_splats_to_records<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, total, n, vis_words, bin, rec, vis);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -214,6 +214,7 @@ cudaError_t launch_raster_shape(const RasterArgs& a, int cap, cudaStream_t st) {
   if (occ < 1) occ = 1;
   const int grid = a.persistent_ctas > 0 ? a.persistent_ctas : sms * occ;
   k_raster<MW, MH><<<grid, RT, sm, st>>>(a, cap);
+  note_launch();
   return cudaGetLastError();
 }
 

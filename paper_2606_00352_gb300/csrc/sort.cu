@@ -312,6 +312,7 @@ static cudaError_t launch_tier(const SortArgs& a, int tier, int blocks_per_sm, c
   cudaError_t e = cudaFuncSetAttribute(k_block_sort<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_block_sort<NT, IPT><<<num_sms() * blocks_per_sm, NT, sm, st>>>(a, tier);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -324,6 +325,7 @@ cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* ke
   if (e != cudaSuccess) return e;
   const int grid = num_sms() * 2;
   k_os_hist<K, NPASS><<<grid, OS_THREADS, 0, st>>>(tv, keys, seg_hist, fc);
+  note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   size_t sm = sizeof(OneSweepSmem<K>);
   e = cudaFuncSetAttribute(k_os_pass<K, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -339,6 +341,7 @@ cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* ke
     e = cudaMemsetAsync(lookback, 0, lookback_words * 4, st);
     if (e != cudaSuccess) return e;
     k_os_pass<K, NPASS><<<num_sms() * occ, OS_THREADS, sm, st>>>(tv, sk, sv, dk, dv, lookback, claims + p, p, fc);
+    note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     K* tk = sk;
     sk = dk;
@@ -368,6 +371,7 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
                                    a.fc->os_claim, 0, 4, a.fc, st, &alt);
   if (e != cudaSuccess) return e;
   k_os_fixup<<<num_sms() * 4, 256, 0, st>>>(tv, a.keys, a.vals, a.fc);
+  note_launch();
   return cudaGetLastError();
 }
 

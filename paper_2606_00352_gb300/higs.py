@@ -25,7 +25,9 @@ BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_
 
 EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",
            "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",
-           "hg_state_free", "hg_state_sync", "hg_render_stats", "hg_state_read"]
+           "hg_state_free", "hg_state_sync", "hg_render_stats", "hg_state_read", "hg_graph_create",
+           "hg_graph_launch", "hg_graph_set_cameras", "hg_graph_sync", "hg_graph_kernels", "hg_graph_destroy",
+           "hg_kernel_launches"]
 
 
 class HgError(RuntimeError):
@@ -89,8 +91,18 @@ def load(path: str = LIB_PATH):
     lib.hg_version.restype = C.c_char_p
     lib.hg_scene_size.restype = C.c_int64
     for name in ("hg_ctx_create", "hg_create_scene", "hg_render", "hg_render_splats",
-                 "hg_state_sync", "hg_render_stats", "hg_state_read"):
+                 "hg_state_sync", "hg_render_stats", "hg_state_read", "hg_graph_create", "hg_graph_launch",
+                 "hg_graph_set_cameras", "hg_graph_sync"):
         getattr(lib, name).restype = C.c_int
+    lib.hg_graph_create.argtypes = [C.c_void_p, C.POINTER(CameraC), C.c_int, C.POINTER(RenderOpts), C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.hg_graph_launch.argtypes = [C.c_void_p, C.c_void_p]
+    lib.hg_graph_set_cameras.argtypes = [C.c_void_p, C.POINTER(CameraC), C.c_int]
+    lib.hg_graph_sync.argtypes = [C.c_void_p]
+    lib.hg_graph_kernels.argtypes = [C.c_void_p]
+    lib.hg_graph_kernels.restype = C.c_int64
+    lib.hg_graph_destroy.argtypes = [C.c_void_p]
+    lib.hg_kernel_launches.restype = C.c_int64
     lib.hg_ctx_create.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
     lib.hg_ctx_destroy.argtypes = [C.c_void_p]
     lib.hg_create_scene.argtypes = [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(C.c_void_p)]
@@ -262,6 +274,51 @@ def _out_tensors(cams, device, out_rgb=None, out_T=None, with_T=True):
     if out_T is None and with_T:
         out_T = torch.empty(pix, dtype=torch.float32, device=device)
     return out_rgb, out_T
+
+
+class Graph:
+    """A captured multi-view frame (hg_graph_*): replay with new poses of the
+    same resolutions."""
+
+    def __init__(self, scene: GpuScene, cams, opts: Options, out_rgb, out_T, state: State, stream):
+        self.lib = scene.ctx.lib
+        if not state.h:
+            # the state's workspace is created by a first synchronous render
+            render(scene, cams, Options(**{**opts.__dict__, "flags": 0}), state=state, stream=stream,
+                   out_rgb=out_rgb, out_T=out_T)
+        cam_arr = cameras_array(cams)
+        o = opts.struct()
+        h = C.c_void_p()
+        check(self.lib.hg_graph_create(scene.h, cam_arr, len(cams), C.byref(o), C.c_void_p(out_rgb.data_ptr()),
+                                       C.c_void_p(out_T.data_ptr()) if out_T is not None else None, state.h,
+                                       C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self.h, self.state, self.scene, self.stream, self.n_views = h, state, scene, stream, len(cams)
+        self.kernels = int(self.lib.hg_graph_kernels(h))
+
+    def set_cameras(self, cams):
+        check(self.lib.hg_graph_set_cameras(self.h, cameras_array(cams), len(cams)))
+
+    def launch(self, stream=None):
+        s = self.stream if stream is None else stream
+        check(self.lib.hg_graph_launch(self.h, C.c_void_p(s.cuda_stream)))
+
+    def sync(self):
+        check(self.lib.hg_graph_sync(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.hg_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches() -> int:
+    return int(load().hg_kernel_launches())
 
 
 def split_views(flat, cams, channels):
