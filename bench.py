@@ -277,7 +277,7 @@ def roofline(stage_ms, stats0, n, pk, clock_mhz):
     }
     out = {}
     for name, d in table.items():
-        ms = stage_ms[name]
+        ms = max(stage_ms[name], 1e-6)
         if d["unit"] == "GB/s":
             ach = d["units"] / (ms * 1e-3) / 1e9
         else:

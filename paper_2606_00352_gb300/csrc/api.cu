@@ -319,7 +319,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   if (o->flags & HG_FLAG_KEEP_SPLATS) ENS(B_SPLATS, sizeof(hg_splat) * n * V);
   FrameCounters* fc = (FrameCounters*)s->bufs[B_FC].p;
   ViewDesc* views = (ViewDesc*)s->bufs[B_VIEWS].p;
-  if (timing) cudaEventRecord(s->ev[0], st);
+  if (timing) cudaEventRecordWithFlags(s->ev[0], st, cudaEventRecordExternal);
   HG_TRY(cudaMemsetAsync(fc, 0, sizeof(FrameCounters), st), "memset counters");
   HG_TRY(cudaMemcpyAsync(views, s->views_host, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st), "upload views");
   if (in.splats) {
@@ -344,7 +344,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pa.fc = fc;
     HG_TRY(launch_project(pa, in.scene->deg, st), "project");
   }
-  if (timing) cudaEventRecord(s->ev[1], st);
+  if (timing) cudaEventRecordWithFlags(s->ev[1], st, cudaEventRecordExternal);
 
   if (o->path == HG_PATH_PLAIN) {
     ENS(P_COUNTS, sizeof(uint32_t) * n * V);
@@ -385,7 +385,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     uint32_t* sv = nullptr;
     HG_TRY(launch_plain(pa, st, &sk, &sv), "plain path");
     if (timing)
-      for (int k = 2; k < 6; ++k) cudaEventRecord(s->ev[k], st);
+      for (int k = 2; k < 6; ++k) cudaEventRecordWithFlags(s->ev[k], st, cudaEventRecordExternal);
   } else {
     ENS(B_HIST, sizeof(uint16_t) * (size_t)n_pb * g.S + 16);
     ENS(B_COLPRE, sizeof(uint32_t) * (size_t)n_pb * g.S + 16);
@@ -445,7 +445,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pa.cap_big_segs = (uint32_t)s->cap_big_segs;
     pa.fc = fc;
     if (n > 0) HG_TRY(launch_partition(pa, st), "partition");
-    if (timing) cudaEventRecord(s->ev[2], st);
+    if (timing) cudaEventRecordWithFlags(s->ev[2], st, cudaEventRecordExternal);
 
     SortArgs sa{};
     sa.keys = pa.keys;
@@ -464,7 +464,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     sa.cap_big_segs = pa.cap_big_segs;
     sa.fc = fc;
     if (n > 0) HG_TRY(launch_sort(sa, st), "sort");
-    if (timing) cudaEventRecord(s->ev[3], st);
+    if (timing) cudaEventRecordWithFlags(s->ev[3], st, cudaEventRecordExternal);
 
     HG_TRY(cudaMemsetAsync(s->bufs[B_TILESAT].p, 0xff, sizeof(uint32_t) * g.total_tiles, st), "memset tile_sat");
     RasterArgs ra{};
@@ -488,7 +488,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.persistent_ctas = 0;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");
-    if (timing) cudaEventRecord(s->ev[4], st);
+    if (timing) cudaEventRecordWithFlags(s->ev[4], st, cudaEventRecordExternal);
 
     MergeArgs ma{};
     ma.partial = ra.partial;
@@ -513,7 +513,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
       HG_TRY(cudaMemsetAsync(pa.first_batch, 0, sizeof(uint32_t) * (g.S + 1), st), "memset first_batch");
     }
     HG_TRY(launch_merge(ma, st), "merge");
-    if (timing) cudaEventRecord(s->ev[5], st);
+    if (timing) cudaEventRecordWithFlags(s->ev[5], st, cudaEventRecordExternal);
   }
   HG_TRY(cudaMemcpyAsync(s->fc_host, fc, sizeof(FrameCounters), cudaMemcpyDeviceToHost, st), "read counters");
 #undef ENS
