@@ -57,6 +57,15 @@ extern "C" const char* hg_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char* hg_version(void) { return "higs-gb300 0.1 (sm_103a)"; }
 extern "C" int64_t hg_kernel_launches(void) { return hg::launches_issued(); }
 
+// Stage timing events: inside a stream capture an event record must be an
+// external node to be recorded when the graph runs.
+static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  return cudaEventRecord(ev, st);
+}
+
 // ---------------------------------------------------------------- memory
 void* ctx_alloc(hg_ctx* ctx, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 256;
@@ -80,6 +89,12 @@ void ctx_free(hg_ctx* ctx, void* p, size_t bytes, cudaStream_t st) {
 hg_status ws_ensure(hg_state* s, int id, size_t bytes, cudaStream_t st) {
   Buf& b = s->bufs[id];
   if (b.bytes >= bytes && b.p) return HG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    hg_set_error("workspace buffer " + std::to_string(id) + " must grow to " + std::to_string(bytes) +
+                 " bytes during graph capture");
+    return HG_ERR_CAPACITY;
+  }
   if (b.p) {
     // the old buffer may still be read by work queued earlier on any stream
     cudaDeviceSynchronize();
@@ -319,7 +334,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   if (o->flags & HG_FLAG_KEEP_SPLATS) ENS(B_SPLATS, sizeof(hg_splat) * n * V);
   FrameCounters* fc = (FrameCounters*)s->bufs[B_FC].p;
   ViewDesc* views = (ViewDesc*)s->bufs[B_VIEWS].p;
-  if (timing) cudaEventRecordWithFlags(s->ev[0], st, cudaEventRecordExternal);
+  if (timing) HG_TRY(record_stage(s->ev[0], st), "stage event 0");
   HG_TRY(cudaMemsetAsync(fc, 0, sizeof(FrameCounters), st), "memset counters");
   HG_TRY(cudaMemcpyAsync(views, s->views_host, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st), "upload views");
   if (in.splats) {
@@ -344,7 +359,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pa.fc = fc;
     HG_TRY(launch_project(pa, in.scene->deg, st), "project");
   }
-  if (timing) cudaEventRecordWithFlags(s->ev[1], st, cudaEventRecordExternal);
+  if (timing) HG_TRY(record_stage(s->ev[1], st), "stage event 1");
 
   if (o->path == HG_PATH_PLAIN) {
     ENS(P_COUNTS, sizeof(uint32_t) * n * V);
@@ -385,7 +400,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     uint32_t* sv = nullptr;
     HG_TRY(launch_plain(pa, st, &sk, &sv), "plain path");
     if (timing)
-      for (int k = 2; k < 6; ++k) cudaEventRecordWithFlags(s->ev[k], st, cudaEventRecordExternal);
+      for (int k = 2; k < 6; ++k) HG_TRY(record_stage(s->ev[k], st), "stage event");
   } else {
     ENS(B_HIST, sizeof(uint16_t) * (size_t)n_pb * g.S + 16);
     ENS(B_COLPRE, sizeof(uint32_t) * (size_t)n_pb * g.S + 16);
@@ -445,7 +460,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pa.cap_big_segs = (uint32_t)s->cap_big_segs;
     pa.fc = fc;
     if (n > 0) HG_TRY(launch_partition(pa, st), "partition");
-    if (timing) cudaEventRecordWithFlags(s->ev[2], st, cudaEventRecordExternal);
+    if (timing) HG_TRY(record_stage(s->ev[2], st), "stage event 2");
 
     SortArgs sa{};
     sa.keys = pa.keys;
@@ -464,7 +479,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     sa.cap_big_segs = pa.cap_big_segs;
     sa.fc = fc;
     if (n > 0) HG_TRY(launch_sort(sa, st), "sort");
-    if (timing) cudaEventRecordWithFlags(s->ev[3], st, cudaEventRecordExternal);
+    if (timing) HG_TRY(record_stage(s->ev[3], st), "stage event 3");
 
     HG_TRY(cudaMemsetAsync(s->bufs[B_TILESAT].p, 0xff, sizeof(uint32_t) * g.total_tiles, st), "memset tile_sat");
     RasterArgs ra{};
@@ -488,7 +503,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.persistent_ctas = 0;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");
-    if (timing) cudaEventRecordWithFlags(s->ev[4], st, cudaEventRecordExternal);
+    if (timing) HG_TRY(record_stage(s->ev[4], st), "stage event 4");
 
     MergeArgs ma{};
     ma.partial = ra.partial;
@@ -513,7 +528,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
       HG_TRY(cudaMemsetAsync(pa.first_batch, 0, sizeof(uint32_t) * (g.S + 1), st), "memset first_batch");
     }
     HG_TRY(launch_merge(ma, st), "merge");
-    if (timing) cudaEventRecordWithFlags(s->ev[5], st, cudaEventRecordExternal);
+    if (timing) HG_TRY(record_stage(s->ev[5], st), "stage event 5");
   }
   HG_TRY(cudaMemcpyAsync(s->fc_host, fc, sizeof(FrameCounters), cudaMemcpyDeviceToHost, st), "read counters");
 #undef ENS
