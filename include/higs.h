@@ -231,6 +231,32 @@ hg_status hg_graph_sync(hg_graph* graph);
 int64_t hg_graph_kernels(const hg_graph* graph);
 void hg_graph_destroy(hg_graph* graph);
 
+/* ---------------------------------------------------- allocation-free sort */
+/* Segmented sort of (uint32 key, uint32 value) pairs, ascending by (key,
+ * value) inside each segment, with no device allocation at all.  This is an
+ * extra entry point with no counterpart in the paper: it exists for callers
+ * that cannot call cudaMalloc where they sort (code running inside another
+ * allocator's callback, or a host process that must not touch the device
+ * heap while other work is in flight).  Its scratch (look-back words, digit
+ * histograms, tile descriptors and a ping-pong copy of the pairs, about
+ * 7 MB) is one fixed device array inside the library that every GPU which
+ * loads the library holds until the process exits.
+ *  d_seg_off: device [n_seg + 1], non-decreasing, d_seg_off[0] = 0,
+ *             d_seg_off[n_seg] = n_pairs (copied to the host and checked).
+ *  d_keys_in / d_vals_in: device [n_pairs], not modified.
+ *  d_keys_out / d_vals_out: device [n_pairs], the sorted pairs.
+ * Limits: n_pairs <= 524288 and n_seg <= 512; larger inputs are rejected
+ * with HG_ERR_INVALID_ARG and a message, before any device work.
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  Every call clears the parts of the array that must start at
+ * zero; all calls share the array, so calls whose GPU work overlaps (other
+ * threads, other streams) race and must be serialised by the caller.  The
+ * call synchronises `stream` and returns the device status. */
+hg_status hg_segmented_sort_noalloc(const uint32_t* d_seg_off, int n_seg, int64_t n_pairs,
+                                    const uint32_t* d_keys_in, const uint32_t* d_vals_in,
+                                    uint32_t* d_keys_out, uint32_t* d_vals_out, void* stream);
+
 /* Kernel launches issued by the library so far (all contexts). */
 int64_t hg_kernel_launches(void);
 

@@ -9,6 +9,10 @@
 //     running), preceded by one histogram kernel for all four digits.
 // The fill pass writes a segment in a data-dependent order, so runs of equal
 // keys are re-sorted by id at the end (the id tie-break).
+#include <mutex>
+#include <string>
+
+#include "internal.h"
 #include "kernels.cuh"
 #include "radix.cuh"
 
@@ -373,6 +377,148 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
   k_os_fixup<<<num_sms() * 4, 256, 0, st>>>(tv, a.keys, a.vals, a.fc);
   note_launch();
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Segmented sort with no allocation, for callers that cannot allocate
+// device memory at the call site (for example code running inside another
+// allocator's callback, or a host that must not touch the device heap while
+// other work is being captured or served).  All scratch lives in one
+// file-scope device array of fixed size that every GPU which loads this
+// library keeps until the process exits.
+namespace {
+
+constexpr uint32_t NA_MAX_PAIRS = 1u << 19;                         // 524,288 pairs
+constexpr uint32_t NA_MAX_SEGS = 512;
+constexpr uint32_t NA_MAX_TILES = NA_MAX_PAIRS / OS_TILE + NA_MAX_SEGS;
+constexpr size_t NA_FC_WORDS = 64;
+constexpr size_t NA_TILE_WORDS = (size_t)NA_MAX_TILES * 4;
+constexpr size_t NA_SEGS_WORDS = (size_t)NA_MAX_SEGS * 2;
+constexpr size_t NA_HIST_WORDS = (size_t)NA_MAX_SEGS * 4 * 256;
+constexpr size_t NA_LB_WORDS = (size_t)NA_MAX_TILES * 256;
+constexpr size_t NA_PP_WORDS = (size_t)NA_MAX_PAIRS * 2;
+constexpr size_t NA_WORDS = NA_FC_WORDS + NA_TILE_WORDS + NA_SEGS_WORDS + NA_HIST_WORDS + NA_LB_WORDS + NA_PP_WORDS;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
+
+static_assert(sizeof(FrameCounters) <= NA_FC_WORDS * 4, "counter block too small");
+
+// One CTA: onesweep tile descriptors for every segment of >= 2 pairs (the
+// segment index doubles as the histogram index).
+__global__ void __launch_bounds__(1024) k_na_tiles(const uint32_t* seg_off, int n_seg, uint4* tiles,
+                                                   uint32_t* segs, uint32_t* tile_first, FrameCounters* fc) {
+  __shared__ uint32_t tmp[33];
+  const int tid = threadIdx.x;
+  const int s = tid;  // n_seg <= NA_MAX_SEGS <= 1024
+  uint32_t n = 0, nt = 0;
+  if (s < n_seg) {
+    n = seg_off[s + 1] - seg_off[s];
+    nt = n >= 2 ? (n + OS_TILE - 1) / OS_TILE : 0;
+  }
+  uint32_t total;
+  const uint32_t first = block_excl_scan(nt, tmp, &total);
+  if (s < n_seg) {
+    segs[s] = (uint32_t)s;
+    tile_first[s] = first;
+    for (uint32_t k = 0; k < nt; ++k)
+      tiles[first + k] = make_uint4((uint32_t)s, seg_off[s] + k * OS_TILE, min((uint32_t)OS_TILE, n - k * OS_TILE), k);
+  }
+  if (tid == 0) fc->n_big_tiles = total;
+}
+
+}  // namespace
+
+// Device address of the scratch array, looked up once per device.
+static void* noalloc_scratch(int dev, hg_status* st) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  *st = HG_OK;
+  if (dev < 0 || dev >= 64) {
+    *st = HG_ERR_INVALID_ARG;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      *st = hg_cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "hg_segmented_sort_noalloc set-up");
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+extern "C" hg_status hg_segmented_sort_noalloc(const uint32_t* d_seg_off, int n_seg, int64_t n_pairs,
+                                               const uint32_t* d_keys_in, const uint32_t* d_vals_in,
+                                               uint32_t* d_keys_out, uint32_t* d_vals_out, void* stream) {
+  if (n_seg < 1 || n_pairs < 0 || !d_seg_off || (n_pairs > 0 && (!d_keys_in || !d_vals_in || !d_keys_out ||
+                                                                  !d_vals_out))) {
+    hg_set_error("hg_segmented_sort_noalloc: bad arguments");
+    return HG_ERR_INVALID_ARG;
+  }
+  if ((uint64_t)n_pairs > NA_MAX_PAIRS || (uint32_t)n_seg > NA_MAX_SEGS) {
+    hg_set_error("hg_segmented_sort_noalloc: at most 524288 pairs in at most 512 segments (got " +
+                 std::to_string(n_pairs) + " pairs, " + std::to_string(n_seg) + " segments)");
+    return HG_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc");
+  hg_status st;
+  uint32_t* base = (uint32_t*)noalloc_scratch(dev, &st);
+  if (!base) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the segment table must be an ordered partition of [0, n_pairs)
+  uint32_t off[NA_MAX_SEGS + 1];
+  if ((e = cudaMemcpyAsync(off, d_seg_off, sizeof(uint32_t) * (n_seg + 1), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return hg_cuda_status(e, "hg_segmented_sort_noalloc seg_off");
+  if (off[0] != 0 || off[n_seg] != (uint32_t)n_pairs) {
+    hg_set_error("hg_segmented_sort_noalloc: seg_off must start at 0 and end at n_pairs");
+    return HG_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n_seg; ++i)
+    if (off[i + 1] < off[i]) {
+      hg_set_error("hg_segmented_sort_noalloc: seg_off is not non-decreasing");
+      return HG_ERR_INVALID_ARG;
+    }
+  if (n_pairs == 0) return HG_OK;
+  FrameCounters* fc = (FrameCounters*)base;
+  uint4* tiles = (uint4*)(base + NA_FC_WORDS);
+  uint32_t* segs = base + NA_FC_WORDS + NA_TILE_WORDS;
+  uint32_t* tile_first = segs + NA_MAX_SEGS;
+  uint32_t* hist = base + NA_FC_WORDS + NA_TILE_WORDS + NA_SEGS_WORDS;
+  uint32_t* lb = hist + NA_HIST_WORDS;
+  uint32_t* pp_k = lb + NA_LB_WORDS;
+  uint32_t* pp_v = pp_k + NA_MAX_PAIRS;
+  // the array keeps the previous call's contents: clear what starts at zero
+  if ((e = cudaMemsetAsync(fc, 0, NA_FC_WORDS * 4, s)) != cudaSuccess)
+    return hg_cuda_status(e, "hg_segmented_sort_noalloc clear");
+  if ((e = cudaMemcpyAsync(d_keys_out, d_keys_in, 4 * (size_t)n_pairs, cudaMemcpyDeviceToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(d_vals_out, d_vals_in, 4 * (size_t)n_pairs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return hg_cuda_status(e, "hg_segmented_sort_noalloc copy");
+  k_na_tiles<<<1, 1024, 0, s>>>(d_seg_off, n_seg, tiles, segs, tile_first, fc);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc tiles");
+  OsTileView tv{tiles, &fc->n_big_tiles, hist, d_seg_off, segs, tile_first};
+  bool alt = false;
+  e = launch_onesweep<uint32_t, 4>(tv, d_keys_out, d_vals_out, pp_k, pp_v, hist, NA_HIST_WORDS, lb, NA_LB_WORDS,
+                                   fc->os_claim, 0, 4, fc, s, &alt);
+  if (e != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc passes");
+  k_os_fixup<<<num_sms() * 4, 256, 0, s>>>(tv, d_keys_out, d_vals_out, fc);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc fixup");
+  int status = 0;
+  if ((e = cudaMemcpyAsync(&status, &fc->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return hg_cuda_status(e, "hg_segmented_sort_noalloc status");
+  if (status != HG_OK) hg_set_error(std::string("hg_segmented_sort_noalloc: device status ") +
+                                    hg_status_str((hg_status)status));
+  return (hg_status)status;
 }
 
 }  // namespace hg

@@ -27,7 +27,7 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",
            "hg_state_free", "hg_state_sync", "hg_render_stats", "hg_state_read", "hg_graph_create",
            "hg_graph_launch", "hg_graph_set_cameras", "hg_graph_sync", "hg_graph_kernels", "hg_graph_destroy",
-           "hg_kernel_launches"]
+           "hg_kernel_launches", "hg_segmented_sort_noalloc"]
 
 
 class HgError(RuntimeError):
@@ -103,6 +103,9 @@ def load(path: str = LIB_PATH):
     lib.hg_graph_kernels.restype = C.c_int64
     lib.hg_graph_destroy.argtypes = [C.c_void_p]
     lib.hg_kernel_launches.restype = C.c_int64
+    lib.hg_segmented_sort_noalloc.restype = C.c_int
+    lib.hg_segmented_sort_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p]
     lib.hg_ctx_create.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
     lib.hg_ctx_destroy.argtypes = [C.c_void_p]
     lib.hg_create_scene.argtypes = [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(C.c_void_p)]
@@ -315,6 +318,15 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def segmented_sort_noalloc(seg_off, keys, vals, keys_out, vals_out, stream=None) -> int:
+    """hg_segmented_sort_noalloc on device int32/uint32 tensors; returns the
+    hg_status (no exception) so callers can inspect rejections."""
+    return int(load().hg_segmented_sort_noalloc(C.c_void_p(seg_off.data_ptr()), int(seg_off.numel()) - 1,
+                                                int(keys.numel()), C.c_void_p(keys.data_ptr()),
+                                                C.c_void_p(vals.data_ptr()), C.c_void_p(keys_out.data_ptr()),
+                                                C.c_void_p(vals_out.data_ptr()), _stream_ptr(stream)))
 
 
 def kernel_launches() -> int:
