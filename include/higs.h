@@ -110,7 +110,11 @@ enum { HG_BIN_RECT = 0 };
 enum {
   HG_FLAG_ASYNC = 1,       /* do not synchronise or check the status word */
   HG_FLAG_TIMING = 2,      /* record per-stage CUDA events (hg_render_stats) */
-  HG_FLAG_KEEP_SPLATS = 4  /* also write hg_splat records (hg_state_read) */
+  HG_FLAG_KEEP_SPLATS = 4, /* also write hg_splat records (hg_state_read) */
+  HG_FLAG_INDEPENDENT = 8  /* render every batch independently from T = 1 and
+                              composite the partials by Eq. 1 with exact-termination
+                              replay (the paper's schedule) instead of chaining the
+                              batches of a macro-tile in depth order */
 };
 
 typedef struct {

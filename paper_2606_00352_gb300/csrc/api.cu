@@ -420,7 +420,10 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ENS(B_RANKC, sizeof(uint32_t) * (MAX_RANKS + 1));
     ENS(B_PARTIAL, sizeof(float4) * TILE_PX * M * s->cap_batches);
     ENS(B_ACTIVE, sizeof(unsigned long long) * s->cap_batches);
-    ENS(B_TILESAT, sizeof(uint32_t) * g.total_tiles);
+    ENS(B_CHAIN, sizeof(uint32_t) * g.S);
+    ENS(B_MODE, sizeof(uint32_t) * s->cap_batches);
+    ENS(B_TSTATE, sizeof(float4) * TILE_PX * (size_t)g.total_tiles);
+    ENS(B_TRANK, sizeof(uint32_t) * g.total_tiles);
     ENS(B_SEGHIST, sizeof(uint32_t) * 4 * 256 * s->cap_big_segs);
     ENS(B_LOOKBACK, sizeof(uint32_t) * 256 * s->cap_tiles);
     if (o->save_for_backward) {
@@ -481,7 +484,8 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     if (n > 0) HG_TRY(launch_sort(sa, st), "sort");
     if (timing) HG_TRY(record_stage(s->ev[3], st), "stage event 3");
 
-    HG_TRY(cudaMemsetAsync(s->bufs[B_TILESAT].p, 0xff, sizeof(uint32_t) * g.total_tiles, st), "memset tile_sat");
+    HG_TRY(cudaMemsetAsync(s->bufs[B_CHAIN].p, 0, sizeof(uint32_t) * g.S, st), "memset chain");
+    HG_TRY(cudaMemsetAsync(s->bufs[B_TRANK].p, 0, sizeof(uint32_t) * g.total_tiles, st), "memset tile rank");
     RasterArgs ra{};
     ra.rec = (const float4*)s->bufs[B_REC].p;
     ra.n = n;
@@ -498,9 +502,14 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.macro_h = o->macro_h;
     ra.partial = (float4*)s->bufs[B_PARTIAL].p;
     ra.active = (unsigned long long*)s->bufs[B_ACTIVE].p;
-    ra.tile_sat = (uint32_t*)s->bufs[B_TILESAT].p;
+    ra.chain = (uint32_t*)s->bufs[B_CHAIN].p;
+    ra.mode = (uint32_t*)s->bufs[B_MODE].p;
+    ra.tile_state = (float4*)s->bufs[B_TSTATE].p;
+    ra.tile_rank = (uint32_t*)s->bufs[B_TRANK].p;
     ra.stop_pos = o->save_for_backward ? (uint16_t*)s->bufs[B_STOPPOS].p : nullptr;
+    ra.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
     ra.persistent_ctas = 0;
+    ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");
     if (timing) HG_TRY(record_stage(s->ev[4], st), "stage event 4");
@@ -508,6 +517,9 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     MergeArgs ma{};
     ma.partial = ra.partial;
     ma.active = ra.active;
+    ma.mode = ra.mode;
+    ma.tile_state = ra.tile_state;
+    ma.tile_rank = ra.tile_rank;
     ma.first_batch = pa.first_batch;
     ma.batches = pa.batches;
     ma.vals = pa.vals;

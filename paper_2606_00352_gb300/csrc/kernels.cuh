@@ -91,17 +91,29 @@ struct RasterArgs {
   uint32_t cap_batches;
   int batch_cap;              // B_r
   int macro_w, macro_h;
-  float4* partial;            // [cap_batches][M][64] (r, g, b, +-T)
-  unsigned long long* active; // [cap_batches] tile bits
-  uint32_t* tile_sat;         // [total render tiles] first batch rank that saturated the tile (+1), 0 = none
-  uint16_t* stop_pos;         // optional [cap_batches][M][64]: local stop position (backward)
+  float4* partial;            // [cap_batches][M][64] (r, g, b, +-T) of batches rendered unchained
+  unsigned long long* active; // [cap_batches] tiles the batch blended
+  uint32_t* chain;            // [S] batches of the segment composited in order so far; bit 31: chain broken
+  uint32_t* mode;             // [cap_batches] BATCH_CHAINED or BATCH_LOCAL
+  float4* tile_state;         // [total tiles][64] (r, g, b, +-T) after the chained batches
+  uint32_t* tile_rank;        // [total tiles] rank + 1 of the last chained batch that blended the tile, 0 = none
+  uint16_t* stop_pos;         // optional [cap_batches][M][64]: stop position inside the batch (backward)
+  float4* prefix;             // optional [cap_batches][M][64]: (C, +-T) entering the batch (backward)
   int persistent_ctas;
+  int independent;            // never wait: every batch after the first renders from T = 1
   FrameCounters* fc;
 };
+
+constexpr uint32_t BATCH_CHAINED = 1;  // rendered from the exact transmittance entering it
+constexpr uint32_t BATCH_LOCAL = 2;    // rendered from T = 1; composited by the merge
+constexpr uint32_t CHAIN_BROKEN = 0x80000000u;
 
 struct MergeArgs {
   const float4* partial;
   const unsigned long long* active;
+  const uint32_t* mode;
+  const float4* tile_state;
+  const uint32_t* tile_rank;
   const uint32_t* first_batch;
   const uint4* batches;
   const uint32_t* vals;

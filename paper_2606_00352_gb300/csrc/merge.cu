@@ -3,8 +3,10 @@
 // C = C_0 + T_0 C_1 + T_0 T_1 C_2 + ..., reading a batch's partial only when
 // the batch's active-tile mask has the tile's bit.
 //
-// Exact per-pixel termination across batches: let T_acc be the transmittance
-// entering batch k.  If the pixel stopped inside batch k, or T_acc T_k < 1e-4,
+// Batches the rasteriser rendered in order (chained) already hold the exact
+// result in the per-tile state; the merge starts from it.  For batches
+// rendered from T = 1 (a broken chain), exact per-pixel termination across
+// batches: let T_acc be the transmittance entering batch k.  If the pixel stopped inside batch k, or T_acc T_k < 1e-4,
 // the 3DGS stop lies inside batch k; unless T_acc = 1 (then the local stop is
 // the global one) the warp replays batch k for that pixel from T_acc with the
 // same blend arithmetic as the rasteriser.
@@ -73,7 +75,20 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
     pixel_init(p1, in1);
     const uint32_t r0 = a.first_batch[seg], r1 = a.first_batch[seg + 1];
     const float4* rec_v = a.rec + (size_t)v * a.n * 3;
-    for (uint32_t r = r0; r < r1; ++r) {
+    // batches rendered in order from the exact entering transmittance: their
+    // result is the per-tile state
+    uint32_t g = r0;
+    while (g < r1 && a.mode[g] == BATCH_CHAINED) ++g;
+    if (g > r0 && a.tile_rank[tile] != 0) {
+      const float4 s0 = a.tile_state[(size_t)tile * TILE_PX + lane];
+      const float4 s1 = a.tile_state[(size_t)tile * TILE_PX + lane + 32];
+      p0.r = s0.x, p0.g = s0.y, p0.b = s0.z, p0.T = fabsf(s0.w), p0.stopped = signbit(s0.w);
+      p1.r = s1.x, p1.g = s1.y, p1.b = s1.z, p1.T = fabsf(s1.w), p1.stopped = signbit(s1.w);
+      p0.done = p0.done || p0.stopped;
+      p1.done = p1.done || p1.stopped;
+    }
+    // the rest (batches rendered from T = 1): Eq. 1 with replay
+    for (uint32_t r = g; r < r1; ++r) {
       if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
       if (!((a.active[r] >> tl) & 1ull)) continue;
       const float4* src = a.partial + ((size_t)r * M + tl) * TILE_PX;

@@ -6,15 +6,22 @@
 //   phase 1 each warp takes mini-batches of 32 gaussians, computes the
 //           gaussian's render-tile mask inside the macro-tile and transposes
 //           the 32 x M bit matrix with ballots (per-tile gaussian masks)
-//   queue   warp 0 ORs the masks per tile and compacts the active tiles;
-//           tiles that an earlier batch of the macro-tile already saturated
-//           are dropped (their pixels never composite this batch)
+//   queue   warp 0 ORs the masks per tile and compacts the active tiles
+//   chain   (exact termination) the unit of rank k waits, with a bounded
+//           spin, until rank k-1 of the same macro-tile has finished; it then
+//           blends from the exact transmittance entering the batch, read from
+//           the per-tile state, so pixels and tiles that already stopped cost
+//           nothing and no merge-time replay is needed.  Units are claimed
+//           rank-major, so the awaited unit was claimed earlier and is running
+//           or done.  If the wait gives up, the unit renders from T = 1 (an
+//           independent partial) and the merge composites it by Eq. 1 with
+//           replay.
 //   phase 2 warps claim tiles from the queue; a warp blends the tile's 64
 //           pixels (two per lane) front to back over the set mask bits, with
 //           a unanimous-vote early out when every pixel has stopped
-//   store   partial (r, g, b, +-T) per pixel with streaming stores (T is
-//           negated when the pixel stopped inside the batch) and the unit's
-//           active-tile mask
+//   store   chained: the new per-tile state; unchained: the partial
+//           (r, g, b, +-T) with streaming stores (T negated when the pixel
+//           stopped inside the batch)
 #include "blend.cuh"
 #include "kernels.cuh"
 
@@ -24,15 +31,12 @@ namespace {
 
 constexpr int RW = 8;  // warps per CTA
 constexpr int RT = RW * 32;
+constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
-template <int MW, int MH>
-struct RasterShape {
-  static constexpr int M = MW * MH;
-};
-
-__global__ void k_zero_u32(uint32_t* p, uint32_t v, size_t n) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 template <int MW, int MH>
@@ -42,9 +46,9 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   float4* s_rec = reinterpret_cast<float4*>(smem_raw);                       // [cap][3]
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);   // [cap/32][M]
   __shared__ uint64_t bar;
-  __shared__ uint32_t s_unit, s_qn, s_qhead;
+  __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
-  __shared__ unsigned long long s_active;
+  __shared__ unsigned long long s_active, s_blended;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -61,6 +65,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     if (tid == 0) {
       s_unit = atomicAdd(&a.fc->raster_claim, 1u);
       s_qhead = 0;
+      s_blended = 0;
     }
     __syncthreads();
     const uint32_t u = s_unit;
@@ -127,11 +132,6 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           uint32_t o = 0;
           for (int k = 0; k < K; ++k) o |= s_mask[k * M + t];
           hit = o != 0;
-          if (hit) {
-            const int gtx = mtx0 + t % MW, gty = mty0 + t / MW;
-            const uint32_t sat = a.tile_sat[V.tile_base + gty * V.tiles_x + gtx];
-            if (sat < rank) hit = false;  // an earlier batch stopped every pixel
-          }
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, hit);
         if (hit) s_q[qn + __popc(bal & lanemask_lt())] = (uint8_t)t;
@@ -143,9 +143,27 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         s_active = act;
       }
     }
+    // chain: wait for the previous batch of this macro-tile
+    if (tid == 0) {
+      uint32_t mode = BATCH_CHAINED;
+      if (rank > 0) {
+        mode = BATCH_LOCAL;
+        for (uint32_t it = 0; it < (a.independent ? 0u : CHAIN_SPIN); ++it) {
+          const uint32_t c = ld_acquire(&a.chain[seg]);
+          if (c == rank) {
+            mode = BATCH_CHAINED;
+            break;
+          }
+          if (c & CHAIN_BROKEN) break;
+          __nanosleep(256);
+        }
+      }
+      __threadfence();
+      s_mode = mode;
+    }
     __syncthreads();
-    if (tid == 0) a.active[r] = s_active;
     const uint32_t qn = s_qn;
+    const bool chained = s_mode == BATCH_CHAINED;
 
     // phase 2: warps claim tiles
     while (true) {
@@ -155,11 +173,31 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       if (qi >= qn) break;
       const int t = s_q[qi];
       const int gtx = mtx0 + t % MW, gty = mty0 + t / MW;
+      const int gt = V.tile_base + gty * V.tiles_x + gtx;
       const int px = gtx * TILE + (lane & 7);
       const int py = gty * TILE + (lane >> 3);
+      const bool in0 = px < V.W && py < V.H, in1 = px < V.W && py + 4 < V.H;
       PixelAcc p0, p1;
-      pixel_init(p0, px < V.W && py < V.H);
-      pixel_init(p1, px < V.W && py + 4 < V.H);
+      pixel_init(p0, in0);
+      pixel_init(p1, in1);
+      if (chained && __ldcg(&a.tile_rank[gt]) != 0) {
+        const float4 s0 = __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane]);
+        const float4 s1 = __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane + 32]);
+        p0.r = s0.x, p0.g = s0.y, p0.b = s0.z, p0.T = fabsf(s0.w);
+        p1.r = s1.x, p1.g = s1.y, p1.b = s1.z, p1.T = fabsf(s1.w);
+        p0.stopped = signbit(s0.w);
+        p1.stopped = signbit(s1.w);
+        p0.done = p0.done || p0.stopped;
+        p1.done = p1.done || p1.stopped;
+      }
+      // every pixel already stopped in an earlier batch: nothing to blend
+      if (__all_sync(0xffffffffu, p0.done && p1.done)) continue;
+      if (lane == 0) atomicOr(&s_blended, 1ull << t);
+      if (a.prefix) {
+        float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
+        pre[lane] = make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T);
+        pre[lane + 32] = make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T);
+      }
       uint32_t stop0 = count, stop1 = count;
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
       uint32_t n_blend = 0;
@@ -170,8 +208,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           m &= m - 1;
           const uint32_t j = (uint32_t)k * 32 + bit;
           const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
-          const float dx = fpx - g0.x;
-          const float ub = g0.z * dx;
+          const float ub = g0.z * (fpx - g0.x);
           if (blend_one(p0, ub, fpy - g0.y, g0, g1, g2)) stop0 = j;
           if (blend_one(p1, ub, fpy1 - g0.y, g0, g1, g2)) stop1 = j;
           ++n_blend;
@@ -182,21 +219,33 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         }
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
-      float4* out = a.partial + ((size_t)r * M + t) * TILE_PX;
-      st_cs(out + lane, make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T));
-      st_cs(out + lane + 32, make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T));
+      if (chained) {
+        float4* st = a.tile_state + (size_t)gt * TILE_PX;
+        st[lane] = make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T);
+        st[lane + 32] = make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T);
+        if (lane == 0) a.tile_rank[gt] = rank + 1;
+      } else {
+        float4* out = a.partial + ((size_t)r * M + t) * TILE_PX;
+        st_cs(out + lane, make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T));
+        st_cs(out + lane + 32, make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T));
+      }
       if (a.stop_pos) {
         uint16_t* sp = a.stop_pos + ((size_t)r * M + t) * TILE_PX;
         sp[lane] = (uint16_t)stop0;
         sp[lane + 32] = (uint16_t)stop1;
       }
-      // every in-image pixel stopped inside this batch: later batches skip the tile
-      const bool sat0 = p0.stopped || !(px < V.W && py < V.H);
-      const bool sat1 = p1.stopped || !(px < V.W && py + 4 < V.H);
-      if (__all_sync(0xffffffffu, sat0 && sat1) && lane == 0)
-        atomicMin(&a.tile_sat[V.tile_base + gty * V.tiles_x + gtx], rank);
     }
+    // publish: the tile states are visible before the chain advances
+    __threadfence();
     __syncthreads();
+    if (tid == 0) {
+      a.active[r] = chained ? s_blended : s_active;
+      a.mode[r] = chained ? BATCH_CHAINED : BATCH_LOCAL;
+      if (chained)
+        atomicCAS(&a.chain[seg], rank, rank + 1);
+      else
+        atomicOr(&a.chain[seg], CHAIN_BROKEN);
+    }
   }
   if (lane == 0 && evals) atomicAdd(&a.fc->raster_evals, evals);
 }

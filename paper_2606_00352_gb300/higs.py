@@ -20,7 +20,7 @@ HG_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "capacity",
           -5: "device timeout", -6: "busy", -7: "not found", -8: "cancelled", -9: "unsupported"}
 PATH_HIGS, PATH_PLAIN = 0, 1
-FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS = 1, 2, 4
+FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT = 1, 2, 4, 8
 BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE = range(6)
 
 EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",

@@ -167,20 +167,23 @@ def test_image_tiny(lib, ctx, path):
     compare_image(imgs[0], ts[0], ref)
 
 
+@pytest.mark.parametrize("independent", [False, True])
 @pytest.mark.parametrize("macro,cap", [((8, 4), 32), ((4, 4), 64), ((8, 8), 256), ((8, 4), 2048)])
-def test_image_invariant_to_macro_shape_and_cap(lib, ctx, macro, cap):
-    """Small caps force many batches per macro-tile and exercise the
-    exact-termination replay of the merge."""
+def test_image_invariant_to_macro_shape_and_cap(lib, ctx, macro, cap, independent):
+    """Small caps force many batches per macro-tile.  Chained batches render
+    from the exact entering transmittance; independent batches exercise the
+    Eq. 1 merge with exact-termination replay."""
     scene = scenes.uniform_scene(30_000, seed=2)
     scene.log_scales += np.float32(0.7)
     cam = scenes.look_at((3, 0, 0), width=192, height=136)
     gs = lib.GpuScene.from_scene(ctx, scene)
     st = lib.State(ctx)
-    imgs, ts = render_np(lib, gs, [cam], macro_w=macro[0], macro_h=macro[1], batch_cap=cap, state=st)
+    imgs, ts = render_np(lib, gs, [cam], macro_w=macro[0], macro_h=macro[1], batch_cap=cap, state=st,
+                         flags=lib.FLAG_INDEPENDENT if independent else 0)
     ref = C.render(P.project(scene, cam))
     compare_image(imgs[0], ts[0], ref)
     if cap <= 64:
-        assert st.stats()["n_replays"] > 0
+        assert (st.stats()["n_replays"] > 0) == independent
 
 
 def test_image_background_and_multiview(lib, ctx):
