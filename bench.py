@@ -368,6 +368,27 @@ def gpu_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Small case for kernel captures: the 1M-gaussian SH-3 scene, 4 views
+    at 1080p, rendered `--steps` times through hg_render (no graph)."""
+    import torch
+    from paper_2606_00352_gb300 import higs, scenes
+    higs.load()
+    torch.cuda.set_device(0)
+    scene = scenes.scene_1m()
+    cams = scenes.scene_orbit(32, WIDTH, HEIGHT)
+    ctx = higs.Context(0)
+    gs = higs.GpuScene.from_scene(ctx, scene)
+    st = higs.State(ctx)
+    path = higs.PATH_PLAIN if args.case == "1m-plain" else higs.PATH_HIGS
+    opts = higs.Options(path=path, flags=higs.FLAG_TIMING)
+    for k in range(args.warmup + args.steps):
+        higs.render(gs, pose_batch(cams, k, 0), opts, state=st)
+    torch.cuda.synchronize()
+    s = st.stats()
+    print(json.dumps({"case": args.case, "stats": s}), flush=True)
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -393,8 +414,10 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--case", default="", choices=["", "1m", "1m-plain"],
+                    help="small profiling case instead of the benchmark")
     args = ap.parse_args()
-    if args.warmup < 3 and not args.oracle_steps:
+    if args.warmup < 3 and not args.oracle_steps and not args.case:
         args.warmup = 3
     if args.oracle_steps:
         times = oracle_sample_steps(args.oracle_steps, args.warmup)
@@ -402,7 +425,9 @@ def main():
         print(json.dumps({"value": 1.0 / (statistics.mean(times) * ORACLE_FRACTION), "ms_per_step": ms,
                           "times": times}))
         return
-    if args.impl == "reference":
+    if args.case:
+        profile_case(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)
