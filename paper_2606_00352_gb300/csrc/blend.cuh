@@ -53,6 +53,28 @@ __device__ __forceinline__ bool blend_one(PixelAcc& p, float ubase, float dy, co
   return false;
 }
 
+// Branch-free form of blend_one with the same arithmetic (so every kernel
+// that blends the same gaussian at the same pixel gets the same bits).
+__device__ __forceinline__ bool blend_bf(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
+                                         const float4& g2) {
+  const float u = fmaf(g0.w, dy, ubase);
+  const float w = g1.x * dy;
+  const float e = fmaf(u, u, w * w);
+  const float al = fminf(ALPHA_MAX, g1.y * ex2_approx(-e));
+  const bool ok = !p.done && (e <= SUPPORT_E) && (al >= ALPHA_MIN);
+  const float tn = p.T * (1.f - al);
+  const bool stop = ok && (tn < T_EPS);
+  const bool contrib = ok && !stop;
+  const float wt = contrib ? al * p.T : 0.f;
+  p.r = fmaf(g2.x, wt, p.r);
+  p.g = fmaf(g2.y, wt, p.g);
+  p.b = fmaf(g2.z, wt, p.b);
+  p.T = contrib ? tn : p.T;
+  p.done = p.done || stop;
+  p.stopped = p.stopped || stop;
+  return stop;
+}
+
 // Conservative test of a gaussian's 3-sigma rectangle against render tile
 // (tx, ty) (same integer rule as the macro binning, at 8x8 granularity).
 __device__ __forceinline__ void tile_rect(const float4& g0, const float4& g1, int& x0, int& x1, int& y0, int& y1) {

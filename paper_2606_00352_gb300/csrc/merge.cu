@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
           bal &= bal - 1;
           const float4 h0 = shfl4(g0, b), h1 = shfl4(g1, b), h2 = shfl4(g2, b);
           const float ub = h0.z * (fpx - h0.x);
-          blend_one(q0r, ub, fpy - h0.y, h0, h1, h2);
-          blend_one(q1r, ub, fpy1 - h0.y, h0, h1, h2);
+          blend_bf(q0r, ub, fpy - h0.y, h0, h1, h2);
+          blend_bf(q1r, ub, fpy1 - h0.y, h0, h1, h2);
         }
       }
       if (need0) {

@@ -153,9 +153,9 @@ __global__ void __launch_bounds__(TILE_PX) k_plain_raster(PlainArgs a, const uin
     }
     __syncthreads();
     const int nb = (int)min((uint32_t)TILE_PX, rg.y - base);
-    for (int k = 0; k < nb && !p.done; ++k) {
+    for (int k = 0; k < nb; ++k) {
       const float4 g0 = s_rec[k * 3 + 0], g1 = s_rec[k * 3 + 1], g2 = s_rec[k * 3 + 2];
-      blend_one(p, g0.z * (fpx - g0.x), fpy - g0.y, g0, g1, g2);
+      blend_bf(p, g0.z * (fpx - g0.x), fpy - g0.y, g0, g1, g2);
     }
   }
   if (inside) {

@@ -39,7 +39,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   return v;
 }
 
-template <int MW, int MH>
+template <int MW, int MH, bool SAVE>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
+  __shared__ uint8_t s_list[RW * 32];
   __shared__ unsigned long long s_active, s_blended;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       // every pixel already stopped in an earlier batch: nothing to blend
       if (__all_sync(0xffffffffu, p0.done && p1.done)) continue;
       if (lane == 0) atomicOr(&s_blended, 1ull << t);
-      if (a.prefix) {
+      if (SAVE) {
         float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
         pre[lane] = make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T);
         pre[lane + 32] = make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T);
@@ -201,22 +202,34 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       uint32_t stop0 = count, stop1 = count;
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
       uint32_t n_blend = 0;
+      uint8_t* list = s_list + warp * 32;
       for (int k = 0; k < K; ++k) {
-        uint32_t m = s_mask[k * M + t];
-        while (m) {
-          const int bit = __ffs(m) - 1;
-          m &= m - 1;
-          const uint32_t j = (uint32_t)k * 32 + bit;
+        const uint32_t m = s_mask[k * M + t];
+        if (!m) continue;
+        // compact the mini-batch's set bits into the warp's index list
+        if ((m >> lane) & 1u) list[__popc(m & lanemask_lt())] = (uint8_t)lane;
+        __syncwarp();
+        const int nk = __popc(m);
+        bool all_done = false;
+        for (int i = 0; i < nk; ++i) {
+          const uint32_t j = (uint32_t)k * 32 + list[i];
           const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
           const float ub = g0.z * (fpx - g0.x);
-          if (blend_one(p0, ub, fpy - g0.y, g0, g1, g2)) stop0 = j;
-          if (blend_one(p1, ub, fpy1 - g0.y, g0, g1, g2)) stop1 = j;
-          ++n_blend;
-          if (__all_sync(0xffffffffu, p0.done && p1.done)) {
-            m = 0;
-            k = K;
+          const bool st0 = blend_bf(p0, ub, fpy - g0.y, g0, g1, g2);
+          const bool st1 = blend_bf(p1, ub, fpy1 - g0.y, g0, g1, g2);
+          if (SAVE) {
+            stop0 = st0 ? j : stop0;
+            stop1 = st1 ? j : stop1;
+          }
+          if ((i & 7) == 7 && __all_sync(0xffffffffu, p0.done && p1.done)) {
+            all_done = true;
+            n_blend += i + 1;
+            break;
           }
         }
+        if (!all_done) n_blend += nk;
+        __syncwarp();
+        if (all_done || __all_sync(0xffffffffu, p0.done && p1.done)) break;
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
       if (chained) {
@@ -229,7 +242,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         st_cs(out + lane, make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T));
         st_cs(out + lane + 32, make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T));
       }
-      if (a.stop_pos) {
+      if (SAVE) {
         uint16_t* sp = a.stop_pos + ((size_t)r * M + t) * TILE_PX;
         sp[lane] = (uint16_t)stop0;
         sp[lane + 32] = (uint16_t)stop1;
@@ -250,21 +263,28 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   if (lane == 0 && evals) atomicAdd(&a.fc->raster_evals, evals);
 }
 
-template <int MW, int MH>
-cudaError_t launch_raster_shape(const RasterArgs& a, int cap, cudaStream_t st) {
+template <int MW, int MH, bool SAVE>
+cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) {
   constexpr int M = MW * MH;
   const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_raster<MW, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_raster<MW, MH, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1, dev = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raster<MW, MH>, RT, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raster<MW, MH, SAVE>, RT, sm);
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (occ < 1) occ = 1;
   const int grid = a.persistent_ctas > 0 ? a.persistent_ctas : sms * occ;
-  k_raster<MW, MH><<<grid, RT, sm, st>>>(a, cap);
+  k_raster<MW, MH, SAVE><<<grid, RT, sm, st>>>(a, cap);
   note_launch();
   return cudaGetLastError();
+}
+
+template <int MW, int MH>
+cudaError_t launch_raster_shape(const RasterArgs& a, int cap, cudaStream_t st) {
+  return (a.stop_pos || a.prefix) ? launch_raster_kernel<MW, MH, true>(a, cap, st)
+                                  : launch_raster_kernel<MW, MH, false>(a, cap, st);
 }
 
 }  // namespace
