@@ -375,13 +375,13 @@ def profile_case(args):
     from paper_2606_00352_gb300 import higs, scenes
     higs.load()
     torch.cuda.set_device(0)
-    scene = scenes.scene_1m()
-    cams = scenes.scene_orbit(32, WIDTH, HEIGHT)
+    scene = scenes.scene_5m8() if args.case == "5m8" else scenes.scene_1m()
+    cams = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)
     ctx = higs.Context(0)
     gs = higs.GpuScene.from_scene(ctx, scene)
     st = higs.State(ctx)
     path = higs.PATH_PLAIN if args.case == "1m-plain" else higs.PATH_HIGS
-    opts = higs.Options(path=path, flags=higs.FLAG_TIMING)
+    opts = higs.Options(path=path, flags=higs.FLAG_TIMING | (higs.FLAG_PROFILE if args.profile else 0))
     for k in range(args.warmup + args.steps):
         higs.render(gs, pose_batch(cams, k, 0), opts, state=st)
     torch.cuda.synchronize()
@@ -414,8 +414,9 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--case", default="", choices=["", "1m", "1m-plain"],
+    ap.add_argument("--case", default="", choices=["", "1m", "1m-plain", "5m8"],
                     help="small profiling case instead of the benchmark")
+    ap.add_argument("--profile", action="store_true", help="count rasteriser phase cycles (profiling case)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.oracle_steps and not args.case:
         args.warmup = 3

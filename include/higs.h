@@ -111,10 +111,11 @@ enum {
   HG_FLAG_ASYNC = 1,       /* do not synchronise or check the status word */
   HG_FLAG_TIMING = 2,      /* record per-stage CUDA events (hg_render_stats) */
   HG_FLAG_KEEP_SPLATS = 4, /* also write hg_splat records (hg_state_read) */
-  HG_FLAG_INDEPENDENT = 8  /* render every batch independently from T = 1 and
+  HG_FLAG_INDEPENDENT = 8, /* render every batch independently from T = 1 and
                               composite the partials by Eq. 1 with exact-termination
                               replay (the paper's schedule) instead of chaining the
                               batches of a macro-tile in depth order */
+  HG_FLAG_PROFILE = 16     /* count rasteriser phase cycles (hg_frame_stats) */
 };
 
 typedef struct {
@@ -142,6 +143,10 @@ typedef struct {
   int32_t status;         /* device status word (hg_status) */
   int32_t pad;
   float ms_project, ms_partition, ms_sort, ms_raster, ms_merge, ms_total;
+  /* with HG_FLAG_PROFILE: SM clock cycles summed over processing units of
+   * [0] record gather, [1] tile masks + queue, [2] chain wait, and over warps
+   * of [3] tile blending, [4] end-of-unit barrier; [5] units */
+  int64_t raster_cycles[6];
 } hg_frame_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -510,6 +510,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
     ra.persistent_ctas = 0;
     ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;
+    ra.profile = (o->flags & HG_FLAG_PROFILE) ? 1 : 0;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");
     if (timing) HG_TRY(record_stage(s->ev[4], st), "stage event 4");
@@ -660,6 +661,7 @@ extern "C" hg_status hg_render_stats(hg_state* s, hg_frame_stats* out) {
   out->n_replays = (int64_t)f.replays;
   out->raster_evals = (int64_t)f.raster_evals;
   out->status = f.status;
+  for (int k = 0; k < 6; ++k) out->raster_cycles[k] = (int64_t)f.raster_cycles[k];
   if (s->opts.flags & HG_FLAG_TIMING) {
     float ms[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&ms[k], s->ev[k], s->ev[k + 1]);

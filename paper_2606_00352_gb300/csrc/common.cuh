@@ -54,6 +54,9 @@ struct FrameCounters {
   uint32_t pad0;
   unsigned long long replays;
   unsigned long long raster_evals;
+  // rasteriser phase cycles summed over units (HG_FLAG_PROFILE): load, masks,
+  // chain wait, blend (per warp, summed), end barrier (per warp, summed), units
+  unsigned long long raster_cycles[6];
 };
 
 __device__ __forceinline__ void set_status(FrameCounters* fc, int code) {

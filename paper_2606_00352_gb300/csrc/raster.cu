@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     const int mloc = (int)seg - V.seg_base;
     const int mtx0 = (mloc % V.mgx) * MW, mty0 = (mloc / V.mgx) * MH;  // macro origin (tiles)
     const float4* rec_v = a.rec + (size_t)v * a.n * 3;
+    long long t_start = a.profile ? clock64() : 0;
 
     // gather the batch records: one bulk copy of 48 bytes per gaussian
     if (tid == 0) mbar_arrive_expect_tx(&bar, count * 48u);
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       return;
     }
     phase ^= 1u;
+    long long t_loaded = a.profile ? clock64() : 0;
 
     // phase 1: per-gaussian tile masks, transposed to per-tile masks
     const int K = (int)((count + 31) / 32);
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     }
     // chain: wait for the previous batch of this macro-tile
     if (tid == 0) {
+      const long long t_masks = a.profile ? clock64() : 0;
       uint32_t mode = BATCH_CHAINED;
       if (rank > 0) {
         mode = BATCH_LOCAL;
@@ -161,8 +164,16 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       }
       __threadfence();
       s_mode = mode;
+      if (a.profile) {
+        const long long t_chain = clock64();
+        atomicAdd(&a.fc->raster_cycles[0], (unsigned long long)(t_loaded - t_start));
+        atomicAdd(&a.fc->raster_cycles[1], (unsigned long long)(t_masks - t_loaded));
+        atomicAdd(&a.fc->raster_cycles[2], (unsigned long long)(t_chain - t_masks));
+        atomicAdd(&a.fc->raster_cycles[5], 1ull);
+      }
     }
     __syncthreads();
+    const long long t_p2 = a.profile ? clock64() : 0;
     const uint32_t qn = s_qn;
     const bool chained = s_mode == BATCH_CHAINED;
 
@@ -250,7 +261,13 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     }
     // publish: the tile states are visible before the chain advances
     __threadfence();
+    long long t_warp_done = a.profile ? clock64() : 0;
     __syncthreads();
+    if (a.profile && lane == 0) {
+      const long long t_end = clock64();
+      atomicAdd(&a.fc->raster_cycles[3], (unsigned long long)(t_warp_done - t_p2));
+      atomicAdd(&a.fc->raster_cycles[4], (unsigned long long)(t_end - t_warp_done));
+    }
     if (tid == 0) {
       a.active[r] = chained ? s_blended : s_active;
       a.mode[r] = chained ? BATCH_CHAINED : BATCH_LOCAL;

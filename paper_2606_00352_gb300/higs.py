@@ -20,7 +20,7 @@ HG_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "capacity",
           -5: "device timeout", -6: "busy", -7: "not found", -8: "cancelled", -9: "unsupported"}
 PATH_HIGS, PATH_PLAIN = 0, 1
-FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT = 1, 2, 4, 8
+FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT, FLAG_PROFILE = 1, 2, 4, 8, 16
 BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE = range(6)
 
 EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",
@@ -60,11 +60,12 @@ class FrameStats(C.Structure):
                 ("n_replays", C.c_int64), ("raster_evals", C.c_int64), ("status", C.c_int32),
                 ("pad", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
                 ("ms_sort", C.c_float), ("ms_raster", C.c_float), ("ms_merge", C.c_float),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("raster_cycles", C.c_int64 * 6)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "seg_by_tier")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "seg_by_tier", "raster_cycles")}
         d["seg_by_tier"] = list(self.seg_by_tier)
+        d["raster_cycles"] = list(self.raster_cycles)
         return d
 
 
