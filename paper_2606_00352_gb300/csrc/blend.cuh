@@ -75,6 +75,34 @@ __device__ __forceinline__ bool blend_bf(PixelAcc& p, float ubase, float dy, con
   return stop;
 }
 
+// blend_bf split in two: the alpha of a gaussian at a pixel does not depend
+// on the pixel's transmittance, so several gaussians' alphas can be computed
+// independently (instruction-level parallelism) before the ordered updates.
+// Together they perform exactly the operations of blend_bf.
+__device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g0, const float4& g1, bool& ok) {
+  const float u = fmaf(g0.w, dy, ubase);
+  const float w = g1.x * dy;
+  const float e = fmaf(u, u, w * w);
+  const float al = fminf(ALPHA_MAX, g1.y * ex2_approx(-e));
+  ok = (e <= SUPPORT_E) && (al >= ALPHA_MIN);
+  return al;
+}
+
+__device__ __forceinline__ bool apply_alpha(PixelAcc& p, float al, bool ok_in, const float4& g2) {
+  const bool ok = !p.done && ok_in;
+  const float tn = p.T * (1.f - al);
+  const bool stop = ok && (tn < T_EPS);
+  const bool contrib = ok && !stop;
+  const float wt = contrib ? al * p.T : 0.f;
+  p.r = fmaf(g2.x, wt, p.r);
+  p.g = fmaf(g2.y, wt, p.g);
+  p.b = fmaf(g2.z, wt, p.b);
+  p.T = contrib ? tn : p.T;
+  p.done = p.done || stop;
+  p.stopped = p.stopped || stop;
+  return stop;
+}
+
 // Conservative test of a gaussian's 3-sigma rectangle against render tile
 // (tx, ty) (same integer rule as the macro binning, at 8x8 granularity).
 __device__ __forceinline__ void tile_rect(const float4& g0, const float4& g1, int& x0, int& x1, int& y0, int& y1) {

@@ -30,6 +30,7 @@ namespace hg {
 namespace {
 
 constexpr int RW = 8;  // warps per CTA
+constexpr int UNROLL = 4;  // gaussians whose alphas are computed together
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
@@ -222,19 +223,36 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         __syncwarp();
         const int nk = __popc(m);
         bool all_done = false;
-        for (int i = 0; i < nk; ++i) {
-          const uint32_t j = (uint32_t)k * 32 + list[i];
-          const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
-          const float ub = g0.z * (fpx - g0.x);
-          const bool st0 = blend_bf(p0, ub, fpy - g0.y, g0, g1, g2);
-          const bool st1 = blend_bf(p1, ub, fpy1 - g0.y, g0, g1, g2);
-          if (SAVE) {
-            stop0 = st0 ? j : stop0;
-            stop1 = st1 ? j : stop1;
+        for (int i = 0; i < nk; i += UNROLL) {
+          float a0[UNROLL], a1[UNROLL];
+          bool k0[UNROLL], k1[UNROLL];
+          float4 c[UNROLL];
+          uint32_t jj[UNROLL];
+#pragma unroll
+          for (int q = 0; q < UNROLL; ++q) {
+            const bool valid = i + q < nk;
+            const uint32_t j = (uint32_t)k * 32 + list[valid ? i + q : i];
+            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1];
+            c[q] = s_rec[j * 3 + 2];
+            jj[q] = j;
+            const float ub = g0.z * (fpx - g0.x);
+            a0[q] = alpha_of(ub, fpy - g0.y, g0, g1, k0[q]);
+            a1[q] = alpha_of(ub, fpy1 - g0.y, g0, g1, k1[q]);
+            k0[q] = k0[q] && valid;
+            k1[q] = k1[q] && valid;
           }
-          if ((i & 7) == 7 && __all_sync(0xffffffffu, p0.done && p1.done)) {
+#pragma unroll
+          for (int q = 0; q < UNROLL; ++q) {
+            const bool st0 = apply_alpha(p0, a0[q], k0[q], c[q]);
+            const bool st1 = apply_alpha(p1, a1[q], k1[q], c[q]);
+            if (SAVE) {
+              stop0 = st0 ? jj[q] : stop0;
+              stop1 = st1 ? jj[q] : stop1;
+            }
+          }
+          if ((i & 7) == 4 && i + UNROLL < nk && __all_sync(0xffffffffu, p0.done && p1.done)) {
             all_done = true;
-            n_blend += i + 1;
+            n_blend += i + UNROLL;
             break;
           }
         }
