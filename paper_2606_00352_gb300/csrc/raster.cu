@@ -30,7 +30,9 @@ namespace hg {
 namespace {
 
 constexpr int RW = 8;  // warps per CTA
-constexpr int UNROLL = 4;  // gaussians whose alphas are computed together
+constexpr int UNROLL = 4;    // gaussians whose alphas are computed together
+constexpr int DRAIN = 32;    // gaussians blended per drain of the scheduling buffer
+constexpr uint32_t RING = 64;  // scheduling buffer capacity per warp (2 x DRAIN)
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
-  __shared__ uint8_t s_list[RW * 32];
+  __shared__ uint16_t s_ring[RW * RING];
   __shared__ unsigned long long s_active, s_blended;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -214,51 +216,61 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       uint32_t stop0 = count, stop1 = count;
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
       uint32_t n_blend = 0;
-      uint8_t* list = s_list + warp * 32;
-      for (int k = 0; k < K; ++k) {
+      // scheduling buffer (Alg. 2): indices of the tile's gaussians from
+      // successive mini-batches accumulate in a per-warp ring and are
+      // drained DRAIN at a time, UNROLL gaussians per step
+      uint16_t* ring = s_ring + warp * RING;
+      uint32_t head = 0, tail = 0;
+      bool all_done = false;
+      for (int k = 0; k < K && !all_done; ++k) {
         const uint32_t m = s_mask[k * M + t];
-        if (!m) continue;
-        // compact the mini-batch's set bits into the warp's index list
-        if ((m >> lane) & 1u) list[__popc(m & lanemask_lt())] = (uint8_t)lane;
-        __syncwarp();
-        const int nk = __popc(m);
-        bool all_done = false;
-        for (int i = 0; i < nk; i += UNROLL) {
-          float a0[UNROLL], a1[UNROLL];
-          bool k0[UNROLL], k1[UNROLL];
-          float4 c[UNROLL];
-          uint32_t jj[UNROLL];
+        if (m) {
+          if ((m >> lane) & 1u) ring[(tail + __popc(m & lanemask_lt())) & (RING - 1)] = (uint16_t)(k * 32 + lane);
+          tail += __popc(m);
+          __syncwarp();
+        }
+        while (tail - head >= DRAIN || (k == K - 1 && tail > head)) {
+          const uint32_t n = min(tail - head, (uint32_t)DRAIN);
+          for (uint32_t i = 0; i < n; i += UNROLL) {
+            float a0[UNROLL], a1[UNROLL];
+            bool k0[UNROLL], k1[UNROLL];
+            float4 c[UNROLL];
+            uint32_t jj[UNROLL];
 #pragma unroll
-          for (int q = 0; q < UNROLL; ++q) {
-            const bool valid = i + q < nk;
-            const uint32_t j = (uint32_t)k * 32 + list[valid ? i + q : i];
-            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1];
-            c[q] = s_rec[j * 3 + 2];
-            jj[q] = j;
-            const float ub = g0.z * (fpx - g0.x);
-            a0[q] = alpha_of(ub, fpy - g0.y, g0, g1, k0[q]);
-            a1[q] = alpha_of(ub, fpy1 - g0.y, g0, g1, k1[q]);
-            k0[q] = k0[q] && valid;
-            k1[q] = k1[q] && valid;
-          }
+            for (int q = 0; q < UNROLL; ++q) {
+              const bool valid = i + q < n;
+              const uint32_t j = ring[(head + (valid ? i + q : i)) & (RING - 1)];
+              const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1];
+              c[q] = s_rec[j * 3 + 2];
+              jj[q] = j;
+              const float ub = g0.z * (fpx - g0.x);
+              a0[q] = alpha_of(ub, fpy - g0.y, g0, g1, k0[q]);
+              a1[q] = alpha_of(ub, fpy1 - g0.y, g0, g1, k1[q]);
+              k0[q] = k0[q] && valid;
+              k1[q] = k1[q] && valid;
+            }
 #pragma unroll
-          for (int q = 0; q < UNROLL; ++q) {
-            const bool st0 = apply_alpha(p0, a0[q], k0[q], c[q]);
-            const bool st1 = apply_alpha(p1, a1[q], k1[q], c[q]);
-            if (SAVE) {
-              stop0 = st0 ? jj[q] : stop0;
-              stop1 = st1 ? jj[q] : stop1;
+            for (int q = 0; q < UNROLL; ++q) {
+              const bool st0 = apply_alpha(p0, a0[q], k0[q], c[q]);
+              const bool st1 = apply_alpha(p1, a1[q], k1[q], c[q]);
+              if (SAVE) {
+                stop0 = st0 ? jj[q] : stop0;
+                stop1 = st1 ? jj[q] : stop1;
+              }
+            }
+            n_blend += min((uint32_t)UNROLL, n - i);
+            if ((i & 7) == 4 && __all_sync(0xffffffffu, p0.done && p1.done)) {
+              all_done = true;
+              break;
             }
           }
-          if ((i & 7) == 4 && i + UNROLL < nk && __all_sync(0xffffffffu, p0.done && p1.done)) {
+          head += n;
+          __syncwarp();
+          if (all_done || __all_sync(0xffffffffu, p0.done && p1.done)) {
             all_done = true;
-            n_blend += i + UNROLL;
             break;
           }
         }
-        if (!all_done) n_blend += nk;
-        __syncwarp();
-        if (all_done || __all_sync(0xffffffffu, p0.done && p1.done)) break;
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
       if (chained) {
