@@ -103,6 +103,46 @@ __device__ __forceinline__ bool apply_alpha(PixelAcc& p, float al, bool ok_in, c
   return stop;
 }
 
+// Largest prescaled q a pixel can have and still pass the blend test:
+// alpha >= 1/255 needs o 2^-e >= 1/255, i.e. e <= log2(255 o), and the
+// support is e <= SUPPORT_E.  Slightly enlarged so that float32 rounding in
+// the blend can never pass a pixel this level excludes; negative = nothing.
+__device__ __forceinline__ float support_level(float o) {
+  if (!(o >= ALPHA_MIN)) return -1.f;
+  const float lv = fminf(SUPPORT_E, log2f(255.f * o));
+  return lv * 1.0001f + 1e-4f;
+}
+
+// x-range (pixel-centre coordinates) covered by the ellipse
+// (l0 dx + l1 dy)^2 + (l2 dy)^2 <= E over the rows y in [ya, yb]; false if
+// the rows miss it.  The left edge -(l1 dy + s(dy)) / l0 is convex in dy and
+// the right edge concave, so their extremes lie at the band's ends or at the
+// ellipse's leftmost / rightmost points.  Widened by 0.01 px.
+__device__ __forceinline__ bool ellipse_row_span(const float4& g0, const float4& g1, float E, float ya, float yb,
+                                                 float& xl, float& xr) {
+  const float l0 = g0.z, l1 = g0.w, l2 = g1.x;
+  if (!(l0 > 0.f) || !(l2 > 0.f)) {  // degenerate factors: keep the whole band
+    xl = -1e6f;
+    xr = 1e6f;
+    return true;
+  }
+  const float sE = sqrtf(E);
+  const float hy = sE / l2;
+  const float a = fmaxf(ya - g0.y, -hy), b = fminf(yb - g0.y, hy);
+  if (a > b) return false;
+  const float il0 = 1.f / l0;
+  const float nrm = sqrtf(fmaf(l1, l1, l2 * l2));
+  const float dyl = l1 * sE / (l2 * nrm);  // leftmost point of the ellipse
+  auto half = [&](float dy) { return sqrtf(fmaxf(0.f, fmaf(-(l2 * dy), l2 * dy, E))); };
+  float lo = fminf((-l1 * a - half(a)) * il0, (-l1 * b - half(b)) * il0);
+  float hi = fmaxf((-l1 * a + half(a)) * il0, (-l1 * b + half(b)) * il0);
+  if (dyl >= a && dyl <= b) lo = fminf(lo, (-l1 * dyl - half(dyl)) * il0);
+  if (-dyl >= a && -dyl <= b) hi = fmaxf(hi, (l1 * dyl + half(-dyl)) * il0);
+  xl = fmaxf(g0.x + lo - 0.01f, -1e6f);
+  xr = fminf(g0.x + hi + 0.01f, 1e6f);
+  return xl <= xr;
+}
+
 // Conservative test of a gaussian's 3-sigma rectangle against render tile
 // (tx, ty) (same integer rule as the macro binning, at 8x8 granularity).
 __device__ __forceinline__ void tile_rect(const float4& g0, const float4& g1, int& x0, int& x1, int& y0, int& y1) {

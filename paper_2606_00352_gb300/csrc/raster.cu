@@ -30,7 +30,6 @@ namespace hg {
 namespace {
 
 constexpr int RW = 8;  // warps per CTA
-constexpr int UNROLL = 4;    // gaussians whose alphas are computed together
 constexpr int DRAIN = 32;    // gaussians blended per drain of the scheduling buffer
 constexpr uint32_t RING = 64;  // scheduling buffer capacity per warp (2 x DRAIN)
 constexpr int RT = RW * 32;
@@ -114,8 +113,24 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         y0 = max(max(y0, mty0), 0) - mty0;
         y1 = min(min(y1, mty0 + MH - 1), V.tiles_y - 1) - mty0;
         if (x0 <= x1 && y0 <= y1) {
-          const unsigned long long row = ((1ull << (x1 - x0 + 1)) - 1ull) << x0;
-          for (int y = y0; y <= y1; ++y) gm |= row << (y * MW);
+          // opacity-aware ellipse per tile row (inline visibility, Sec. 4.5)
+          const float E = support_level(g1.y);
+          for (int y = y0; y <= y1; ++y) {
+            int c0 = x0, c1 = x1;
+            if (E < 0.f) {
+              c1 = c0 - 1;
+            } else {
+              float xl, xr;
+              const float ya = (float)((mty0 + y) * TILE);
+              if (!ellipse_row_span(g0, g1, E, ya, ya + (float)(TILE - 1), xl, xr)) {
+                c1 = c0 - 1;
+              } else {
+                c0 = max(c0, floordiv((int)ceilf(xl), TILE) - mtx0);
+                c1 = min(c1, floordiv((int)floorf(xr), TILE) - mtx0);
+              }
+            }
+            if (c0 <= c1) gm |= (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
+          }
         }
       }
 #pragma unroll
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       uint32_t n_blend = 0;
       // scheduling buffer (Alg. 2): indices of the tile's gaussians from
       // successive mini-batches accumulate in a per-warp ring and are
-      // drained DRAIN at a time, UNROLL gaussians per step
+      // drained DRAIN at a time
       uint16_t* ring = s_ring + warp * RING;
       uint32_t head = 0, tail = 0;
       bool all_done = false;
@@ -231,39 +246,23 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         }
         while (tail - head >= DRAIN || (k == K - 1 && tail > head)) {
           const uint32_t n = min(tail - head, (uint32_t)DRAIN);
-          for (uint32_t i = 0; i < n; i += UNROLL) {
-            float a0[UNROLL], a1[UNROLL];
-            bool k0[UNROLL], k1[UNROLL];
-            float4 c[UNROLL];
-            uint32_t jj[UNROLL];
-#pragma unroll
-            for (int q = 0; q < UNROLL; ++q) {
-              const bool valid = i + q < n;
-              const uint32_t j = ring[(head + (valid ? i + q : i)) & (RING - 1)];
-              const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1];
-              c[q] = s_rec[j * 3 + 2];
-              jj[q] = j;
-              const float ub = g0.z * (fpx - g0.x);
-              a0[q] = alpha_of(ub, fpy - g0.y, g0, g1, k0[q]);
-              a1[q] = alpha_of(ub, fpy1 - g0.y, g0, g1, k1[q]);
-              k0[q] = k0[q] && valid;
-              k1[q] = k1[q] && valid;
+          for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t j = ring[(head + i) & (RING - 1)];
+            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
+            const float ub = g0.z * (fpx - g0.x);
+            const bool st0 = blend_bf(p0, ub, fpy - g0.y, g0, g1, g2);
+            const bool st1 = blend_bf(p1, ub, fpy1 - g0.y, g0, g1, g2);
+            if (SAVE) {
+              stop0 = st0 ? j : stop0;
+              stop1 = st1 ? j : stop1;
             }
-#pragma unroll
-            for (int q = 0; q < UNROLL; ++q) {
-              const bool st0 = apply_alpha(p0, a0[q], k0[q], c[q]);
-              const bool st1 = apply_alpha(p1, a1[q], k1[q], c[q]);
-              if (SAVE) {
-                stop0 = st0 ? jj[q] : stop0;
-                stop1 = st1 ? jj[q] : stop1;
-              }
-            }
-            n_blend += min((uint32_t)UNROLL, n - i);
-            if ((i & 7) == 4 && __all_sync(0xffffffffu, p0.done && p1.done)) {
+            if ((i & 7) == 7 && __all_sync(0xffffffffu, p0.done && p1.done)) {
               all_done = true;
+              n_blend += i + 1;
               break;
             }
           }
+          if (!all_done) n_blend += n;
           head += n;
           __syncwarp();
           if (all_done || __all_sync(0xffffffffu, p0.done && p1.done)) {
