@@ -35,6 +35,20 @@ constexpr uint32_t RING = 64;  // scheduling buffer capacity per warp (2 x DRAIN
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
+// 32 x 32 bit-matrix transpose across a warp (5-stage shuffle butterfly):
+// lane i holds row i on entry and column i on return.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int w = 16 >> s;
+    const uint32_t m = masks[s];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, w);
+    x = (lane & w) ? ((x & ~m) | ((y & ~m) >> w)) : ((x & m) | ((y & m) << w));
+  }
+  return x;
+}
+
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -133,10 +147,12 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           }
         }
       }
-#pragma unroll
-      for (int t = 0; t < M; ++t) {
-        const uint32_t b = __ballot_sync(0xffffffffu, (gm >> t) & 1ull);
-        if (lane == (t & 31)) s_mask[k * M + t] = b;
+      // TransposeMasks: lane t receives the 32-gaussian mask of tile t
+      const uint32_t lo = transpose32((uint32_t)gm, lane);
+      if (lane < M) s_mask[k * M + lane] = lo;
+      if (M > 32) {
+        const uint32_t hi = transpose32((uint32_t)(gm >> 32), lane);
+        s_mask[k * M + 32 + lane] = hi;
       }
     }
     __syncthreads();
