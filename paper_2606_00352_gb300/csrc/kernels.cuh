@@ -55,7 +55,7 @@ struct PartitionArgs {
 // Sort tiers: segment-size limits handled by one CTA in shared memory.
 constexpr int TIER0_MAX = 1024;    // 128 threads x 8
 constexpr int TIER1_MAX = 4096;    // 256 threads x 16
-constexpr int TIER2_MAX = 16384;   // 1024 threads x 16
+constexpr int TIER2_MAX = 8192;    // 512 threads x 16
 constexpr int OS_THREADS = 512;    // onesweep tile: 512 threads x 16 items
 constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;

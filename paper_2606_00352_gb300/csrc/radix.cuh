@@ -19,6 +19,19 @@ struct RankSmem {
   uint32_t digit_count[256];
 };
 
+// Lanes of the warp holding the same digit (9 bits, NO_DIGIT included) as
+// this lane, from one ballot per bit (measured faster than match.any here).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 // dig[i] in [0, 256) or NO_DIGIT.  On return pos[i] is the item's position in
 // the block sorted stably by digit (undefined for NO_DIGIT), and
 // digit_start / digit_count describe the sorted block.
@@ -33,7 +46,7 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[IPT], uint32_t 
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const uint32_t d = dig[i];
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t peers = digit_peers(d);
     const uint32_t leader = __ffs(peers) - 1;
     uint32_t base = 0;
     if (d < 256) base = s.hist[warp][d];

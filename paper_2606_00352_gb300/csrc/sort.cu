@@ -1,7 +1,7 @@
 // Segmented depth sort (Sec. 3.3, 4.4).  Every (view, macro-tile) segment of
 // (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
-//   * segments of <= 16K pairs: one CTA sorts the segment in shared memory
-//     (tiers <= 1K / 4K / 16K pairs), skipping digit passes whose byte is
+//   * segments of <= 8K pairs: one CTA sorts the segment in shared memory
+//     (tiers <= 1K / 4K / 8K pairs), skipping digit passes whose byte is
 //     constant over the segment;
 //   * larger segments: a segment-local onesweep (one kernel per 8-bit digit
 //     pass, decoupled look-back across the segment's tiles, tiles claimed in
@@ -367,7 +367,7 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
   cudaError_t e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
   if ((e = launch_tier<256, 16>(a, 1, 4, st)) != cudaSuccess) return e;
-  if ((e = launch_tier<1024, 16>(a, 2, 1, st)) != cudaSuccess) return e;
+  if ((e = launch_tier<512, 16>(a, 2, 2, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   bool alt = false;
   e = launch_onesweep<uint32_t, 4>(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist,

@@ -146,7 +146,7 @@ def test_discrete_stages_all_tiers(lib, ctx):
     cam = scenes.look_at((3, 0, 0), width=640, height=96)
     g = np.random.default_rng(5)
     parts = []
-    for n, w in ((400, 64), (3000, 128), (12000, 256), (40000, 512)):
+    for n, w in ((400, 64), (3000, 128), (6000, 256), (40000, 512)):
         p = _synthetic_records(n, 64, 32, 500, seed=int(g.integers(1 << 30)))
         p["mean2d"][:, 0] += w - 64  # one macro column per density
         parts.append(p)
