@@ -1,0 +1,134 @@
+"""Pins of the oracle gradient: central finite differences of the FP64
+forward model, and the polynomial SH form against the Legendre basis."""
+import hashlib
+
+import numpy as np
+import pytest
+
+from paper_2606_00352_gb300.scenes import Scene, Camera, look_at
+from oracle import composite as C
+from oracle import grad as G
+from oracle import project as P
+from oracle import sh as SH
+
+
+def _scene(n=24, seed=0, deg=3):
+    g = np.random.default_rng(seed)
+    k = (deg + 1) ** 2
+    means = np.stack([g.uniform(-0.4, 0.4, n), g.uniform(-0.3, 0.3, n), g.uniform(-0.3, 0.3, n)], 1)
+    sh = g.normal(0.0, 0.3, (n, k, 3))
+    sh[:, 0, :] = g.normal(0.8, 0.4, (n, 3))
+    return Scene(means, g.normal(-2.3, 0.4, (n, 3)), g.standard_normal((n, 4)), g.normal(0.5, 1.5, n), sh, deg)
+
+
+def _cams():
+    return [look_at((2.5, 0.2, 0.1), width=24, height=20, fov_x_deg=40.0),
+            look_at((0.3, 2.4, -0.5), width=17, height=21, fov_x_deg=45.0)]
+
+
+def _objective(scene, cams, vs, bg):
+    tot = 0.0
+    for cam, v in zip(cams, vs):
+        img = C.render(P.project(scene, cam), bg=bg)["rgb"]
+        tot += float((img * v).sum())
+    return tot
+
+
+def _signature(scene, cams):
+    """Every discrete decision of the forward model, hashed."""
+    h = hashlib.sha256()
+    for cam in cams:
+        pr = P.project(scene, cam)
+        h.update(pr["visible"].tobytes())
+        h.update(pr["radius"].tobytes())
+        h.update((pr["rgb_raw"] > 0).tobytes())
+        t = pr["t_cam"]
+        lim = 1.3 * 0.5 * cam.width / cam.fx
+        h.update((np.abs(t[:, 0] / np.where(t[:, 2] > 0, t[:, 2], 1)) < lim).tobytes())
+        gw, gh, off, gid = C.tile_candidates(pr)
+        h.update(gid.tobytes())
+        for tt in range(gw * gh):
+            ids = gid[off[tt]:off[tt + 1]]
+            if len(ids) == 0:
+                continue
+            px, py = C._tile_pixels(tt % gw, tt // gw, 8, pr["width"], pr["height"])
+            q, a = C.alpha_at(pr, ids, px.astype(float), py.astype(float))
+            raw = pr["opacity"][ids][:, None] * np.exp(-0.5 * q)
+            contrib = (q <= 9.0) & (a >= 1 / 255)
+            h.update(contrib.tobytes())
+            h.update((raw >= 0.99).tobytes())
+            _, _, stopped, _ = C.composite_block(a, q, pr["rgb"][ids])
+            t_after = np.cumprod(1 - np.where(contrib, a, 0), axis=0)
+            h.update((contrib & (t_after < 1e-4)).tobytes())
+    return h.hexdigest()
+
+
+def _params(scene):
+    return {"means": scene.means, "log_scales": scene.log_scales, "quats": scene.quats,
+            "opacity_logits": scene.opacity_logits, "sh": scene.sh}
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_matches_central_differences(seed):
+    scene = _scene(seed=seed)
+    cams = _cams()
+    bg = (0.1, 0.3, 0.2)
+    g = np.random.default_rng(100 + seed)
+    vs = [g.normal(0, 1, (c.height, c.width, 3)) for c in cams]
+    ana = G.render_grads(scene, cams, vs, bg)
+    base_sig = _signature(scene, cams)
+    params = _params(scene)
+    checked = skipped = 0
+    worst = 0.0
+    for name, arr in params.items():
+        flat = arr.reshape(-1)
+        idx = g.choice(flat.size, size=min(flat.size, 40), replace=False)
+        for i in idx:
+            h = 1e-6 * max(1.0, abs(flat[i]))
+            old = flat[i]
+            flat[i] = old + h
+            fp, sp_ = _objective(scene, cams, vs, bg), _signature(scene, cams)
+            flat[i] = old - h
+            fm, sm_ = _objective(scene, cams, vs, bg), _signature(scene, cams)
+            flat[i] = old
+            if sp_ != base_sig or sm_ != base_sig:
+                skipped += 1
+                continue
+            fd = (fp - fm) / (2 * h)
+            an = ana[name].reshape(-1)[i]
+            err = abs(fd - an) / max(1e-3, abs(fd), abs(an))
+            worst = max(worst, err)
+            checked += 1
+            assert err < 1e-4, (name, i, fd, an)
+    assert checked >= 150 and skipped <= checked // 4, (checked, skipped)
+
+
+def test_gradient_nonzero_for_every_parameter_kind():
+    scene = _scene(seed=3)
+    cams = _cams()
+    vs = [np.ones((c.height, c.width, 3)) for c in cams]
+    ana = G.render_grads(scene, cams, vs)
+    for k, v in ana.items():
+        assert np.abs(v).max() > 1e-6, k
+
+
+def test_sh_polynomials_equal_legendre_basis():
+    g = np.random.default_rng(4)
+    d = g.standard_normal((200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    for deg in range(4):
+        y, _ = G.sh_poly_eval(d, deg)
+        np.testing.assert_allclose(y, SH.sh_basis(d, deg), atol=1e-13)
+
+
+def test_single_gaussian_opacity_gradient_closed_form():
+    """C = c o e^{-q/2} at an unclamped pixel: dC/dlogit = C (1 - o)."""
+    cam = Camera(np.eye(4, dtype=np.float32), 20.0, 20.0, 8.5, 8.5, 16, 16)
+    o = 0.3
+    sc = Scene(np.array([[0.01, -0.02, 3.0]]), np.full((1, 3), -1.6), np.array([[1.0, 0.1, 0.0, 0.0]]),
+               np.array([np.log(o / (1 - o))]), np.array([[[0.7, 0.2, -0.1]]]), 0)
+    v = np.zeros((16, 16, 3))
+    v[8, 8, 0] = 1.0
+    ana = G.render_grads(sc, [cam], [v])
+    img = C.render(P.project(sc, cam))["rgb"]
+    np.testing.assert_allclose(ana["opacity_logits"][0], img[8, 8, 0] * (1 - o), rtol=1e-10)
