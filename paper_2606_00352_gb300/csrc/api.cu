@@ -427,8 +427,8 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ENS(B_SEGHIST, sizeof(uint32_t) * 4 * 256 * s->cap_big_segs);
     ENS(B_LOOKBACK, sizeof(uint32_t) * 256 * s->cap_tiles);
     if (o->save_for_backward) {
-      ENS(B_STOPPOS, sizeof(uint16_t) * TILE_PX * M * s->cap_batches);
       ENS(B_PREFIX, sizeof(float4) * TILE_PX * M * s->cap_batches);
+      ENS(B_FINAL, sizeof(float4) * (size_t)g.pixels);
     }
     PartitionArgs pa{};
     pa.bin = (const uint4*)s->bufs[B_BIN].p;
@@ -506,7 +506,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.mode = (uint32_t*)s->bufs[B_MODE].p;
     ra.tile_state = (float4*)s->bufs[B_TSTATE].p;
     ra.tile_rank = (uint32_t*)s->bufs[B_TRANK].p;
-    ra.stop_pos = o->save_for_backward ? (uint16_t*)s->bufs[B_STOPPOS].p : nullptr;
+    ra.stop_pos = nullptr;
     ra.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
     ra.persistent_ctas = 0;
     ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;
@@ -535,6 +535,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ma.out_rgb = out_rgb;
     ma.out_T = out_T;
     ma.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
+    ma.final_px = o->save_for_backward ? (float4*)s->bufs[B_FINAL].p : nullptr;
     ma.fc = fc;
     if (n == 0) {
       // empty scene: the first batch table is all zero, merge writes background

@@ -88,6 +88,18 @@ __device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g
   return al;
 }
 
+// alpha_of that also returns the unclamped o 2^-e (for the backward).
+__device__ __forceinline__ float alpha_raw_of(float ubase, float dy, const float4& g0, const float4& g1, bool& ok,
+                                              float& raw) {
+  const float u = fmaf(g0.w, dy, ubase);
+  const float w = g1.x * dy;
+  const float e = fmaf(u, u, w * w);
+  raw = g1.y * ex2_approx(-e);
+  const float al = fminf(ALPHA_MAX, raw);
+  ok = (e <= SUPPORT_E) && (al >= ALPHA_MIN);
+  return al;
+}
+
 __device__ __forceinline__ bool apply_alpha(PixelAcc& p, float al, bool ok_in, const float4& g2) {
   const bool ok = !p.done && ok_in;
   const float tn = p.T * (1.f - al);

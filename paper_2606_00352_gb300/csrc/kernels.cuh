@@ -128,7 +128,44 @@ struct MergeArgs {
   float* out_rgb;
   float* out_T;
   float4* prefix;             // optional [cap_batches][M][64]: (C, T) entering each batch (backward)
+  float4* final_px;           // optional [pixels]: (r, g, b, T) as written to the outputs (backward)
   FrameCounters* fc;
+};
+
+struct BackwardArgs {
+  const float4* rec;          // forward records [V][n][3]
+  long long n;
+  const ViewDesc* views;
+  int n_views;
+  const uint32_t* vals;       // sorted pair ids
+  const uint4* batches;
+  const uint32_t* batch_order;
+  const unsigned long long* active;
+  const float4* prefix;       // [cap_batches][M][64]
+  const float4* final_px;     // [pixels]
+  const float* dl_drgb;       // [pixels][3]
+  float* g2d;                 // [V][n][9]: d mean2d (2), d conic A B C (3), d opacity, d rgb (3)
+  int batch_cap;
+  int macro_w, macro_h;
+  FrameCounters* fc;
+};
+
+struct ProjectBackwardArgs {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  long long n;
+  int sh_degree;
+  const ViewDesc* views;
+  int n_views;
+  const float* g2d;
+  float* d_means;
+  float* d_log_scales;
+  float* d_quats;
+  float* d_opacity_logits;
+  float* d_sh;
 };
 
 struct PlainArgs {
@@ -186,6 +223,8 @@ cudaError_t launch_partition(const PartitionArgs& a, cudaStream_t st);
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
 cudaError_t launch_raster(const RasterArgs& a, cudaStream_t st);
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
+cudaError_t launch_raster_backward(const BackwardArgs& a, cudaStream_t st);
+cudaError_t launch_project_backward(const ProjectBackwardArgs& a, cudaStream_t st);
 // returns the key pointer that holds the sorted result through *sorted_keys / *sorted_vals
 cudaError_t launch_plain(PlainArgs& a, cudaStream_t st, unsigned long long** sorted_keys, uint32_t** sorted_vals);
 

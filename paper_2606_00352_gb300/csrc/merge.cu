@@ -153,17 +153,21 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
     }
     if (in0) {
       const long long o = V.pix_base + (long long)py * V.W + px;
-      a.out_rgb[o * 3 + 0] = fmaf(p0.T, a.bg[0], p0.r);
-      a.out_rgb[o * 3 + 1] = fmaf(p0.T, a.bg[1], p0.g);
-      a.out_rgb[o * 3 + 2] = fmaf(p0.T, a.bg[2], p0.b);
+      const float4 f = make_float4(fmaf(p0.T, a.bg[0], p0.r), fmaf(p0.T, a.bg[1], p0.g), fmaf(p0.T, a.bg[2], p0.b), p0.T);
+      a.out_rgb[o * 3 + 0] = f.x;
+      a.out_rgb[o * 3 + 1] = f.y;
+      a.out_rgb[o * 3 + 2] = f.z;
       if (a.out_T) a.out_T[o] = p0.T;
+      if (a.final_px) a.final_px[o] = f;
     }
     if (in1) {
       const long long o = V.pix_base + (long long)(py + 4) * V.W + px;
-      a.out_rgb[o * 3 + 0] = fmaf(p1.T, a.bg[0], p1.r);
-      a.out_rgb[o * 3 + 1] = fmaf(p1.T, a.bg[1], p1.g);
-      a.out_rgb[o * 3 + 2] = fmaf(p1.T, a.bg[2], p1.b);
+      const float4 f = make_float4(fmaf(p1.T, a.bg[0], p1.r), fmaf(p1.T, a.bg[1], p1.g), fmaf(p1.T, a.bg[2], p1.b), p1.T);
+      a.out_rgb[o * 3 + 0] = f.x;
+      a.out_rgb[o * 3 + 1] = f.y;
+      a.out_rgb[o * 3 + 2] = f.z;
       if (a.out_T) a.out_T[o] = p1.T;
+      if (a.final_px) a.final_px[o] = f;
     }
   }
   if (lane == 0 && replays) atomicAdd(&a.fc->replays, replays);

@@ -5,7 +5,7 @@
 //           gathers its 48-byte record into shared memory (one mbarrier)
 //   phase 1 each warp takes mini-batches of 32 gaussians, computes the
 //           gaussian's render-tile mask inside the macro-tile and transposes
-//           the 32 x M bit matrix with ballots (per-tile gaussian masks)
+//           the 32 x M bit matrix with a shuffle butterfly (per-tile masks)
 //   queue   warp 0 ORs the masks per tile and compacts the active tiles
 //   chain   (exact termination) the unit of rank k waits, with a bounded
 //           spin, until rank k-1 of the same macro-tile has finished; it then
@@ -24,6 +24,7 @@
 //           stopped inside the batch)
 #include "blend.cuh"
 #include "kernels.cuh"
+#include "raster_common.cuh"
 
 namespace hg {
 
@@ -34,26 +35,6 @@ constexpr int DRAIN = 32;    // gaussians blended per drain of the scheduling bu
 constexpr uint32_t RING = 64;  // scheduling buffer capacity per warp (2 x DRAIN)
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
-
-// 32 x 32 bit-matrix transpose across a warp (5-stage shuffle butterfly):
-// lane i holds row i on entry and column i on return.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int w = 16 >> s;
-    const uint32_t m = masks[s];
-    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, w);
-    x = (lane & w) ? ((x & ~m) | ((y & ~m) >> w)) : ((x & m) | ((y & m) << w));
-  }
-  return x;
-}
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 template <int MW, int MH, bool SAVE>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
@@ -115,46 +96,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 
     // phase 1: per-gaussian tile masks, transposed to per-tile masks
     const int K = (int)((count + 31) / 32);
-    for (int k = warp; k < K; k += RW) {
-      const uint32_t j = (uint32_t)k * 32 + lane;
-      unsigned long long gm = 0;
-      if (j < count) {
-        const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1];
-        int x0, x1, y0, y1;
-        tile_rect(g0, g1, x0, x1, y0, y1);
-        x0 = max(max(x0, mtx0), 0) - mtx0;
-        x1 = min(min(x1, mtx0 + MW - 1), V.tiles_x - 1) - mtx0;
-        y0 = max(max(y0, mty0), 0) - mty0;
-        y1 = min(min(y1, mty0 + MH - 1), V.tiles_y - 1) - mty0;
-        if (x0 <= x1 && y0 <= y1) {
-          // opacity-aware ellipse per tile row (inline visibility, Sec. 4.5)
-          const float E = support_level(g1.y);
-          for (int y = y0; y <= y1; ++y) {
-            int c0 = x0, c1 = x1;
-            if (E < 0.f) {
-              c1 = c0 - 1;
-            } else {
-              float xl, xr;
-              const float ya = (float)((mty0 + y) * TILE);
-              if (!ellipse_row_span(g0, g1, E, ya, ya + (float)(TILE - 1), xl, xr)) {
-                c1 = c0 - 1;
-              } else {
-                c0 = max(c0, floordiv((int)ceilf(xl), TILE) - mtx0);
-                c1 = min(c1, floordiv((int)floorf(xr), TILE) - mtx0);
-              }
-            }
-            if (c0 <= c1) gm |= (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
-          }
-        }
-      }
-      // TransposeMasks: lane t receives the 32-gaussian mask of tile t
-      const uint32_t lo = transpose32((uint32_t)gm, lane);
-      if (lane < M) s_mask[k * M + lane] = lo;
-      if (M > 32) {
-        const uint32_t hi = transpose32((uint32_t)(gm >> 32), lane);
-        s_mask[k * M + 32 + lane] = hi;
-      }
-    }
+    build_tile_masks<MW, MH>(s_rec, s_mask, count, V, mtx0, mty0, RW);
     __syncthreads();
 
     // tile work queue (warp 0)
@@ -298,7 +240,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         st_cs(out + lane, make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T));
         st_cs(out + lane + 32, make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T));
       }
-      if (SAVE) {
+      if (SAVE && a.stop_pos) {
         uint16_t* sp = a.stop_pos + ((size_t)r * M + t) * TILE_PX;
         sp[lane] = (uint16_t)stop0;
         sp[lane + 32] = (uint16_t)stop1;

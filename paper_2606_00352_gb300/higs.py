@@ -27,7 +27,7 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",
            "hg_state_free", "hg_state_sync", "hg_render_stats", "hg_state_read", "hg_graph_create",
            "hg_graph_launch", "hg_graph_set_cameras", "hg_graph_sync", "hg_graph_kernels", "hg_graph_destroy",
-           "hg_kernel_launches", "hg_segmented_sort_noalloc"]
+           "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward"]
 
 
 class HgError(RuntimeError):
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
     lib.hg_graph_kernels.restype = C.c_int64
     lib.hg_graph_destroy.argtypes = [C.c_void_p]
     lib.hg_kernel_launches.restype = C.c_int64
+    lib.hg_render_backward.restype = C.c_int
+    lib.hg_render_backward.argtypes = [C.c_void_p] + [C.c_void_p] * 7
     lib.hg_segmented_sort_noalloc.restype = C.c_int
     lib.hg_segmented_sort_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p]
@@ -328,6 +330,58 @@ def segmented_sort_noalloc(seg_off, keys, vals, keys_out, vals_out, stream=None)
                                                 int(keys.numel()), C.c_void_p(keys.data_ptr()),
                                                 C.c_void_p(vals.data_ptr()), C.c_void_p(keys_out.data_ptr()),
                                                 C.c_void_p(vals_out.data_ptr()), _stream_ptr(stream)))
+
+
+def render_backward(state: State, scene: GpuScene, dl_drgb, stream=None):
+    """hg_render_backward for the frame saved in `state`: returns device
+    tensors (d_means, d_log_scales, d_quats, d_opacity_logits, d_sh)."""
+    import torch
+    dev = torch.device("cuda", scene.ctx.device)
+    n, k = scene.n, (scene.sh_degree + 1) ** 2
+    outs = [torch.empty((n, 3), device=dev), torch.empty((n, 3), device=dev), torch.empty((n, 4), device=dev),
+            torch.empty((n,), device=dev), torch.empty((n, k, 3), device=dev)]
+    g = dl_drgb.contiguous().to(torch.float32)
+    check(scene.ctx.lib.hg_render_backward(state.h, C.c_void_p(g.data_ptr()),
+                                           *[C.c_void_p(o.data_ptr()) for o in outs], _stream_ptr(stream)))
+    return tuple(outs)
+
+
+class _RenderFn:
+    """torch.autograd.Function wrapping hg_render / hg_render_backward."""
+    fn = None
+
+    @classmethod
+    def get(cls):
+        if cls.fn is None:
+            import torch
+
+            class RenderFunction(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, means, log_scales, quats, opacity_logits, sh, gctx, cams, opts, sh_degree):
+                    scene = GpuScene(gctx, means.detach(), log_scales.detach(), quats.detach(),
+                                     opacity_logits.detach(), sh.detach(), sh_degree, borrow=True)
+                    state = State(gctx)
+                    o = Options(**{**opts.__dict__, "save_for_backward": True, "path": PATH_HIGS})
+                    rgb, _ = render(scene, cams, o, state=state, with_T=False)
+                    ctx.hg = (scene, state)
+                    return rgb
+
+                @staticmethod
+                def backward(ctx, grad_rgb):
+                    scene, state = ctx.hg
+                    grads = render_backward(state, scene, grad_rgb)
+                    return (*grads, None, None, None, None)
+
+            cls.fn = RenderFunction
+        return cls.fn
+
+
+def render_differentiable(gctx: Context, means, log_scales, quats, opacity_logits, sh, sh_degree: int, cams,
+                          opts: Options | None = None):
+    """Differentiable render of views `cams`: packed rgb [sum_v H_v W_v * 3]
+    whose gradient flows to the five scene tensors (float32 CUDA)."""
+    return _RenderFn.get().apply(means, log_scales, quats, opacity_logits, sh, gctx, cams, opts or Options(),
+                                 sh_degree)
 
 
 def kernel_launches() -> int:
