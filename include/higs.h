@@ -240,6 +240,70 @@ hg_status hg_graph_sync(hg_graph* graph);
 int64_t hg_graph_kernels(const hg_graph* graph);
 void hg_graph_destroy(hg_graph* graph);
 
+/* ---------------------------------------------------------------- serving */
+/* Continuous-batching render server over device-resident scenes (not in the
+ * paper).  A dispatcher thread keeps up to max_inflight launches on the
+ * device, each on its own stream with its own workspace; whenever a launch
+ * slot is free it packs up to max_views_per_launch pending requests of the
+ * scene of the oldest pending request (any mix of resolutions) into one
+ * multi-view launch, if the memory the slots then hold stays within
+ * mem_budget_bytes (0 = no limit).  Requests arriving meanwhile are admitted
+ * as slots and memory free up, so their work overlaps on the device. */
+typedef struct {
+  int32_t max_inflight;          /* 1..64 launches on the device at once */
+  int32_t max_views_per_launch;  /* 1..64 */
+  int64_t mem_budget_bytes;
+  hg_render_opts opts;           /* render options of every launch (path HiGS) */
+} hg_serve_config;
+
+typedef struct {
+  int64_t submitted, completed, rejected, cancelled, failed, launches, queued, inflight_launches,
+      max_inflight_seen, held_bytes;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> completion, completed requests */
+  double req_per_s;                       /* completed requests per second since the last reset */
+  double mean_views_per_launch;
+} hg_serve_counters;
+
+hg_status hg_serve_create(hg_ctx* ctx, const hg_serve_config* cfg, hg_server** out);
+/* Register a scene (kept alive by the caller while the server exists). */
+hg_status hg_serve_add_scene(hg_server* server, hg_scene* scene, int* scene_id);
+/* Queue one view; returns at once.  out_rgb receives H*W*3 floats: device
+ * memory (out_on_host = 0) or page-locked host memory (out_on_host = 1;
+ * pageable memory would stall the dispatcher).  HG_ERR_NOT_FOUND for an
+ * unknown scene, HG_ERR_OOM when the request alone exceeds the budget. */
+hg_status hg_serve_submit(hg_server* server, int scene_id, const hg_camera* cam, float* out_rgb, int out_on_host,
+                          uint64_t* req_id);
+/* *done = 1 once the request finished; returns its status when done. */
+hg_status hg_serve_poll(hg_server* server, uint64_t req_id, int* done);
+/* Wait up to timeout_ms (< 0: forever) and release the request; returns its
+ * status, HG_ERR_BUSY on timeout. */
+hg_status hg_serve_wait(hg_server* server, uint64_t req_id, int timeout_ms);
+/* Cancel a request that has not been launched (HG_ERR_BUSY if it has). */
+hg_status hg_serve_cancel(hg_server* server, uint64_t req_id);
+hg_status hg_serve_stats(hg_server* server, hg_serve_counters* out);
+hg_status hg_serve_reset_stats(hg_server* server);
+/* Stops the dispatcher after the launches in flight complete. */
+void hg_serve_destroy(hg_server* server);
+
+/* ----------------------------------------------------------------- tuning */
+typedef struct {
+  int32_t macro_w, macro_h, batch_cap;
+  float ms; /* median frame time of the candidate */
+} hg_tune_result;
+
+/* Pick the macro-tile shape (4x4, 8x4, 8x8 render tiles; the partitioning
+ * scale of Sec. 3.1) and the batch cap B_r (256, 512, 1024, 2048) that
+ * render `cams` of `scene` fastest: every candidate renders the views
+ * 1 + `iters` times on `stream` (synchronously) and is scored by the median
+ * frame time.  *best receives `base` with the winning shape and cap (path
+ * HiGS).  results (may be NULL) receives up to max_results candidates,
+ * *n_results their count.  cache_path (may be NULL): a text file of
+ * "key macro_w macro_h batch_cap ms" lines; a hit returns without rendering,
+ * a sweep appends its winner.  Allocates a temporary workspace. */
+hg_status hg_autotune(hg_scene* scene, const hg_camera* cams, int n_views, const hg_render_opts* base, int iters,
+                      const char* cache_path, hg_render_opts* best, hg_tune_result* results, int max_results,
+                      int* n_results, void* stream);
+
 /* ---------------------------------------------------- allocation-free sort */
 /* Segmented sort of (uint32 key, uint32 value) pairs, ascending by (key,
  * value) inside each segment, with no device allocation at all.  This is an

@@ -27,7 +27,9 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",
            "hg_state_free", "hg_state_sync", "hg_render_stats", "hg_state_read", "hg_graph_create",
            "hg_graph_launch", "hg_graph_set_cameras", "hg_graph_sync", "hg_graph_kernels", "hg_graph_destroy",
-           "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward"]
+           "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward", "hg_autotune",
+           "hg_serve_create", "hg_serve_add_scene", "hg_serve_submit", "hg_serve_poll", "hg_serve_wait",
+           "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats", "hg_serve_destroy"]
 
 
 class HgError(RuntimeError):
@@ -51,6 +53,25 @@ class RenderOpts(C.Structure):
     _fields_ = [("path", C.c_int32), ("macro_w", C.c_int32), ("macro_h", C.c_int32),
                 ("batch_cap", C.c_int32), ("bin_test", C.c_int32), ("bg", C.c_float * 3),
                 ("save_for_backward", C.c_int32), ("flags", C.c_int32)]
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("max_views_per_launch", C.c_int32), ("mem_budget_bytes", C.c_int64),
+                ("opts", RenderOpts)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "rejected", "cancelled", "failed", "launches",
+                                          "queued", "inflight_launches", "max_inflight_seen", "held_bytes")] + \
+               [(k, C.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "req_per_s",
+                                           "mean_views_per_launch")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("macro_w", C.c_int32), ("macro_h", C.c_int32), ("batch_cap", C.c_int32), ("ms", C.c_float)]
 
 
 class FrameStats(C.Structure):
@@ -104,6 +125,22 @@ def load(path: str = LIB_PATH):
     lib.hg_graph_kernels.restype = C.c_int64
     lib.hg_graph_destroy.argtypes = [C.c_void_p]
     lib.hg_kernel_launches.restype = C.c_int64
+    for name in ("hg_serve_create", "hg_serve_add_scene", "hg_serve_submit", "hg_serve_poll", "hg_serve_wait",
+                 "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats"):
+        getattr(lib, name).restype = C.c_int
+    lib.hg_serve_create.argtypes = [C.c_void_p, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]
+    lib.hg_serve_add_scene.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    lib.hg_serve_submit.argtypes = [C.c_void_p, C.c_int, C.POINTER(CameraC), C.c_void_p, C.c_int,
+                                    C.POINTER(C.c_uint64)]
+    lib.hg_serve_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]
+    lib.hg_serve_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_int]
+    lib.hg_serve_cancel.argtypes = [C.c_void_p, C.c_uint64]
+    lib.hg_serve_stats.argtypes = [C.c_void_p, C.POINTER(ServeStats)]
+    lib.hg_serve_reset_stats.argtypes = [C.c_void_p]
+    lib.hg_serve_destroy.argtypes = [C.c_void_p]
+    lib.hg_autotune.restype = C.c_int
+    lib.hg_autotune.argtypes = [C.c_void_p, C.POINTER(CameraC), C.c_int, C.POINTER(RenderOpts), C.c_int, C.c_char_p,
+                                C.POINTER(RenderOpts), C.POINTER(TuneResult), C.c_int, C.POINTER(C.c_int), C.c_void_p]
     lib.hg_render_backward.restype = C.c_int
     lib.hg_render_backward.argtypes = [C.c_void_p] + [C.c_void_p] * 7
     lib.hg_segmented_sort_noalloc.restype = C.c_int
@@ -382,6 +419,85 @@ def render_differentiable(gctx: Context, means, log_scales, quats, opacity_logit
     whose gradient flows to the five scene tensors (float32 CUDA)."""
     return _RenderFn.get().apply(means, log_scales, quats, opacity_logits, sh, gctx, cams, opts or Options(),
                                  sh_degree)
+
+
+def autotune(scene: GpuScene, cams, base: Options | None = None, iters: int = 3, cache_path: str | None = None,
+             stream=None):
+    """hg_autotune: returns (best Options, [(macro_w, macro_h, batch_cap, ms)])."""
+    base = base or Options()
+    best = RenderOpts()
+    res = (TuneResult * 16)()
+    nres = C.c_int()
+    check(scene.ctx.lib.hg_autotune(scene.h, cameras_array(cams), len(cams), C.byref(base.struct()), iters,
+                                    cache_path.encode() if cache_path else None, C.byref(best), res, 16,
+                                    C.byref(nres), _stream_ptr(stream)))
+    opts = Options(path=best.path, macro_w=best.macro_w, macro_h=best.macro_h, batch_cap=best.batch_cap,
+                   bg=tuple(best.bg), save_for_backward=bool(best.save_for_backward), flags=best.flags)
+    return opts, [(r.macro_w, r.macro_h, r.batch_cap, r.ms) for r in res[:nres.value]]
+
+
+class Server:
+    """Continuous-batching render server (hg_serve_*)."""
+
+    def __init__(self, ctx: Context, max_inflight: int = 4, max_views_per_launch: int = 8, mem_budget_bytes: int = 0,
+                 opts: Options | None = None):
+        self.ctx, self.lib = ctx, ctx.lib
+        cfg = ServeConfig(max_inflight, max_views_per_launch, mem_budget_bytes, (opts or Options()).struct())
+        h = C.c_void_p()
+        check(self.lib.hg_serve_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.scenes = []
+
+    def add_scene(self, scene: GpuScene) -> int:
+        sid = C.c_int()
+        check(self.lib.hg_serve_add_scene(self.h, scene.h, C.byref(sid)))
+        self.scenes.append(scene)
+        return sid.value
+
+    def submit(self, scene_id: int, cam, out, on_host: bool = False) -> int:
+        """Non-blocking; `out` is a float32 tensor of H*W*3 (CUDA, or pinned CPU)."""
+        rid = C.c_uint64()
+        check(self.lib.hg_serve_submit(self.h, scene_id, C.byref(camera_struct(cam)), C.c_void_p(out.data_ptr()),
+                                       int(on_host), C.byref(rid)))
+        return rid.value
+
+    def submit_status(self, scene_id: int, cam, out, on_host: bool = False):
+        rid = C.c_uint64()
+        st = self.lib.hg_serve_submit(self.h, scene_id, C.byref(camera_struct(cam)), C.c_void_p(out.data_ptr()),
+                                      int(on_host), C.byref(rid))
+        return st, rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = C.c_int()
+        st = self.lib.hg_serve_poll(self.h, rid, C.byref(done))
+        if done.value:
+            check(st)
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> int:
+        return int(self.lib.hg_serve_wait(self.h, rid, timeout_ms))
+
+    def cancel(self, rid: int) -> int:
+        return int(self.lib.hg_serve_cancel(self.h, rid))
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        check(self.lib.hg_serve_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        check(self.lib.hg_serve_reset_stats(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.hg_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches() -> int:
