@@ -253,6 +253,10 @@ typedef struct {
   int32_t max_inflight;          /* 1..64 launches on the device at once */
   int32_t max_views_per_launch;  /* 1..64 */
   int64_t mem_budget_bytes;
+  int32_t batch_window_us;       /* hold the oldest request up to this long while fewer than
+                                    max_views_per_launch requests of its scene are pending
+                                    (0: launch as soon as a slot is free) */
+  int32_t pad;
   hg_render_opts opts;           /* render options of every launch (path HiGS) */
 } hg_serve_config;
 

@@ -184,9 +184,20 @@ static void dispatcher(hg_server* S) {
       S->cv_done.notify_all();
     }
     // admit pending requests into free slots
+    bool holding = false;
     for (Slot& sl : S->slots) {
       if (sl.busy || S->pending.empty()) continue;
-      const int scene = S->reqs[S->pending.front()].scene;
+      const Request& oldest = S->reqs[S->pending.front()];
+      const int scene = oldest.scene;
+      if (S->cfg.batch_window_us > 0) {
+        int same = 0;
+        for (uint64_t id : S->pending) same += S->reqs[id].scene == scene;
+        const double age_us = std::chrono::duration<double, std::micro>(Clock::now() - oldest.t_submit).count();
+        if (same < S->cfg.max_views_per_launch && age_us < S->cfg.batch_window_us) {
+          holding = true;  // wait for more views of this scene
+          break;
+        }
+      }
       sl.reqs.clear();
       sl.cams.clear();
       sl.pixels = 0;
@@ -226,7 +237,7 @@ static void dispatcher(hg_server* S) {
     for (const Slot& sl : S->slots) inflight += sl.busy;
     S->max_inflight_seen = std::max(S->max_inflight_seen, inflight);
     if (!progressed) {
-      if (inflight == 0 && S->pending.empty())
+      if (inflight == 0 && S->pending.empty() && !holding)
         S->cv_work.wait(lk, [S] { return S->stop || !S->pending.empty(); });
       else
         S->cv_work.wait_for(lk, std::chrono::microseconds(50));

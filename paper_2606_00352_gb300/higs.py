@@ -57,7 +57,7 @@ class RenderOpts(C.Structure):
 
 class ServeConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("max_views_per_launch", C.c_int32), ("mem_budget_bytes", C.c_int64),
-                ("opts", RenderOpts)]
+                ("batch_window_us", C.c_int32), ("pad", C.c_int32), ("opts", RenderOpts)]
 
 
 class ServeStats(C.Structure):
@@ -440,9 +440,10 @@ class Server:
     """Continuous-batching render server (hg_serve_*)."""
 
     def __init__(self, ctx: Context, max_inflight: int = 4, max_views_per_launch: int = 8, mem_budget_bytes: int = 0,
-                 opts: Options | None = None):
+                 batch_window_us: int = 0, opts: Options | None = None):
         self.ctx, self.lib = ctx, ctx.lib
-        cfg = ServeConfig(max_inflight, max_views_per_launch, mem_budget_bytes, (opts or Options()).struct())
+        cfg = ServeConfig(max_inflight, max_views_per_launch, mem_budget_bytes, batch_window_us, 0,
+                          (opts or Options()).struct())
         h = C.c_void_p()
         check(self.lib.hg_serve_create(ctx.h, C.byref(cfg), C.byref(h)))
         self.h = h

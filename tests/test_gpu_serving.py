@@ -33,7 +33,7 @@ def test_results_equal_alone_and_in_the_mix(lib, ctx, scene_set):
     the same as rendering that view alone (views are independent, so bit
     for bit), and requests were batched and overlapped on the device."""
     import torch
-    srv = lib.Server(ctx, max_inflight=3, max_views_per_launch=6)
+    srv = lib.Server(ctx, max_inflight=3, max_views_per_launch=6, batch_window_us=3000)
     ids = [srv.add_scene(g) for g in scene_set]
     g = np.random.default_rng(0)
     res = [(320, 180), (640, 360), (200, 120), (97, 61)]
