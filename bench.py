@@ -289,6 +289,88 @@ def roofline(stage_ms, stats0, n, pk, clock_mhz):
     return top, out
 
 
+SERVE_RATES = (200, 500, 1000, 2000)
+SERVE_RES = ((1280, 720), (1920, 1080), (3840, 2160))
+SERVE_RES_W = (0.3, 0.5, 0.2)
+
+
+def serving_run(higs, ctx, gscenes, seconds, seed=0):
+    """Poisson arrivals at each rate over the resident scenes; every request
+    is a random orbit pose at a random resolution (weights 0.3/0.5/0.2).
+    Returns one row per rate."""
+    import numpy as np
+    import torch
+    from paper_2606_00352_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    srv = higs.Server(ctx, max_inflight=4, max_views_per_launch=8, mem_budget_bytes=64 << 30)
+    sids = [srv.add_scene(g) for g in gscenes]
+    pool = [torch.empty(3840 * 2160 * 3, device="cuda") for _ in range(48)]
+    poses = {r: scenes.scene_orbit(N_POSES, r[0], r[1]) for r in SERVE_RES}
+    # warm the slots' workspaces at every resolution
+    warm = [srv.submit(sids[k % len(sids)], poses[SERVE_RES[k % 3]][k], pool[k]) for k in range(12)]
+    for rid in warm:
+        srv.wait(rid)
+    rows = []
+    for rate in SERVE_RATES:
+        srv.reset_stats()
+        inflight = [None] * len(pool)
+        n = int(rate * seconds)
+        gaps = rng.exponential(1.0 / rate, n)
+        t = time.perf_counter()
+        t_next = t
+        for k in range(n):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                pass
+            slot = k % len(pool)
+            if inflight[slot] is not None:
+                srv.wait(inflight[slot])  # back-pressure: the output buffer is still in use
+            res = SERVE_RES[rng.choice(3, p=SERVE_RES_W)]
+            cam = poses[res][int(rng.integers(0, N_POSES))]
+            inflight[slot] = srv.submit(sids[int(rng.integers(0, len(sids)))], cam, pool[slot])
+        for rid in inflight:
+            if rid is not None:
+                srv.wait(rid)
+        wall = time.perf_counter() - t
+        st = srv.stats()
+        rows.append({"offered_req_per_s": rate, "completed": st["completed"],
+                     "throughput_req_per_s": round(st["completed"] / wall, 1),
+                     "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                     "max_ms": round(st["max_ms"], 3), "views_per_launch": round(st["mean_views_per_launch"], 2),
+                     "max_inflight": st["max_inflight_seen"]})
+    srv.close()
+    return rows
+
+
+def train_step_ms(higs, ctx, steps=5):
+    """Forward (saving what the backward needs) + backward of 4 views at
+    1080p of the 1M-gaussian scene, with 0.5 ||C - C*||^2 upstream."""
+    import torch
+    from paper_2606_00352_gb300 import scenes
+    scene = scenes.scene_1m()
+    gs = higs.GpuScene.from_scene(ctx, scene)
+    cams = scenes.scene_orbit(32, WIDTH, HEIGHT)[:VIEWS]
+    st = higs.State(ctx)
+    opts = higs.Options(save_for_backward=True)
+    target = torch.rand(VIEWS * WIDTH * HEIGHT * 3, device="cuda")
+    times = []
+    for k in range(steps + 2):
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        rgb, _ = higs.render(gs, cams, opts, state=st, with_T=False)
+        e1.record()
+        higs.render_backward(st, gs, rgb - target)
+        e2.record()
+        e2.synchronize()
+        if k >= 2:
+            times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    return {"forward_ms": round(statistics.median(t[0] for t in times), 3),
+            "backward_ms": round(statistics.median(t[1] for t in times), 3),
+            "workload": "1M-gaussian SH-3 scene (64 clusters, Zipf 1.2), 4 views at 1920x1080, "
+                        "forward with saved prefixes + hg_render_backward"}
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -302,7 +384,14 @@ def gpu_arm(args):
     del scene
     stream = torch.cuda.Stream()
     pk = peaks()
+    tuned = None
     opts = higs.Options(path=higs.PATH_HIGS, macro_w=8, macro_h=4, batch_cap=1024, flags=higs.FLAG_TIMING)
+    if not args.skip_tune:
+        best, table = higs.autotune(gs, pose_batch(cams, 0, rank), higs.Options(), iters=3, stream=stream)
+        opts = higs.Options(path=higs.PATH_HIGS, macro_w=best.macro_w, macro_h=best.macro_h,
+                            batch_cap=best.batch_cap, flags=higs.FLAG_TIMING)
+        tuned = {"chosen": f"{best.macro_w}x{best.macro_h}/{best.batch_cap}",
+                 "candidates_ms": {f"{r[0]}x{r[1]}/{r[2]}": round(r[3], 3) for r in table}}
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -326,7 +415,24 @@ def gpu_arm(args):
                  "ms_per_step": round(pms / psteps, 3),
                  "tile_pairs_per_step": int(statistics.mean(s["n_pairs"] for s in pstats))}
 
-    e2e_opts = higs.Options(path=higs.PATH_HIGS)
+    serving = None
+    if not args.skip_serve and world == 1:
+        from paper_2606_00352_gb300 import scenes as sc_mod
+        small = [higs.GpuScene.from_scene(ctx, sc_mod.cluster_scene(n, 256, 1.4, seed=11 + k,
+                                                                    sigma_range=sc_mod.CLUSTER_SIGMA,
+                                                                    extent=sc_mod.EXTENT))
+                 for k, n in enumerate((500_000, 2_000_000))]
+        serving = {"rows": serving_run(higs, ctx, small + [gs], seconds=1.5),
+                   "workload": "3 resident scenes (0.5M, 2M, 5.8M gaussians, 256 clusters, Zipf 1.4); Poisson "
+                               "arrivals; random orbit pose at 1280x720 / 1920x1080 / 3840x2160 (0.3/0.5/0.2); "
+                               "up to 4 launches in flight, up to 8 views per launch; latency submit -> completion"}
+        del small
+    training = None
+    if not args.skip_train and world == 1:
+        training = train_step_ms(higs, ctx)
+
+    e2e_opts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
+                            batch_cap=opts.batch_cap)
     e2e_steps = max(3, min(args.steps, 10))
     e = time_e2e(higs, gs, cams, e2e_opts, e2e_steps, min(args.warmup, 3), rank, stream)
     e2e_t = max_over_ranks(e["seconds"], world)
@@ -344,7 +450,7 @@ def gpu_arm(args):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(),
+        "config": workload_config() | {"macro_tile": f"{opts.macro_w}x{opts.macro_h}", "batch_cap": opts.batch_cap},
         "roofline": {k: v for k, v in rl[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
         | {"kernel": top, "traffic": None, "peak_source": pk["source"]},
         "stages": rl | {"merge": {"ms": round(stage_ms["merge"], 4)}},
@@ -363,7 +469,11 @@ def gpu_arm(args):
             "raster_evals_per_step": int(statistics.mean(s["raster_evals"] for s in s0)),
             "visible_per_step": int(statistics.mean(s["n_visible"] for s in s0)),
         },
-        "serving_p99_ms": None,
+        "serving_p99_ms": next((r["p99_ms"] for r in serving["rows"] if r["offered_req_per_s"] == 1000), None)
+        if serving else None,
+        "serving": serving,
+        "autotune": tuned,
+        "train_step": training,
     }
     print(json.dumps(line), flush=True)
 
@@ -413,6 +523,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-train", action="store_true")
+    ap.add_argument("--skip-tune", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--case", default="", choices=["", "1m", "1m-plain", "5m8"],
                     help="small profiling case instead of the benchmark")
