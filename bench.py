@@ -171,12 +171,17 @@ def barrier(world):
         dist.barrier()
 
 
+def _reduce_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(x: float, world: int) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -186,9 +191,17 @@ def sum_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_throughput(local_ms: float, local_frames: float, world: int):
+    """Whole-job frames/s: the frames all ranks rendered over the slowest
+    rank's time.  Returns (value, max ms)."""
+    ms = max_over_ranks(local_ms, world)
+    frames = sum_over_ranks(local_frames, world)
+    return frames / (ms * 1e-3), ms
 
 
 def pose_batch(cams, step, rank):
@@ -397,9 +410,7 @@ def gpu_arm(args):
     sampler.start()
     ms, stats, kernels = time_graph(higs, gs, cams, opts, args.steps, args.warmup, rank, world, stream)
     clocks = sampler.stop()
-    ms = max_over_ranks(ms, world)
-    frames = sum_over_ranks(args.steps * VIEWS, world)
-    value = frames / (ms * 1e-3)
+    value, ms = job_throughput(ms, args.steps * VIEWS, world)
 
     stage_ms = {k: statistics.mean(s["ms_" + k] for s in stats) for k in
                 ("project", "partition", "sort", "raster", "merge")}
@@ -410,8 +421,8 @@ def gpu_arm(args):
         popts = higs.Options(path=higs.PATH_PLAIN, flags=higs.FLAG_TIMING)
         psteps = max(3, min(args.steps, 10))
         pms, pstats, _ = time_graph(higs, gs, cams, popts, psteps, min(args.warmup, 3), rank, world, stream)
-        pms = max_over_ranks(pms, world)
-        plain = {"value": round(sum_over_ranks(psteps * VIEWS, world) / (pms * 1e-3), 2), "unit": UNIT,
+        pvalue, pms = job_throughput(pms, psteps * VIEWS, world)
+        plain = {"value": round(pvalue, 2), "unit": UNIT,
                  "ms_per_step": round(pms / psteps, 3),
                  "tile_pairs_per_step": int(statistics.mean(s["n_pairs"] for s in pstats))}
 
