@@ -398,7 +398,8 @@ def gpu_arm(args):
     stream = torch.cuda.Stream()
     pk = peaks()
     tuned = None
-    opts = higs.Options(path=higs.PATH_HIGS, macro_w=8, macro_h=4, batch_cap=1024, flags=higs.FLAG_TIMING)
+    mw, mh = (int(x) for x in args.macro.split("x"))
+    opts = higs.Options(path=higs.PATH_HIGS, macro_w=mw, macro_h=mh, batch_cap=args.cap, flags=higs.FLAG_TIMING)
     if not args.skip_tune:
         best, table = higs.autotune(gs, pose_batch(cams, 0, rank), higs.Options(), iters=3, stream=stream)
         opts = higs.Options(path=higs.PATH_HIGS, macro_w=best.macro_w, macro_h=best.macro_h,
@@ -502,7 +503,9 @@ def profile_case(args):
     gs = higs.GpuScene.from_scene(ctx, scene)
     st = higs.State(ctx)
     path = higs.PATH_PLAIN if args.case == "1m-plain" else higs.PATH_HIGS
-    opts = higs.Options(path=path, flags=higs.FLAG_TIMING | (higs.FLAG_PROFILE if args.profile else 0))
+    mw, mh = (int(x) for x in args.macro.split("x"))
+    opts = higs.Options(path=path, macro_w=mw, macro_h=mh, batch_cap=args.cap,
+                        flags=higs.FLAG_TIMING | (higs.FLAG_PROFILE if args.profile else 0))
     for k in range(args.warmup + args.steps):
         higs.render(gs, pose_batch(cams, k, 0), opts, state=st)
     torch.cuda.synchronize()
@@ -541,6 +544,8 @@ def main():
     ap.add_argument("--case", default="", choices=["", "1m", "1m-plain", "5m8"],
                     help="small profiling case instead of the benchmark")
     ap.add_argument("--profile", action="store_true", help="count rasteriser phase cycles (profiling case)")
+    ap.add_argument("--macro", default="8x4", choices=["4x4", "8x4", "8x8"], help="macro shape without autotuning")
+    ap.add_argument("--cap", type=int, default=1024, help="batch cap B_r without autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and not args.oracle_steps and not args.case:
         args.warmup = 3

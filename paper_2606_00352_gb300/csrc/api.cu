@@ -377,6 +377,8 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pa.bin = (const uint4*)s->bufs[B_BIN].p;
     pa.rec = (const float4*)s->bufs[B_REC].p;
     pa.n = n;
+    pa.vis = (const uint32_t*)s->bufs[B_VIS].p;
+    pa.vis_words = vis_words;
     pa.views = views;
     pa.n_views = V;
     pa.total_tiles = g.total_tiles;
@@ -506,7 +508,6 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.mode = (uint32_t*)s->bufs[B_MODE].p;
     ra.tile_state = (float4*)s->bufs[B_TSTATE].p;
     ra.tile_rank = (uint32_t*)s->bufs[B_TRANK].p;
-    ra.stop_pos = nullptr;
     ra.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
     ra.persistent_ctas = 0;
     ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;

@@ -74,15 +74,12 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
 __device__ __forceinline__ void bwd_pixel(PixelAcc& p, float ub, float dx, float dy, const float4& g0, const float4& g1,
                                           const float4& g2, float cA, float cB, float cC, const float3& ctot,
                                           const float3& vv, float (&g)[16], bool& contrib) {
-  bool ok;
   float raw;
-  const float a = alpha_raw_of(ub, dy, g0, g1, ok, raw);
-  const bool was_done = p.done;
+  const float a = alpha_of(ub, dy, g0, g1, g2, raw);
   const float tb = p.T;
-  contrib = !was_done && ok && !(tb * (1.f - a) < T_EPS);
-  apply_alpha(p, a, ok, g2);
+  const float wt = apply_alpha(p, a, g2);
+  contrib = wt > 0.f;
   if (!contrib) return;
-  const float wt = a * tb;
   g[6] += vv.x * wt;
   g[7] += vv.y * wt;
   g[8] += vv.z * wt;
@@ -181,12 +178,8 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       const float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
       const float4 q0 = pre[lane], q1 = pre[lane + 32];
       PixelAcc p0, p1;
-      pixel_init(p0, in0);
-      pixel_init(p1, in1);
-      p0.r = q0.x, p0.g = q0.y, p0.b = q0.z, p0.T = fmaxf(q0.w, 0.f);
-      p1.r = q1.x, p1.g = q1.y, p1.b = q1.z, p1.T = fmaxf(q1.w, 0.f);
-      p0.done = p0.done || !(q0.w > 0.f);
-      p1.done = p1.done || !(q1.w > 0.f);
+      pixel_load(p0, in0, q0);
+      pixel_load(p1, in1, q1);
       float3 ct0 = make_float3(0.f, 0.f, 0.f), ct1 = ct0, v0 = ct0, v1 = ct0;
       if (in0) {
         const long long o = V.pix_base + (long long)py * V.W + px;
@@ -203,7 +196,7 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
       uint16_t* ring = s_ring + warp * BRING;
       uint32_t head = 0, tail = 0;
-      bool all_done = __all_sync(0xffffffffu, p0.done && p1.done);
+      bool all_done = !__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1));
       for (int k = 0; k < K && !all_done; ++k) {
         const uint32_t m = s_mask[k * M + t];
         if (m) {
@@ -233,7 +226,7 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
           }
           head += n;
           __syncwarp();
-          if (__all_sync(0xffffffffu, p0.done && p1.done)) {
+          if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
             all_done = true;
             break;
           }

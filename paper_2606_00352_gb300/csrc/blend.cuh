@@ -2,7 +2,11 @@
 // q <= 9, alpha = min(0.99, o exp(-q/2)), skip alpha < 1/255, stop before
 // T (1 - alpha) < 1e-4.  q is evaluated as the sum of squares of the
 // prescaled Cholesky factors (Sec. 3.5), e = (l0 dx + l1 dy)^2 + (l2 dy)^2 =
-// q log2(e) / 2, so alpha = o exp2(-e).
+// q log2(e) / 2, so alpha = o exp2(-e).  Every kernel that blends (forward
+// raster, merge replay, plain path, backward replay) uses these functions, so
+// the same gaussian at the same pixel gives the same bits everywhere.  The
+// decisions are written as saturated multiply-adds, which keeps the inner
+// loop off the integer/compare pipe.
 #pragma once
 #include "common.cuh"
 
@@ -14,106 +18,83 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Pixel state.  T is the live transmittance: it is 0 once the pixel has
+// stopped (and for pixels outside the image), so later gaussians add nothing;
+// Ts is the transmittance at the stop (0 while the pixel is live).  The final
+// transmittance is T + Ts (one of the two is 0).
 struct PixelAcc {
-  float r, g, b, T;
-  bool done;      // stopped (or outside the image)
-  bool stopped;   // stopped by the termination rule
+  float r, g, b, T, Ts;
 };
 
 __device__ __forceinline__ void pixel_init(PixelAcc& p, bool inside, float t_in = 1.f) {
   p.r = p.g = p.b = 0.f;
-  p.T = t_in;
-  p.done = !inside;
-  p.stopped = false;
+  p.T = inside ? t_in : 0.f;
+  p.Ts = 0.f;
 }
 
-// One gaussian (g0 = {mx, my, l0', l1'}, g1 = {l2', o, ., .}, g2 = {r, g, b, .})
-// at pixel offset (dx, dy) from its centre.  Returns true if the pixel
-// stopped at this gaussian.
-__device__ __forceinline__ bool blend_one(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
-                                          const float4& g2) {
-  if (p.done) return false;
-  const float u = fmaf(g0.w, dy, ubase);
-  const float w = g1.x * dy;
-  const float e = fmaf(u, u, w * w);
-  if (e > SUPPORT_E) return false;
-  const float al = fminf(ALPHA_MAX, g1.y * ex2_approx(-e));
-  if (al < ALPHA_MIN) return false;
-  const float tn = p.T * (1.f - al);
-  if (tn < T_EPS) {
-    p.done = true;
-    p.stopped = true;
-    return true;
-  }
-  const float wt = al * p.T;
-  p.r = fmaf(g2.x, wt, p.r);
-  p.g = fmaf(g2.y, wt, p.g);
-  p.b = fmaf(g2.z, wt, p.b);
-  p.T = tn;
-  return false;
+__device__ __forceinline__ bool pixel_live(const PixelAcc& p) { return p.T > 0.f; }
+__device__ __forceinline__ float pixel_final_T(const PixelAcc& p) { return p.T + p.Ts; }
+
+// Stored per-pixel state (per-tile chain state, partials, saved prefixes):
+// {r, g, b, w} with w = T while live and -Ts once stopped.
+__device__ __forceinline__ float4 pixel_state(const PixelAcc& p) {
+  return make_float4(p.r, p.g, p.b, p.T > 0.f ? p.T : -p.Ts);
+}
+__device__ __forceinline__ void pixel_load(PixelAcc& p, bool inside, const float4& s) {
+  p.r = s.x;
+  p.g = s.y;
+  p.b = s.z;
+  const bool st = signbit(s.w);
+  p.T = inside && !st ? s.w : 0.f;
+  p.Ts = st ? -s.w : 0.f;
 }
 
-// Branch-free form of blend_one with the same arithmetic (so every kernel
-// that blends the same gaussian at the same pixel gets the same bits).
-__device__ __forceinline__ bool blend_bf(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
-                                         const float4& g2) {
-  const float u = fmaf(g0.w, dy, ubase);
-  const float w = g1.x * dy;
-  const float e = fmaf(u, u, w * w);
-  const float al = fminf(ALPHA_MAX, g1.y * ex2_approx(-e));
-  const bool ok = !p.done && (e <= SUPPORT_E) && (al >= ALPHA_MIN);
-  const float tn = p.T * (1.f - al);
-  const bool stop = ok && (tn < T_EPS);
-  const bool contrib = ok && !stop;
-  const float wt = contrib ? al * p.T : 0.f;
-  p.r = fmaf(g2.x, wt, p.r);
-  p.g = fmaf(g2.y, wt, p.g);
-  p.b = fmaf(g2.z, wt, p.b);
-  p.T = contrib ? tn : p.T;
-  p.done = p.done || stop;
-  p.stopped = p.stopped || stop;
-  return stop;
-}
-
-// blend_bf split in two: the alpha of a gaussian at a pixel does not depend
-// on the pixel's transmittance, so several gaussians' alphas can be computed
-// independently (instruction-level parallelism) before the ordered updates.
-// Together they perform exactly the operations of blend_bf.
-__device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g0, const float4& g1, bool& ok) {
-  const float u = fmaf(g0.w, dy, ubase);
-  const float w = g1.x * dy;
-  const float e = fmaf(u, u, w * w);
-  const float al = fminf(ALPHA_MAX, g1.y * ex2_approx(-e));
-  ok = (e <= SUPPORT_E) && (al >= ALPHA_MIN);
-  return al;
-}
-
-// alpha_of that also returns the unclamped o 2^-e (for the backward).
-__device__ __forceinline__ float alpha_raw_of(float ubase, float dy, const float4& g0, const float4& g1, bool& ok,
-                                              float& raw) {
+// Blend test and alpha of gaussian (g0 = {mx, my, l0', l1'}, g1 = {l2', o, ., .},
+// g2 = {r, g, b, E}) at pixel offset dy from its centre, ubase = l0' dx:
+// e = (l0' dx + l1' dy)^2 + (l2' dy)^2 = q log2(e) / 2 and alpha =
+// min(0.99, o 2^-e).  The support q <= 9 and alpha >= 1/255 together are
+// e <= E with E = min(9 log2(e) / 2, log2(255 o)) (stored per gaussian).
+// Returns alpha, or 0 when the gaussian fails the test; raw = o 2^-e.
+// The test is the sign of E - e scaled by 2^64 and saturated (a multiply-add,
+// not a compare-select): exact whenever E and e differ by at least 2^-64.
+__device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g0, const float4& g1,
+                                          const float4& g2, float& raw) {
   const float u = fmaf(g0.w, dy, ubase);
   const float w = g1.x * dy;
   const float e = fmaf(u, u, w * w);
   raw = g1.y * ex2_approx(-e);
-  const float al = fminf(ALPHA_MAX, raw);
-  ok = (e <= SUPPORT_E) && (al >= ALPHA_MIN);
-  return al;
+  const float f = __saturatef(fmaf(g2.w - e, 18446744073709551616.f, 1.f));
+  return fminf(ALPHA_MAX, raw) * f;
 }
 
-__device__ __forceinline__ bool apply_alpha(PixelAcc& p, float al, bool ok_in, const float4& g2) {
-  const bool ok = !p.done && ok_in;
-  const float tn = p.T * (1.f - al);
-  const bool stop = ok && (tn < T_EPS);
-  const bool contrib = ok && !stop;
-  const float wt = contrib ? al * p.T : 0.f;
+// Ordered update with the alpha from alpha_of: T' = T - alpha T; the pixel
+// stops before T' < 1e-4 (that gaussian excluded).  The stop test is the
+// sign of T' - 1e-4 scaled by 2^40 and saturated: exact, since two distinct
+// floats near 1e-4 differ by at least 2^-37.  Returns the gaussian's weight
+// alpha T (0 when it did not contribute).
+__device__ __forceinline__ float apply_alpha(PixelAcc& p, float al, const float4& g2) {
+  const float aT = al * p.T;
+  const float tn = p.T - aT;
+  const float dt = tn - T_EPS;
+  const float s = __saturatef(fmaf(dt, 1099511627776.f, 1.f));  // 1: keeps going
+  const float ns = __saturatef(dt * -1099511627776.f);           // 1: stops (or stopped)
+  const float wt = aT * s;
   p.r = fmaf(g2.x, wt, p.r);
   p.g = fmaf(g2.y, wt, p.g);
   p.b = fmaf(g2.z, wt, p.b);
-  p.T = contrib ? tn : p.T;
-  p.done = p.done || stop;
-  p.stopped = p.stopped || stop;
-  return stop;
+  p.Ts = fmaf(ns, p.T, p.Ts);
+  p.T = tn * s;
+  return wt;
 }
+
+__device__ __forceinline__ void blend(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
+                                      const float4& g2) {
+  float raw;
+  apply_alpha(p, alpha_of(ubase, dy, g0, g1, g2, raw), g2);
+}
+
+// Per-gaussian level E of the blend test (stored in the record's g2.w).
+__device__ __forceinline__ float blend_level(float o) { return fminf(SUPPORT_E, log2f(255.f * o)); }
 
 // Largest prescaled q a pixel can have and still pass the blend test:
 // alpha >= 1/255 needs o 2^-e >= 1/255, i.e. e <= log2(255 o), and the

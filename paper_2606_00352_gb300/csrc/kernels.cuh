@@ -97,7 +97,6 @@ struct RasterArgs {
   uint32_t* mode;             // [cap_batches] BATCH_CHAINED or BATCH_LOCAL
   float4* tile_state;         // [total tiles][64] (r, g, b, +-T) after the chained batches
   uint32_t* tile_rank;        // [total tiles] rank + 1 of the last chained batch that blended the tile, 0 = none
-  uint16_t* stop_pos;         // optional [cap_batches][M][64]: stop position inside the batch (backward)
   float4* prefix;             // optional [cap_batches][M][64]: (C, +-T) entering the batch (backward)
   int persistent_ctas;
   int independent;            // never wait: every batch after the first renders from T = 1
@@ -169,8 +168,10 @@ struct ProjectBackwardArgs {
 };
 
 struct PlainArgs {
-  const uint4* bin;
+  const uint4* bin;           // valid where the visibility bit is set
   const float4* rec;
+  const uint32_t* vis;        // [V][vis_words]
+  long long vis_words;
   long long n;
   const ViewDesc* views;
   int n_views;

@@ -25,7 +25,7 @@ __device__ __forceinline__ int find_view_tile(const ViewDesc* views, int n_views
 
 __device__ __forceinline__ void apply_partial(PixelAcc& p, const float4& q, bool& need) {
   need = false;
-  if (p.done) return;
+  if (!pixel_live(p)) return;
   const float tk = fabsf(q.w);
   const bool st = signbit(q.w);
   if (st || p.T * tk < T_EPS) {
@@ -33,9 +33,8 @@ __device__ __forceinline__ void apply_partial(PixelAcc& p, const float4& q, bool
       p.r += q.x;
       p.g += q.y;
       p.b += q.z;
-      p.T = tk;
-      p.done = true;
-      p.stopped = true;
+      p.Ts = tk;
+      p.T = 0.f;
     } else {
       need = true;
     }
@@ -80,23 +79,19 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
     uint32_t g = r0;
     while (g < r1 && a.mode[g] == BATCH_CHAINED) ++g;
     if (g > r0 && a.tile_rank[tile] != 0) {
-      const float4 s0 = a.tile_state[(size_t)tile * TILE_PX + lane];
-      const float4 s1 = a.tile_state[(size_t)tile * TILE_PX + lane + 32];
-      p0.r = s0.x, p0.g = s0.y, p0.b = s0.z, p0.T = fabsf(s0.w), p0.stopped = signbit(s0.w);
-      p1.r = s1.x, p1.g = s1.y, p1.b = s1.z, p1.T = fabsf(s1.w), p1.stopped = signbit(s1.w);
-      p0.done = p0.done || p0.stopped;
-      p1.done = p1.done || p1.stopped;
+      pixel_load(p0, in0, a.tile_state[(size_t)tile * TILE_PX + lane]);
+      pixel_load(p1, in1, a.tile_state[(size_t)tile * TILE_PX + lane + 32]);
     }
     // the rest (batches rendered from T = 1): Eq. 1 with replay
     for (uint32_t r = g; r < r1; ++r) {
-      if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
+      if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
       if (!((a.active[r] >> tl) & 1ull)) continue;
       const float4* src = a.partial + ((size_t)r * M + tl) * TILE_PX;
       const float4 q0 = src[lane], q1 = src[lane + 32];
       if (a.prefix) {
         float4* pre = a.prefix + ((size_t)r * M + tl) * TILE_PX;
-        pre[lane] = make_float4(p0.r, p0.g, p0.b, p0.done ? 0.f : p0.T);
-        pre[lane + 32] = make_float4(p1.r, p1.g, p1.b, p1.done ? 0.f : p1.T);
+        pre[lane] = pixel_state(p0);
+        pre[lane + 32] = pixel_state(p1);
       }
       bool need0, need1;
       apply_partial(p0, q0, need0);
@@ -110,7 +105,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
       pixel_init(q1r, need1, p1.T);
       const uint4 bt = a.batches[r];
       for (uint32_t c = 0; c < bt.z; c += 32) {
-        if (__all_sync(0xffffffffu, q0r.done && q1r.done)) break;
+        if (!__any_sync(0xffffffffu, pixel_live(q0r) || pixel_live(q1r))) break;
         const uint32_t j = c + lane;
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
         bool ov = false;
@@ -130,8 +125,8 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
           bal &= bal - 1;
           const float4 h0 = shfl4(g0, b), h1 = shfl4(g1, b), h2 = shfl4(g2, b);
           const float ub = h0.z * (fpx - h0.x);
-          blend_bf(q0r, ub, fpy - h0.y, h0, h1, h2);
-          blend_bf(q1r, ub, fpy1 - h0.y, h0, h1, h2);
+          blend(q0r, ub, fpy - h0.y, h0, h1, h2);
+          blend(q1r, ub, fpy1 - h0.y, h0, h1, h2);
         }
       }
       if (need0) {
@@ -139,34 +134,34 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
         p0.g += q0r.g;
         p0.b += q0r.b;
         p0.T = q0r.T;
-        p0.done = q0r.stopped;
-        p0.stopped = q0r.stopped;
+        p0.Ts = q0r.Ts;
       }
       if (need1) {
         p1.r += q1r.r;
         p1.g += q1r.g;
         p1.b += q1r.b;
         p1.T = q1r.T;
-        p1.done = q1r.stopped;
-        p1.stopped = q1r.stopped;
+        p1.Ts = q1r.Ts;
       }
     }
     if (in0) {
       const long long o = V.pix_base + (long long)py * V.W + px;
-      const float4 f = make_float4(fmaf(p0.T, a.bg[0], p0.r), fmaf(p0.T, a.bg[1], p0.g), fmaf(p0.T, a.bg[2], p0.b), p0.T);
+      const float tf = pixel_final_T(p0);
+      const float4 f = make_float4(fmaf(tf, a.bg[0], p0.r), fmaf(tf, a.bg[1], p0.g), fmaf(tf, a.bg[2], p0.b), tf);
       a.out_rgb[o * 3 + 0] = f.x;
       a.out_rgb[o * 3 + 1] = f.y;
       a.out_rgb[o * 3 + 2] = f.z;
-      if (a.out_T) a.out_T[o] = p0.T;
+      if (a.out_T) a.out_T[o] = tf;
       if (a.final_px) a.final_px[o] = f;
     }
     if (in1) {
       const long long o = V.pix_base + (long long)(py + 4) * V.W + px;
-      const float4 f = make_float4(fmaf(p1.T, a.bg[0], p1.r), fmaf(p1.T, a.bg[1], p1.g), fmaf(p1.T, a.bg[2], p1.b), p1.T);
+      const float tf = pixel_final_T(p1);
+      const float4 f = make_float4(fmaf(tf, a.bg[0], p1.r), fmaf(tf, a.bg[1], p1.g), fmaf(tf, a.bg[2], p1.b), tf);
       a.out_rgb[o * 3 + 0] = f.x;
       a.out_rgb[o * 3 + 1] = f.y;
       a.out_rgb[o * 3 + 2] = f.z;
-      if (a.out_T) a.out_T[o] = p1.T;
+      if (a.out_T) a.out_T[o] = tf;
       if (a.final_px) a.final_px[o] = f;
     }
   }

@@ -25,13 +25,19 @@ __device__ __forceinline__ int tile_span(const uint4& r, const ViewDesc& V, int&
   return (x1 - x0 + 1) * (y1 - y0 + 1);
 }
 
+// Culled (view, gaussian) entries have no record: test the visibility bit.
+__device__ __forceinline__ bool visible(const PlainArgs& a, int v, long long i) {
+  return (a.vis[(long long)v * a.vis_words + (i >> 5)] >> (i & 31)) & 1u;
+}
+
 __global__ void k_plain_count(PlainArgs a) {
   const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = a.n * a.n_views;
   if (o >= total) return;
   const int v = (int)(o / a.n);
   int x0, x1, y0, y1;
-  a.counts[o] = (uint32_t)tile_span(a.bin[o], a.views[v], x0, x1, y0, y1);
+  a.counts[o] = visible(a, v, o - (long long)v * a.n) ? (uint32_t)tile_span(a.bin[o], a.views[v], x0, x1, y0, y1)
+                                                       : 0u;
 }
 
 // exclusive scan of counts[total] into offsets[total + 1]
@@ -100,6 +106,7 @@ __global__ void k_plain_dup(PlainArgs a) {
   if (o >= total || read_status(a.fc)) return;
   const int v = (int)(o / a.n);
   const ViewDesc& V = a.views[v];
+  if (!visible(a, v, o - (long long)v * a.n)) return;
   const uint4 r = a.bin[o];
   int x0, x1, y0, y1;
   if (!tile_span(r, V, x0, x1, y0, y1)) return;
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(TILE_PX) k_plain_raster(PlainArgs a, const uin
   const uint2 rg = a.ranges[tile];
   const float fpx = (float)px, fpy = (float)py;
   for (uint32_t base = rg.x; base < rg.y; base += TILE_PX) {
-    if (__syncthreads_count(!p.done) == 0) break;
+    if (__syncthreads_count(pixel_live(p)) == 0) break;
     const uint32_t j = base + tid;
     if (j < rg.y) {
       const float4* rp = a.rec + (size_t)vals[j] * 3;
@@ -155,15 +162,16 @@ __global__ void __launch_bounds__(TILE_PX) k_plain_raster(PlainArgs a, const uin
     const int nb = (int)min((uint32_t)TILE_PX, rg.y - base);
     for (int k = 0; k < nb; ++k) {
       const float4 g0 = s_rec[k * 3 + 0], g1 = s_rec[k * 3 + 1], g2 = s_rec[k * 3 + 2];
-      blend_bf(p, g0.z * (fpx - g0.x), fpy - g0.y, g0, g1, g2);
+      blend(p, g0.z * (fpx - g0.x), fpy - g0.y, g0, g1, g2);
     }
   }
   if (inside) {
     const long long o = V.pix_base + (long long)py * V.W + px;
-    a.out_rgb[o * 3 + 0] = fmaf(p.T, a.bg[0], p.r);
-    a.out_rgb[o * 3 + 1] = fmaf(p.T, a.bg[1], p.g);
-    a.out_rgb[o * 3 + 2] = fmaf(p.T, a.bg[2], p.b);
-    if (a.out_T) a.out_T[o] = p.T;
+    const float tf = pixel_final_T(p);
+    a.out_rgb[o * 3 + 0] = fmaf(tf, a.bg[0], p.r);
+    a.out_rgb[o * 3 + 1] = fmaf(tf, a.bg[1], p.g);
+    a.out_rgb[o * 3 + 2] = fmaf(tf, a.bg[2], p.b);
+    if (a.out_T) a.out_T[o] = tf;
   }
 }
 

@@ -5,66 +5,18 @@
 //
 // Outputs per (view, gaussian), index v * N + i:
 //   bin  uint4  {mx bits, my bits, radius, depth key}      radius 0 = culled
-//   rec  float4 x3 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, depth}
+//   rec  float4 x3 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, E}
+//        (E: the per-gaussian level of the blend test)
 //   vis  one bit per gaussian, written per warp (Sec. 4.2 visibility bitfield)
+// bin and rec are written for visible entries only.
 // l' are the Cholesky factors of the conic prescaled by sqrt(log2(e)/2), so the
 // rasteriser evaluates alpha = o exp2(-((l0' dx + l1' dy)^2 + (l2' dy)^2)).
+#include "blend.cuh"
 #include "kernels.cuh"
 
 namespace hg {
 
 namespace {
-
-// Real SH basis with the Condon-Shortley phase, k = l*l + l + m; constants
-// are K_l^m (times sqrt(2) for m != 0) from their closed forms.
-template <int DEG>
-__device__ __forceinline__ void sh_eval(const float* c, float x, float y, float z, float& r, float& g,
-                                        float& b) {
-  const float C0 = 0.28209479177387814f;           // 1/(2 sqrt(pi))
-  r = C0 * c[0];
-  g = C0 * c[1];
-  b = C0 * c[2];
-  if (DEG >= 1) {
-    const float C1 = 0.48860251190291992f;         // sqrt(3/(4 pi))
-    float y1[3] = {-C1 * y, C1 * z, -C1 * x};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      r = fmaf(y1[k], c[3 * (1 + k) + 0], r);
-      g = fmaf(y1[k], c[3 * (1 + k) + 1], g);
-      b = fmaf(y1[k], c[3 * (1 + k) + 2], b);
-    }
-  }
-  if (DEG >= 2) {
-    const float C2a = 1.0925484305920792f;         // (1/2) sqrt(15/pi)
-    const float C2b = 0.31539156525252005f;        // (1/4) sqrt(5/pi)
-    const float C2c = 0.54627421529603959f;        // (1/4) sqrt(15/pi)
-    float xx = x * x, yy = y * y, zz = z * z;
-    float y2[5] = {C2a * x * y, -C2a * y * z, C2b * (2.f * zz - xx - yy), -C2a * x * z, C2c * (xx - yy)};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      r = fmaf(y2[k], c[3 * (4 + k) + 0], r);
-      g = fmaf(y2[k], c[3 * (4 + k) + 1], g);
-      b = fmaf(y2[k], c[3 * (4 + k) + 2], b);
-    }
-    if (DEG >= 3) {
-      const float C3a = 0.59004358992664352f;      // (1/4) sqrt(35/(2 pi))
-      const float C3b = 2.8906114426405538f;       // (1/2) sqrt(105/pi)
-      const float C3c = 0.45704579946446577f;      // (1/4) sqrt(21/(2 pi))
-      const float C3d = 0.3731763325901154f;       // (1/4) sqrt(7/pi)
-      const float C3e = 1.4453057213202769f;       // (1/4) sqrt(105/pi)
-      float t4 = 4.f * zz - xx - yy;
-      float y3[7] = {-C3a * y * (3.f * xx - yy), C3b * x * y * z, -C3c * y * t4,
-                     C3d * z * (2.f * zz - 3.f * xx - 3.f * yy), -C3c * x * t4, C3e * z * (xx - yy),
-                     -C3a * x * (xx - 3.f * yy)};
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        r = fmaf(y3[k], c[3 * (9 + k) + 0], r);
-        g = fmaf(y3[k], c[3 * (9 + k) + 1], g);
-        b = fmaf(y3[k], c[3 * (9 + k) + 2], b);
-      }
-    }
-  }
-}
 
 constexpr int PROJ_THREADS = 256;
 
@@ -77,17 +29,87 @@ struct ProjSmem {
   float logits[PROJ_THREADS];
   float sh[PROJ_THREADS * K * 3];
   uint64_t bar;
+  ViewDesc views[1];  // [n_views], sized at launch
 };
 
 template <int DEG>
+__host__ __device__ constexpr size_t proj_smem_bytes(int n_views) {
+  return sizeof(ProjSmem<DEG>) + sizeof(ViewDesc) * (size_t)(n_views > 1 ? n_views - 1 : 0);
+}
+
+// SH colour of one band for up to VG views: acc[v] += sum_m Y_lm(d_v) c_lm.
+template <int L, int VG>
+__device__ __forceinline__ void sh_band(const float* __restrict__ sh_g, const float (&d)[VG][3], float (&acc)[VG][3],
+                                        int nv) {
+  constexpr int B = 2 * L + 1, OFF = L * L;
+  float c[B * 3];
+#pragma unroll
+  for (int k = 0; k < B * 3; ++k) c[k] = sh_g[OFF * 3 + k];
+#pragma unroll
+  for (int v = 0; v < VG; ++v) {
+    if (v >= nv) break;
+    const float x = d[v][0], y = d[v][1], z = d[v][2];
+    float Y[B];
+    if (L == 0) {
+      Y[0] = 0.28209479177387814f;  // 1/(2 sqrt(pi))
+    } else if (L == 1) {
+      const float C1 = 0.48860251190291992f;  // sqrt(3/(4 pi))
+      Y[0] = -C1 * y;
+      Y[1] = C1 * z;
+      Y[2] = -C1 * x;
+    } else if (L == 2) {
+      const float C2a = 1.0925484305920792f;   // (1/2) sqrt(15/pi)
+      const float C2b = 0.31539156525252005f;  // (1/4) sqrt(5/pi)
+      const float C2c = 0.54627421529603959f;  // (1/4) sqrt(15/pi)
+      const float xx = x * x, yy = y * y, zz = z * z;
+      Y[0] = C2a * x * y;
+      Y[1] = -C2a * y * z;
+      Y[2] = C2b * (2.f * zz - xx - yy);
+      Y[3] = -C2a * x * z;
+      Y[4] = C2c * (xx - yy);
+    } else {
+      const float C3a = 0.59004358992664352f;  // (1/4) sqrt(35/(2 pi))
+      const float C3b = 2.8906114426405538f;   // (1/2) sqrt(105/pi)
+      const float C3c = 0.45704579946446577f;  // (1/4) sqrt(21/(2 pi))
+      const float C3d = 0.3731763325901154f;   // (1/4) sqrt(7/pi)
+      const float C3e = 1.4453057213202769f;   // (1/4) sqrt(105/pi)
+      const float xx = x * x, yy = y * y, zz = z * z;
+      const float t4 = 4.f * zz - xx - yy;
+      Y[0] = -C3a * y * (3.f * xx - yy);
+      Y[1] = C3b * x * y * z;
+      Y[2] = -C3c * y * t4;
+      Y[3] = C3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[4] = -C3c * x * t4;
+      Y[5] = C3e * z * (xx - yy);
+      Y[6] = -C3a * x * (xx - 3.f * yy);
+    }
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      acc[v][0] = fmaf(Y[m], c[3 * m + 0], acc[v][0]);
+      acc[v][1] = fmaf(Y[m], c[3 * m + 1], acc[v][1]);
+      acc[v][2] = fmaf(Y[m], c[3 * m + 2], acc[v][2]);
+    }
+  }
+}
+
+// One thread per gaussian, every view of the frame.  Two passes per thread
+// keep the register footprint small (more CTAs per SM, so more copies in
+// flight): geometry for every view (bin record and the first 32 bytes of the
+// raster record), then the SH colour band by band for groups of up to 4
+// views, each band's coefficients read from shared memory once per group.
+// Culled (view, gaussian) entries write nothing: consumers test the
+// visibility bits first.
+template <int DEG>
 __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int VG = 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ProjSmem<DEG>& s = *reinterpret_cast<ProjSmem<DEG>*>(smem_raw);
   const int tid = threadIdx.x;
   const long long i0 = (long long)blockIdx.x * PROJ_THREADS;
   const int cnt = (int)min((long long)PROJ_THREADS, a.n - i0);
   const bool full = cnt == PROJ_THREADS;
+  const int nv = a.n_views;
 
   if (full) {
     // TMA: five contiguous slices, one mbarrier
@@ -106,12 +128,6 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       tma_load_1d(s.logits, a.opacity_logits + i0, b1, &s.bar);
       tma_load_1d(s.sh, a.sh + i0 * K * 3, bsh, &s.bar);
     }
-    if (!mbar_wait_bounded(&s.bar, 0)) {
-      set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
-      // the copies were issued by this CTA: wait (bounded again) before exit
-      mbar_wait_bounded(&s.bar, 0);
-      return;
-    }
   } else {
     for (int j = tid; j < cnt * 3; j += PROJ_THREADS) {
       s.means[j] = a.means[i0 * 3 + j];
@@ -122,135 +138,166 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       s.logits[j] = a.opacity_logits[i0 + j];
     }
     for (int j = tid; j < cnt * K * 3; j += PROJ_THREADS) s.sh[j] = a.sh[i0 * K * 3 + j];
-    __syncthreads();
   }
+  // the view table, while the copies are in flight
+  {
+    const int words = nv * (int)(sizeof(ViewDesc) / 4);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(a.views);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s.views);
+    for (int j = tid; j < words; j += PROJ_THREADS) dst[j] = src[j];
+  }
+  if (full && !mbar_wait_bounded(&s.bar, 0)) {
+    set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
+    // the copies were issued by this CTA: wait (bounded again) before exit
+    mbar_wait_bounded(&s.bar, 0);
+    return;
+  }
+  __syncthreads();
 
   const bool valid = tid < cnt;
   const long long gi = i0 + tid;
-  float px = 0.f, py = 0.f, pz = 0.f, sx = 1.f, sy = 1.f, sz = 1.f, op = 0.f;
-  float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
-  float coef[K * 3];
-  if (valid) {
-    px = s.means[tid * 3 + 0];
-    py = s.means[tid * 3 + 1];
-    pz = s.means[tid * 3 + 2];
-    sx = expf(s.scales[tid * 3 + 0]);
-    sy = expf(s.scales[tid * 3 + 1]);
-    sz = expf(s.scales[tid * 3 + 2]);
-    q = s.quats[tid];
-    op = 1.f / (1.f + expf(-s.logits[tid]));
-    const float4* c4 = reinterpret_cast<const float4*>(s.sh + tid * K * 3);
-#pragma unroll
-    for (int k = 0; k < K * 3 / 4; ++k) {
-      float4 t = c4[k];
-      coef[4 * k + 0] = t.x;
-      coef[4 * k + 1] = t.y;
-      coef[4 * k + 2] = t.z;
-      coef[4 * k + 3] = t.w;
-    }
-    if ((K * 3) % 4)
-      for (int k = (K * 3 / 4) * 4; k < K * 3; ++k) coef[k] = s.sh[tid * K * 3 + k];
-  } else {
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) coef[k] = 0.f;
-  }
-  // rotation of the normalised quaternion (w, x, y, z), times the scales
-  float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-  float w = q.x * qn, x = q.y * qn, y = q.z * qn, z = q.w * qn;
-  float M[3][3] = {{(1.f - 2.f * (y * y + z * z)) * sx, 2.f * (x * y - w * z) * sy, 2.f * (x * z + w * y) * sz},
-                   {2.f * (x * y + w * z) * sx, (1.f - 2.f * (x * x + z * z)) * sy, 2.f * (y * z - w * x) * sz},
-                   {2.f * (x * z - w * y) * sx, 2.f * (y * z + w * x) * sy, (1.f - 2.f * (x * x + y * y)) * sz}};
-
   const int lane = tid & 31;
-  for (int v = 0; v < a.n_views; ++v) {
-    const ViewDesc& V = a.views[v];
-    // depth in the pinned float32 order (no contraction): the sort key
-    float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(V.vm[8], px), __fmul_rn(V.vm[9], py)),
-                                   __fmul_rn(V.vm[10], pz)),
-                         V.vm[11]);
-    float tx = fmaf(V.vm[0], px, fmaf(V.vm[1], py, fmaf(V.vm[2], pz, V.vm[3])));
-    float ty = fmaf(V.vm[4], px, fmaf(V.vm[5], py, fmaf(V.vm[6], pz, V.vm[7])));
-    bool vis = valid && tz > 0.2f;
-    float itz = 1.f / tz;
-    float limx = 1.3f * V.tan_x, limy = 1.3f * V.tan_y;
-    float ux = fminf(fmaxf(tx * itz, -limx), limx);
-    float uy = fminf(fmaxf(ty * itz, -limy), limy);
-    float j00 = V.fx * itz, j02 = -V.fx * ux * itz;
-    float j11 = V.fy * itz, j12 = -V.fy * uy * itz;
-    // T = J W (2x3), then TM = T M
-    float t0[3], t1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      t0[k] = fmaf(j00, V.vm[k], j02 * V.vm[8 + k]);
-      t1[k] = fmaf(j11, V.vm[4 + k], j12 * V.vm[8 + k]);
-    }
-    float m0[3], m1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      m0[k] = fmaf(t0[0], M[0][k], fmaf(t0[1], M[1][k], t0[2] * M[2][k]));
-      m1[k] = fmaf(t1[0], M[0][k], fmaf(t1[1], M[1][k], t1[2] * M[2][k]));
-    }
-    float ca = fmaf(m0[0], m0[0], fmaf(m0[1], m0[1], m0[2] * m0[2])) + 0.3f;
-    float cb = fmaf(m0[0], m1[0], fmaf(m0[1], m1[1], m0[2] * m1[2]));
-    float cc = fmaf(m1[0], m1[0], fmaf(m1[1], m1[1], m1[2] * m1[2])) + 0.3f;
-    float det = ca * cc - cb * cb;
-    vis = vis && det > 0.f;
-    float mid = 0.5f * (ca + cc);
-    float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-    float rr = ceilf(3.f * sqrtf(lam));
-    int rad = (int)fminf(rr, (float)RADIUS_MAX);
-    float mx = fmaf(V.fx, __fdiv_rn(tx, tz), V.cx - 0.5f);
-    float my = fmaf(V.fy, __fdiv_rn(ty, tz), V.cy - 0.5f);
-    vis = vis && rad > 0 && fabsf(mx) < 1e7f && fabsf(my) < 1e7f;
-    if (vis) {
-      int x0 = (int)floorf(mx), y0 = (int)floorf(my);
-      vis = (x0 + rad >= 0) && (x0 - rad <= V.W - 1) && (y0 + rad >= 0) && (y0 - rad <= V.H - 1);
-    }
-    if (!vis) rad = 0;
-    // Cholesky of the conic: l0 = sqrt(c/det), l1 = -b / sqrt(c det), l2 = 1/sqrt(c)
-    float rc = rsqrtf(cc), rd = rsqrtf(det);
-    float l0 = cc * rc * rd * CHOL_PRESCALE;
-    float l1 = -cb * rc * rd * CHOL_PRESCALE;
-    float l2 = rc * CHOL_PRESCALE;
-    // view-dependent colour
-    float dx = px - V.campos[0], dy = py - V.campos[1], dz = pz - V.campos[2];
-    float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float cr, cg, cbl;
-    sh_eval<DEG>(coef, dx * dn, dy * dn, dz * dn, cr, cg, cbl);
-    cr = fmaxf(cr + 0.5f, 0.f);
-    cg = fmaxf(cg + 0.5f, 0.f);
-    cbl = fmaxf(cbl + 0.5f, 0.f);
-    uint32_t key = __float_as_uint(tz);
-    const long long o = (long long)v * a.n + gi;
-    uint32_t ballot = __ballot_sync(0xffffffffu, vis);
+  float px = 0.f, py = 0.f, pz = 0.f, op = 0.f;
+  unsigned long long vbits = 0;  // views in which the gaussian is visible
+  {
+    float sx = 1.f, sy = 1.f, sz = 1.f;
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
     if (valid) {
-      a.bin[o] = make_uint4(__float_as_uint(mx), __float_as_uint(my), (uint32_t)rad, key);
-      float4* r = a.rec + o * 3;
-      r[0] = make_float4(mx, my, l0, l1);
-      r[1] = make_float4(l2, op, __int_as_float(rad), __uint_as_float(key));
-      r[2] = make_float4(cr, cg, cbl, tz);
-      if (a.splats) {
+      px = s.means[tid * 3 + 0];
+      py = s.means[tid * 3 + 1];
+      pz = s.means[tid * 3 + 2];
+      sx = expf(s.scales[tid * 3 + 0]);
+      sy = expf(s.scales[tid * 3 + 1]);
+      sz = expf(s.scales[tid * 3 + 2]);
+      q = s.quats[tid];
+      op = 1.f / (1.f + expf(-s.logits[tid]));
+    }
+    // rotation of the normalised quaternion (w, x, y, z), times the scales
+    const float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float w = q.x * qn, x = q.y * qn, y = q.z * qn, z = q.w * qn;
+    const float M[3][3] = {
+        {(1.f - 2.f * (y * y + z * z)) * sx, 2.f * (x * y - w * z) * sy, 2.f * (x * z + w * y) * sz},
+        {2.f * (x * y + w * z) * sx, (1.f - 2.f * (x * x + z * z)) * sy, 2.f * (y * z - w * x) * sz},
+        {2.f * (x * z - w * y) * sx, 2.f * (y * z + w * x) * sy, (1.f - 2.f * (x * x + y * y)) * sz}};
+
+    for (int v = 0; v < nv; ++v) {
+      const ViewDesc& V = s.views[v];
+      // depth in the pinned float32 order (no contraction): the sort key
+      const float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(V.vm[8], px), __fmul_rn(V.vm[9], py)),
+                                           __fmul_rn(V.vm[10], pz)),
+                                 V.vm[11]);
+      const float tx = fmaf(V.vm[0], px, fmaf(V.vm[1], py, fmaf(V.vm[2], pz, V.vm[3])));
+      const float ty = fmaf(V.vm[4], px, fmaf(V.vm[5], py, fmaf(V.vm[6], pz, V.vm[7])));
+      bool vis = valid && tz > 0.2f;
+      const float itz = 1.f / tz;
+      const float limx = 1.3f * V.tan_x, limy = 1.3f * V.tan_y;
+      const float ux = fminf(fmaxf(tx * itz, -limx), limx);
+      const float uy = fminf(fmaxf(ty * itz, -limy), limy);
+      const float j00 = V.fx * itz, j02 = -V.fx * ux * itz;
+      const float j11 = V.fy * itz, j12 = -V.fy * uy * itz;
+      // T = J W (2x3), then TM = T M
+      float t0[3], t1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        t0[k] = fmaf(j00, V.vm[k], j02 * V.vm[8 + k]);
+        t1[k] = fmaf(j11, V.vm[4 + k], j12 * V.vm[8 + k]);
+      }
+      float m0[3], m1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        m0[k] = fmaf(t0[0], M[0][k], fmaf(t0[1], M[1][k], t0[2] * M[2][k]));
+        m1[k] = fmaf(t1[0], M[0][k], fmaf(t1[1], M[1][k], t1[2] * M[2][k]));
+      }
+      const float ca = fmaf(m0[0], m0[0], fmaf(m0[1], m0[1], m0[2] * m0[2])) + 0.3f;
+      const float cb = fmaf(m0[0], m1[0], fmaf(m0[1], m1[1], m0[2] * m1[2]));
+      const float cc = fmaf(m1[0], m1[0], fmaf(m1[1], m1[1], m1[2] * m1[2])) + 0.3f;
+      const float det = ca * cc - cb * cb;
+      vis = vis && det > 0.f;
+      const float mid = 0.5f * (ca + cc);
+      const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+      const float rr = ceilf(3.f * sqrtf(lam));
+      int rad = (int)fminf(rr, (float)RADIUS_MAX);
+      const float mx = fmaf(V.fx, __fdiv_rn(tx, tz), V.cx - 0.5f);
+      const float my = fmaf(V.fy, __fdiv_rn(ty, tz), V.cy - 0.5f);
+      vis = vis && rad > 0 && fabsf(mx) < 1e7f && fabsf(my) < 1e7f;
+      if (vis) {
+        const int x0 = (int)floorf(mx), y0 = (int)floorf(my);
+        vis = (x0 + rad >= 0) && (x0 - rad <= V.W - 1) && (y0 + rad >= 0) && (y0 - rad <= V.H - 1);
+      }
+      if (!vis) rad = 0;
+      // Cholesky of the conic: l0 = sqrt(c/det), l1 = -b / sqrt(c det), l2 = 1/sqrt(c)
+      const float rc = rsqrtf(cc), rd = rsqrtf(det);
+      const float l0 = cc * rc * rd * CHOL_PRESCALE;
+      const float l1 = -cb * rc * rd * CHOL_PRESCALE;
+      const float l2 = rc * CHOL_PRESCALE;
+      const uint32_t key = __float_as_uint(tz);
+      const long long o = (long long)v * a.n + gi;
+      const uint32_t ballot = __ballot_sync(0xffffffffu, vis);
+      if (vis) {
+        vbits |= 1ull << v;
+        a.bin[o] = make_uint4(__float_as_uint(mx), __float_as_uint(my), (uint32_t)rad, key);
+        float4* r = a.rec + o * 3;
+        r[0] = make_float4(mx, my, l0, l1);
+        r[1] = make_float4(l2, op, __int_as_float(rad), __uint_as_float(key));
+      }
+      if (a.splats && valid) {
         hg_splat sp;
-        float idet = 1.f / det;
+        const float idet = 1.f / det;
         sp.mean2d[0] = mx;
         sp.mean2d[1] = my;
         sp.conic[0] = cc * idet;
         sp.conic[1] = -cb * idet;
         sp.conic[2] = ca * idet;
         sp.opacity = op;
-        sp.rgb[0] = cr;
-        sp.rgb[1] = cg;
-        sp.rgb[2] = cbl;
+        sp.rgb[0] = sp.rgb[1] = sp.rgb[2] = 0.f;  // the colour pass fills these
         sp.depth_key = key;
         sp.radius = rad;
         sp.depth = tz;
         a.splats[o] = sp;
       }
+      if (lane == 0) {
+        const long long word = (long long)v * a.vis_words + (gi >> 5);
+        if (i0 + (tid & ~31) < a.n) a.vis[word] = ballot;
+        if (ballot) atomicAdd(&a.fc->n_visible, __popc(ballot));
+      }
     }
-    if (lane == 0) {
-      long long word = (long long)v * a.vis_words + (gi >> 5);
-      if (i0 + (tid & ~31) < a.n) a.vis[word] = ballot;
-      if (ballot) atomicAdd(&a.fc->n_visible, __popc(ballot));
+  }
+
+  // view-dependent colour: max(0, SH(d) + 0.5), d = normalise(mean - campos)
+  const float* sh_g = s.sh + tid * K * 3;
+  const bool keep = a.splats != nullptr && valid;
+  for (int v0 = 0; v0 < nv; v0 += VG) {
+    const int g = min(VG, nv - v0);
+    const bool any = (vbits >> v0) & ((1ull << g) - 1ull);
+    if (!__any_sync(0xffffffffu, any || keep)) continue;
+    float d[VG][3], acc[VG][3];
+#pragma unroll
+    for (int v = 0; v < VG; ++v) {
+      const ViewDesc& V = s.views[v0 + (v < g ? v : 0)];
+      const float dx = px - V.campos[0], dy = py - V.campos[1], dz = pz - V.campos[2];
+      const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+      d[v][0] = dx * dn;
+      d[v][1] = dy * dn;
+      d[v][2] = dz * dn;
+      acc[v][0] = acc[v][1] = acc[v][2] = 0.f;
+    }
+    sh_band<0, VG>(sh_g, d, acc, g);
+    if (DEG >= 1) sh_band<1, VG>(sh_g, d, acc, g);
+    if (DEG >= 2) sh_band<2, VG>(sh_g, d, acc, g);
+    if (DEG >= 3) sh_band<3, VG>(sh_g, d, acc, g);
+#pragma unroll
+    for (int v = 0; v < VG; ++v) {
+      if (v >= g) break;
+      const float cr = fmaxf(acc[v][0] + 0.5f, 0.f);
+      const float cg = fmaxf(acc[v][1] + 0.5f, 0.f);
+      const float cbl = fmaxf(acc[v][2] + 0.5f, 0.f);
+      const long long o = (long long)(v0 + v) * a.n + gi;
+      if ((vbits >> (v0 + v)) & 1ull) a.rec[o * 3 + 2] = make_float4(cr, cg, cbl, blend_level(op));
+      if (keep) {
+        a.splats[o].rgb[0] = cr;
+        a.splats[o].rgb[1] = cg;
+        a.splats[o].rgb[2] = cbl;
+      }
     }
   }
 }
@@ -272,7 +319,7 @@ __global__ void k_splats_to_records(const hg_splat* sp, long long total, long lo
     bin[o] = make_uint4(__float_as_uint(s.mean2d[0]), __float_as_uint(s.mean2d[1]), (uint32_t)rad, s.depth_key);
     rec[o * 3 + 0] = make_float4(s.mean2d[0], s.mean2d[1], l0 * CHOL_PRESCALE, l1 * CHOL_PRESCALE);
     rec[o * 3 + 1] = make_float4(l2 * CHOL_PRESCALE, s.opacity, __int_as_float(rad), __uint_as_float(s.depth_key));
-    rec[o * 3 + 2] = make_float4(s.rgb[0], s.rgb[1], s.rgb[2], s.depth);
+    rec[o * 3 + 2] = make_float4(s.rgb[0], s.rgb[1], s.rgb[2], blend_level(s.opacity));
   }
   // visibility words: the splat array is [V][n]; a warp's 32 entries map to
   // one word only when n is a multiple of 32, so set bits atomically.
@@ -286,7 +333,7 @@ __global__ void k_splats_to_records(const hg_splat* sp, long long total, long lo
 
 template <int DEG>
 static cudaError_t launch_project_deg(const ProjectArgs& a, cudaStream_t st) {
-  size_t sm = sizeof(ProjSmem<DEG>);
+  size_t sm = proj_smem_bytes<DEG>(a.n_views);
   cudaError_t e = cudaFuncSetAttribute(k_project<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   long long blocks = (a.n + PROJ_THREADS - 1) / PROJ_THREADS;

@@ -92,6 +92,79 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[IPT], uint32_t 
   }
 }
 
+// Lanes holding the same 8-bit digit as this lane (eight ballots).
+__device__ __forceinline__ uint32_t digit_peers8(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+// block_rank over the first `rows` item slots of every thread (rows <= IPT,
+// the same in every warp), every digit in [0, 256).  Warp w holds elements
+// [w * 32 * rows, (w + 1) * 32 * rows), slot i of lane l being element
+// w * 32 * rows + i * 32 + l.
+template <int NT, int IPT>
+__device__ __forceinline__ void block_rank_rows(const uint32_t (&dig)[IPT], uint32_t (&pos)[IPT], RankSmem<NT>& s,
+                                                int rows) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = lane; j < 256; j += 32) s.hist[warp][j] = 0;
+  __syncwarp();
+  const uint32_t lt = lanemask_lt();
+  uint32_t rk[IPT];
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    if (i >= rows) break;
+    const uint32_t d = dig[i];
+    const uint32_t peers = digit_peers8(d);
+    const uint32_t leader = __ffs(peers) - 1;
+    const uint32_t base = s.hist[warp][d];
+    __syncwarp();
+    if (lane == (int)leader) s.hist[warp][d] = base + __popc(peers);
+    __syncwarp();
+    rk[i] = base + __popc(peers & lt);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += NT) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      uint32_t c = s.hist[w][d];
+      s.hist[w][d] = run;
+      run += c;
+    }
+    s.digit_count[d] = run;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = s.digit_count[lane * 8 + k];
+      sum += v[k];
+    }
+    uint32_t inc = warp_incl_scan(sum);
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      s.digit_start[lane * 8 + k] = run;
+      run += v[k];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    if (i >= rows) break;
+    const uint32_t d = dig[i];
+    pos[i] = s.digit_start[d] + s.hist[warp][d] + rk[i];
+  }
+}
+
 template <int IPT>
 __device__ __forceinline__ int striped_index(int i) {
   return (threadIdx.x >> 5) * 32 * IPT + i * 32 + (threadIdx.x & 31);

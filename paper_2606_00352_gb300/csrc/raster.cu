@@ -40,12 +40,12 @@ template <int MW, int MH, bool SAVE>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* s_rec = reinterpret_cast<float4*>(smem_raw);                       // [cap][3]
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);   // [cap/32][M]
+  float4* s_rec = reinterpret_cast<float4*>(smem_raw);                       // [cap + 1][3]
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)(cap + 1) * 3);  // [cap/32][M]
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
-  __shared__ uint16_t s_ring[RW * RING];
+  __shared__ __align__(16) uint16_t s_ring[RW * RING];
   __shared__ unsigned long long s_active, s_blended;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -53,6 +53,8 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     mbar_init(&bar, 1);
     mbar_fence_init();
   }
+  // null record (blend level -1: never passes the blend test) for padding
+  if (tid < 3) s_rec[(size_t)cap * 3 + tid] = make_float4(0.f, 0.f, 0.f, tid == 2 ? -1.f : 0.f);
   __syncthreads();
   if (read_status(a.fc)) return;
   const uint32_t n_units = a.fc->n_batches;
@@ -99,26 +101,34 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     build_tile_masks<MW, MH>(s_rec, s_mask, count, V, mtx0, mty0, RW);
     __syncthreads();
 
-    // tile work queue (warp 0)
+    // tile work queue (warp 0), longest first: a tile's work is about the
+    // number of gaussians in its mask, and claiming the longest tiles first
+    // shortens the wait of the other warps at the end of the unit
     if (warp == 0) {
+      constexpr int H = (M + 31) / 32;
+      uint32_t key[H];
       unsigned long long act = 0;
-      int qn = 0;
 #pragma unroll
-      for (int h = 0; h < (M + 31) / 32; ++h) {
+      for (int h = 0; h < H; ++h) {
         const int t = h * 32 + lane;
-        bool hit = false;
-        if (t < M) {
-          uint32_t o = 0;
-          for (int k = 0; k < K; ++k) o |= s_mask[k * M + t];
-          hit = o != 0;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-        if (hit) s_q[qn + __popc(bal & lanemask_lt())] = (uint8_t)t;
-        qn += __popc(bal);
-        act |= (unsigned long long)bal << (h * 32);
+        uint32_t n = 0;
+        if (t < M)
+          for (int k = 0; k < K; ++k) n += __popc(s_mask[k * M + t]);
+        // key: count above, tile index below (distinct keys, ties by index)
+        key[h] = n ? ((n << 6) | (uint32_t)(63 - t)) : 0u;
+        act |= (unsigned long long)__ballot_sync(0xffffffffu, n != 0) << (h * 32);
+      }
+      // rank of each active tile among all active tiles by descending key
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        uint32_t rk = 0;
+#pragma unroll
+        for (int h2 = 0; h2 < H; ++h2)
+          for (int src = 0; src < 32; ++src) rk += __shfl_sync(0xffffffffu, key[h2], src) > key[h];
+        if (key[h]) s_q[rk] = (uint8_t)(h * 32 + lane);
       }
       if (lane == 0) {
-        s_qn = (uint32_t)qn;
+        s_qn = (uint32_t)__popcll(act);
         s_active = act;
       }
     }
@@ -169,32 +179,50 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       pixel_init(p0, in0);
       pixel_init(p1, in1);
       if (chained && __ldcg(&a.tile_rank[gt]) != 0) {
-        const float4 s0 = __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane]);
-        const float4 s1 = __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane + 32]);
-        p0.r = s0.x, p0.g = s0.y, p0.b = s0.z, p0.T = fabsf(s0.w);
-        p1.r = s1.x, p1.g = s1.y, p1.b = s1.z, p1.T = fabsf(s1.w);
-        p0.stopped = signbit(s0.w);
-        p1.stopped = signbit(s1.w);
-        p0.done = p0.done || p0.stopped;
-        p1.done = p1.done || p1.stopped;
+        pixel_load(p0, in0, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane]));
+        pixel_load(p1, in1, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane + 32]));
       }
       // every pixel already stopped in an earlier batch: nothing to blend
-      if (__all_sync(0xffffffffu, p0.done && p1.done)) continue;
+      if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) continue;
       if (lane == 0) atomicOr(&s_blended, 1ull << t);
       if (SAVE) {
         float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
-        pre[lane] = make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T);
-        pre[lane + 32] = make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T);
+        pre[lane] = pixel_state(p0);
+        pre[lane + 32] = pixel_state(p1);
       }
-      uint32_t stop0 = count, stop1 = count;
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
       uint32_t n_blend = 0;
       // scheduling buffer (Alg. 2): indices of the tile's gaussians from
       // successive mini-batches accumulate in a per-warp ring and are
-      // drained DRAIN at a time
+      // drained DRAIN at a time.  Drains start at multiples of DRAIN, so
+      // every group of 8 indices is one aligned 16-byte shared load; the
+      // last drain is padded to a multiple of 8 with the null record (index
+      // cap), which never passes the blend test.
       uint16_t* ring = s_ring + warp * RING;
+      const uint4* ring4 = reinterpret_cast<const uint4*>(ring);
       uint32_t head = 0, tail = 0;
       bool all_done = false;
+      auto drain = [&](uint32_t n) {
+        for (uint32_t i0 = 0; i0 < n; i0 += 8) {
+          const uint4 q = ring4[((head + i0) & (RING - 1)) >> 3];
+          const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const uint32_t j = (w4[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
+            const float ub = g0.z * (fpx - g0.x);
+            blend(p0, ub, fpy - g0.y, g0, g1, g2);
+            blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+          }
+          n_blend += 8;
+          if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
+            all_done = true;
+            break;
+          }
+        }
+        head += n;
+        __syncwarp();
+      };
       for (int k = 0; k < K && !all_done; ++k) {
         const uint32_t m = s_mask[k * M + t];
         if (m) {
@@ -202,48 +230,24 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           tail += __popc(m);
           __syncwarp();
         }
-        while (tail - head >= DRAIN || (k == K - 1 && tail > head)) {
-          const uint32_t n = min(tail - head, (uint32_t)DRAIN);
-          for (uint32_t i = 0; i < n; ++i) {
-            const uint32_t j = ring[(head + i) & (RING - 1)];
-            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
-            const float ub = g0.z * (fpx - g0.x);
-            const bool st0 = blend_bf(p0, ub, fpy - g0.y, g0, g1, g2);
-            const bool st1 = blend_bf(p1, ub, fpy1 - g0.y, g0, g1, g2);
-            if (SAVE) {
-              stop0 = st0 ? j : stop0;
-              stop1 = st1 ? j : stop1;
-            }
-            if ((i & 7) == 7 && __all_sync(0xffffffffu, p0.done && p1.done)) {
-              all_done = true;
-              n_blend += i + 1;
-              break;
-            }
-          }
-          if (!all_done) n_blend += n;
-          head += n;
-          __syncwarp();
-          if (all_done || __all_sync(0xffffffffu, p0.done && p1.done)) {
-            all_done = true;
-            break;
-          }
-        }
+        if (tail - head >= DRAIN) drain(DRAIN);
+      }
+      if (!all_done && tail > head) {
+        const uint32_t n8 = (tail - head + 7u) & ~7u;
+        if (lane < n8 - (tail - head)) ring[(tail + lane) & (RING - 1)] = (uint16_t)cap;
+        __syncwarp();
+        drain(n8);
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
       if (chained) {
         float4* st = a.tile_state + (size_t)gt * TILE_PX;
-        st[lane] = make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T);
-        st[lane + 32] = make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T);
+        st[lane] = pixel_state(p0);
+        st[lane + 32] = pixel_state(p1);
         if (lane == 0) a.tile_rank[gt] = rank + 1;
       } else {
         float4* out = a.partial + ((size_t)r * M + t) * TILE_PX;
-        st_cs(out + lane, make_float4(p0.r, p0.g, p0.b, p0.stopped ? -p0.T : p0.T));
-        st_cs(out + lane + 32, make_float4(p1.r, p1.g, p1.b, p1.stopped ? -p1.T : p1.T));
-      }
-      if (SAVE && a.stop_pos) {
-        uint16_t* sp = a.stop_pos + ((size_t)r * M + t) * TILE_PX;
-        sp[lane] = (uint16_t)stop0;
-        sp[lane + 32] = (uint16_t)stop1;
+        st_cs(out + lane, pixel_state(p0));
+        st_cs(out + lane + 32, pixel_state(p1));
       }
     }
     // publish: the tile states are visible before the chain advances
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 template <int MW, int MH, bool SAVE>
 cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) {
   constexpr int M = MW * MH;
-  const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 4;
+  const size_t sm = (size_t)(cap + 1) * 48 + (size_t)((cap + 31) / 32) * M * 4;
   cudaError_t e =
       cudaFuncSetAttribute(k_raster<MW, MH, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -287,7 +291,7 @@ cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) 
 
 template <int MW, int MH>
 cudaError_t launch_raster_shape(const RasterArgs& a, int cap, cudaStream_t st) {
-  return (a.stop_pos || a.prefix) ? launch_raster_kernel<MW, MH, true>(a, cap, st)
+  return a.prefix ? launch_raster_kernel<MW, MH, true>(a, cap, st)
                                   : launch_raster_kernel<MW, MH, false>(a, cap, st);
 }
 

@@ -1,8 +1,7 @@
 // Segmented depth sort (Sec. 3.3, 4.4).  Every (view, macro-tile) segment of
 // (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
 //   * segments of <= 8K pairs: one CTA sorts the segment in shared memory
-//     (tiers <= 1K / 4K / 8K pairs), skipping digit passes whose byte is
-//     constant over the segment;
+//     (tiers <= 1K / 4K / 8K pairs), over the digits of (key - min key);
 //   * larger segments: a segment-local onesweep (one kernel per 8-bit digit
 //     pass, decoupled look-back across the segment's tiles, tiles claimed in
 //     order through an atomic counter so every awaited predecessor is
@@ -41,9 +40,13 @@ __device__ __forceinline__ void sort_run_by_val(uint32_t* vals, int a, int b) {
   }
 }
 
+// One CTA per segment (grid-stride over the tier's list).  The segment's n
+// pairs are spread evenly over the warps (rows = ceil(n / NT) item slots per
+// thread), the tail of the last rows padded with key 0xffffffff and digit
+// 255 so that padding always ranks after the real pairs; the digit passes
+// cover the bits of (key - min key), the only bits that order the segment.
 template <int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
-  constexpr int CAP = NT * IPT;
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<NT, IPT>& s = *reinterpret_cast<BlockSortSmem<NT, IPT>*>(smem_raw);
@@ -55,52 +58,55 @@ __global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
     const uint32_t seg = list[idx];
     const uint32_t start = a.seg_off[seg];
     const int n = (int)(a.seg_off[seg + 1] - start);
-    uint32_t orv = 0, andv = 0xffffffffu;
-    for (int j = tid; j < CAP; j += NT) {
+    const int rows = (n + NT - 1) / NT;  // <= IPT for the segments of this tier
+    const int used = rows * NT;
+    uint32_t kmin = 0xffffffffu, kmax = 0;
+    for (int j = tid; j < used; j += NT) {
       uint32_t k = 0xffffffffu, v = 0xffffffffu;
       if (j < n) {
         k = a.keys[start + j];
         v = a.vals[start + j];
-        orv |= k;
-        andv &= k;
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
       }
       s.keys[j] = k;
       s.vals[j] = v;
     }
-    // bits that vary over the segment's keys
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      orv |= __shfl_xor_sync(0xffffffffu, orv, o);
-      andv &= __shfl_xor_sync(0xffffffffu, andv, o);
+      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
     if (lane == 0) {
-      s.red[0][warp] = orv;
-      s.red[1][warp] = andv;
+      s.red[0][warp] = kmin;
+      s.red[1][warp] = kmax;
     }
     __syncthreads();
-    orv = 0;
-    andv = 0xffffffffu;
+    kmin = 0xffffffffu;
+    kmax = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-      orv |= s.red[0][w];
-      andv &= s.red[1][w];
+      kmin = min(kmin, s.red[0][w]);
+      kmax = max(kmax, s.red[1][w]);
     }
-    const uint32_t vary = orv ^ andv;
-    for (int pass = 0; pass < 4; ++pass) {
+    const uint32_t span = kmax - kmin;
+    const int passes = span ? (32 - __clz(span) + 7) / 8 : 0;
+    for (int pass = 0; pass < passes; ++pass) {
       const int shift = 8 * pass;
-      if (((vary >> shift) & 0xffu) == 0) continue;
       uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
-        int e = striped_index<IPT>(i);
+        if (i >= rows) break;
+        const int e = warp * 32 * rows + i * 32 + lane;
         k[i] = s.keys[e];
         v[i] = s.vals[e];
-        d[i] = (k[i] >> shift) & 0xffu;
+        d[i] = e < n ? ((k[i] - kmin) >> shift) & 0xffu : 0xffu;
       }
-      block_rank<NT, IPT>(d, p, s.rank);
+      block_rank_rows<NT, IPT>(d, p, s.rank, rows);
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
+        if (i >= rows) break;
         s.keys[p[i]] = k[i];
         s.vals[p[i]] = v[i];
       }
