@@ -13,6 +13,28 @@ clamped to the grid (same for y), Bx the tile or macro-tile width in pixels.
 It contains every pixel of the q <= 9 support (a supported pixel x satisfies
 x0 - r <= x <= x0 + r).
 
+Ellipse test (Sec. 3.2 per-row ellipse scan at macro granularity with an
+opacity-aware threshold, Sec. 4.3).  The paper gives no formula; reading: a
+gaussian is paired with a macro-tile of its rectangle when the ellipse
+    (L0 dx + L1 dy)^2 + (L2 dy)^2 <= E_bin
+(L the Cholesky factors of the conic prescaled by sqrt(log2(e) / 2), so the
+left side is q log2(e) / 2) meets the pixel centres of the tile, evaluated
+per macro row band in float32 with a fixed operation order and fixed margins
+so that it is reproducible bit for bit:
+    E_bin  = min(9 log2(e) / 2, lb(255 o)) + 2^-12, where lb is an upper bound
+             of log2 from frexp (z = m 2^k, m in [0.5, 1)):
+             lb(z) = k + (B m + A), A = -475/256, B = 123/64, a line above
+             log2(m) on [0.5, 1] (log2 m <= B m + A - 0.00098; gap <= 0.105)
+    band   rows [ya, yb] of the macro row; dy range [ya - my, yb - my]
+           clipped to +-(hy (1 + 2^-10) + 2^-6), hy = sqrt(E) / L2
+    x span the extremes of (-L1 dy -+ sqrt(E - (L2 dy)^2)) / L0 over the dy
+           range (at its ends or at dy = -+L1 sqrt(E) / (L2 sqrt(L1^2 + L2^2))),
+           widened by 2^-6 + 2^-10 |offset| pixels
+    cols   [floor(ceil(xl) / Bx), floor(floor(xr) / Bx)] within the rectangle
+It is conservative for the blend test (q <= 9 and alpha >= 1/255, i.e.
+q log2(e) / 2 <= min(9 log2(e) / 2, log2(255 o))): the margins cover float32
+rounding.  Gaussians with degenerate factors keep their whole rectangle.
+
 Segments (Sec. 3.3): one per (view, macro-tile); the segment id is
 view * N_M + my * gx + mx.  Order inside a segment: ascending (key, id)
 (reading: the paper sorts by the 32-bit depth key only and is silent on ties;
@@ -47,28 +69,139 @@ def rect_ranges(mx32, my32, radius, width, height, bw, bh):
     return tx0, tx1, ty0, ty1, cells, gw, gh
 
 
-def bin_pairs(mx32, my32, radius, key, width, height, bw, bh, seg_base: int = 0):
-    """Unordered (segment, key, id) pairs of one view."""
+F32 = np.float32
+ELL_A = F32(-475.0 / 256.0)
+ELL_B = F32(123.0 / 64.0)
+ELL_MARGIN_E = F32(2.0 ** -12)
+ELL_PAD = F32(2.0 ** -6)
+ELL_REL = F32(2.0 ** -10)
+SUPPORT_E = F32(4.5 * np.log2(np.e))        # q = 9 in units of q log2(e) / 2
+PRESCALE = F32(np.sqrt(np.log2(np.e) / 2.0))
+
+
+def log2_upper(z32):
+    """lb(z) >= log2(z) for float32 z > 0 (see the module docstring)."""
+    z = np.asarray(z32, F32)
+    m, k = np.frexp(z)
+    return k.astype(F32) + (ELL_B * m.astype(F32) + ELL_A)
+
+
+def ellipse_level(o32):
+    """E_bin of the ellipse test for float32 opacities."""
+    z = F32(255.0) * np.asarray(o32, F32)
+    return np.minimum(SUPPORT_E, log2_upper(z)) + ELL_MARGIN_E
+
+
+def cholesky_from_conic(conic32):
+    """Prescaled Cholesky factors (L0, L1, L2) of float32 conics (A, B, C),
+    q = A dx^2 + 2 B dx dy + C dy^2 = (l0 dx + l1 dy)^2 + (l2 dy)^2:
+    l0 = sqrt(A), l1 = B / l0, l2 = sqrt(C - l1^2), each op rounded to float32."""
+    c = np.asarray(conic32, F32)
+    l0 = np.sqrt(np.maximum(c[:, 0], F32(0)))
+    safe = np.where(l0 > 0, l0, F32(1))
+    l1 = np.where(l0 > 0, c[:, 1] / safe, F32(0)).astype(F32)
+    l2 = np.sqrt(np.maximum(c[:, 2] - l1 * l1, F32(0)))
+    return l0 * PRESCALE, l1 * PRESCALE, l2 * PRESCALE
+
+
+def ellipse_span(mx, my, L0, L1, L2, E, ya, yb):
+    """x span [xl, xr] (pixel-centre coordinates, widened) of the ellipse
+    over the rows [ya, yb] (float32 arrays, one entry per (gaussian, band)).
+    Returns (xl, xr, meet, ok): meet = False when the band misses the
+    ellipse, ok = False for degenerate factors."""
+    mx, my, L0, L1, L2, E = (np.asarray(v, F32) for v in (mx, my, L0, L1, L2, E))
+    ya, yb = np.asarray(ya, F32), np.asarray(yb, F32)
+    ok = (L0 > 0) & (L2 > 0)
+    L0s = np.where(ok, L0, F32(1))
+    L2s = np.where(ok, L2, F32(1))
+    live = E > 0
+    sE = np.sqrt(np.maximum(E, F32(0)))
+    hy = sE / L2s
+    hyw = hy * F32(1.0 + 2.0 ** -10) + ELL_PAD
+    a = np.maximum(ya - my, -hyw)
+    b = np.minimum(yb - my, hyw)
+    meet = live & (a <= b)
+
+    def half(dy):
+        t = L2s * dy
+        return np.sqrt(np.maximum(F32(0), E - t * t))
+
+    def xlo(dy):
+        return (-L1 * dy - half(dy)) / L0s
+
+    def xhi(dy):
+        return (-L1 * dy + half(dy)) / L0s
+
+    lo = np.minimum(xlo(a), xlo(b))
+    hi = np.maximum(xhi(a), xhi(b))
+    nrm = np.sqrt(L1 * L1 + L2s * L2s)
+    dyl = (L1 * sE) / (L2s * nrm)
+    lo = np.where((dyl >= a) & (dyl <= b), np.minimum(lo, xlo(dyl)), lo)
+    hi = np.where((-dyl >= a) & (-dyl <= b), np.maximum(hi, xhi(-dyl)), hi)
+    xl = (mx + lo) - (np.abs(lo) * ELL_REL + ELL_PAD)
+    xr = (mx + hi) + (np.abs(hi) * ELL_REL + ELL_PAD)
+    return xl, xr, meet, ok
+
+
+def ellipse_cols(mx, my, L0, L1, L2, E, ya, yb, bw):
+    """Macro columns [c0, c1] where the ellipse meets the row band [ya, yb];
+    c0 > c1 when it misses.  Returns (c0, c1, ok)."""
+    xl, xr, meet, ok = ellipse_span(mx, my, L0, L1, L2, E, ya, yb)
+    with np.errstate(invalid="ignore"):
+        c0 = np.floor_divide(np.ceil(np.where(meet, xl, 0)).astype(np.int64), bw)
+        c1 = np.floor_divide(np.floor(np.where(meet, xr, 0)).astype(np.int64), bw)
+    c1 = np.where(meet, c1, c0 - 1)
+    return c0, c1, ok
+
+
+def _cells_from_rows(g, row, c0, c1, gw):
+    """Expand (gaussian, macro row, [c0, c1]) into (gaussian, segment)."""
+    n = np.maximum(c1 - c0 + 1, 0)
+    ids = np.repeat(g, n)
+    k = np.arange(int(n.sum()), dtype=np.int64) - np.repeat(np.cumsum(n) - n, n)
+    seg = np.repeat(row, n) * gw + np.repeat(c0, n) + k
+    return ids, seg
+
+
+def bin_pairs(mx32, my32, radius, key, width, height, bw, bh, seg_base: int = 0, ellipse=None):
+    """Unordered (segment, key, id) pairs of one view.  ellipse = (L0, L1,
+    L2, o) float32 arrays selects the ellipse test, else the rectangle."""
     tx0, tx1, ty0, ty1, cells, gw, gh = rect_ranges(mx32, my32, radius, width, height, bw, bh)
-    ids = np.repeat(np.arange(len(cells), dtype=np.int64), cells)
-    k = np.arange(int(cells.sum()), dtype=np.int64) - np.repeat(np.cumsum(cells) - cells, cells)
-    nx = np.repeat(tx1 - tx0 + 1, cells)
-    seg = (np.repeat(ty0, cells) + k // np.maximum(nx, 1)) * gw + np.repeat(tx0, cells) + k % np.maximum(nx, 1)
+    if ellipse is None:
+        ids = np.repeat(np.arange(len(cells), dtype=np.int64), cells)
+        k = np.arange(int(cells.sum()), dtype=np.int64) - np.repeat(np.cumsum(cells) - cells, cells)
+        nx = np.repeat(tx1 - tx0 + 1, cells)
+        seg = (np.repeat(ty0, cells) + k // np.maximum(nx, 1)) * gw + np.repeat(tx0, cells) + k % np.maximum(nx, 1)
+        return seg + seg_base, np.asarray(key, np.uint32)[ids], ids, gw * gh
+    L0, L1, L2, o = (np.asarray(v, F32) for v in ellipse)
+    ny = np.where(cells > 0, ty1 - ty0 + 1, 0)
+    g = np.repeat(np.arange(len(cells), dtype=np.int64), ny)
+    row = np.repeat(ty0, ny) + (np.arange(int(ny.sum()), dtype=np.int64) - np.repeat(np.cumsum(ny) - ny, ny))
+    ya = (row * bh).astype(F32)
+    yb = (row * bh + bh - 1).astype(F32)
+    E = ellipse_level(o)[g]
+    c0, c1, ok = ellipse_cols(np.asarray(mx32, F32)[g], np.asarray(my32, F32)[g], L0[g], L1[g], L2[g], E, ya, yb,
+                              bw)
+    c0 = np.where(ok, np.maximum(c0, tx0[g]), tx0[g])
+    c1 = np.where(ok, np.minimum(c1, tx1[g]), tx1[g])
+    ids, seg = _cells_from_rows(g, row, c0, c1, gw)
     return seg + seg_base, np.asarray(key, np.uint32)[ids], ids, gw * gh
 
 
 def segments(views, width_height, bw, bh):
     """Segmented, sorted pair list over several views.
 
-    views: list of (mx32, my32, radius, key) tuples (one per view, all with
-    the same gaussian count); width_height: list of (W, H) per view.
+    views: list of (mx32, my32, radius, key) tuples, or (mx32, my32,
+    radius, key, (L0, L1, L2, o)) for the ellipse test (one per view, all
+    with the same gaussian count); width_height: list of (W, H) per view.
     Returns dict with seg_off [S+1] (int64), keys [P] uint32, ids [P] int64,
     n_macro per view and the segment base per view.
     """
     segs, keys, ids, bases, nms = [], [], [], [], []
     base = 0
-    for (mx, my, r, key), (w, h) in zip(views, width_height):
-        s, k, i, nm = bin_pairs(mx, my, r, key, w, h, bw, bh, base)
+    for vw, (w, h) in zip(views, width_height):
+        mx, my, r, key = vw[:4]
+        s, k, i, nm = bin_pairs(mx, my, r, key, w, h, bw, bh, base, ellipse=vw[4] if len(vw) > 4 else None)
         segs.append(s), keys.append(k), ids.append(i), bases.append(base), nms.append(nm)
         base += nm
     seg = np.concatenate(segs) if segs else np.zeros(0, np.int64)

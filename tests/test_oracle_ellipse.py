@@ -1,0 +1,163 @@
+"""Pins of the oracle's ellipse binning test (macro-tile granularity,
+opacity-aware level, Sec. 3.2 / 4.3), against the mathematics it must
+satisfy: the log2 bound, the Cholesky factorisation of the conic, exact
+ellipse extents found by brute force, coverage of every pixel that passes
+the float64 blend test, and the rectangle it refines."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2606_00352_gb300.scenes import tiny_workload
+from oracle import binning as BN
+from oracle import composite as C
+from oracle import project as P
+
+from test_oracle_pins import _tiny_random
+
+F32 = np.float32
+
+
+def test_log2_upper_bound():
+    g = np.random.default_rng(0)
+    z = np.concatenate([2.0 ** np.arange(-20, 21), g.uniform(1e-6, 1e6, 20000), g.uniform(0.5, 2.0, 20000)])
+    z = z.astype(F32)
+    lb = BN.log2_upper(z).astype(np.float64)
+    ex = np.log2(z.astype(np.float64))
+    assert np.all(lb >= ex)
+    assert np.max(lb - ex) <= 0.11
+    # powers of two: m = 1/2, lb = k + (B / 2 + A) = log2(z) + 0.10546875
+    p2 = (2.0 ** np.arange(-10, 11)).astype(F32)
+    np.testing.assert_array_equal(BN.log2_upper(p2).astype(np.float64) - np.log2(p2.astype(np.float64)),
+                                  0.10546875)
+
+
+def test_level_covers_blend_threshold():
+    """E_bin >= min(9 log2(e) / 2, log2(255 o)): the blend test (q <= 9 and
+    alpha >= 1/255) never passes outside the level set."""
+    g = np.random.default_rng(1)
+    o = g.uniform(1.0 / 255.0, 1.0, 50000).astype(F32)
+    e_bin = BN.ellipse_level(o).astype(np.float64)
+    exact = np.minimum(4.5 * np.log2(np.e), np.log2(255.0 * o.astype(np.float64)))
+    assert np.all(e_bin >= exact + 2.0 ** -13)
+    assert np.max(e_bin - exact) <= 0.11 + 2.0 ** -12
+    # below 1/255 nothing can pass: the level is negative
+    assert np.all(BN.ellipse_level(np.array([0.0, 1e-4, 0.0035], F32)) < 0)
+
+
+def test_cholesky_factors_reproduce_the_conic():
+    """(L0 dx + L1 dy)^2 + (L2 dy)^2 = q log2(e) / 2 for SPD conics."""
+    g = np.random.default_rng(2)
+    a = g.uniform(0.01, 5.0, 1000)
+    c = g.uniform(0.01, 5.0, 1000)
+    b = g.uniform(-0.95, 0.95, 1000) * np.sqrt(a * c)
+    conic = np.stack([a, b, c], 1).astype(F32)
+    L0, L1, L2 = (v.astype(np.float64) for v in BN.cholesky_from_conic(conic))
+    dx, dy = g.normal(0, 3, 1000), g.normal(0, 3, 1000)
+    cf = conic.astype(np.float64)
+    q = cf[:, 0] * dx * dx + 2 * cf[:, 1] * dx * dy + cf[:, 2] * dy * dy
+    e = (L0 * dx + L1 * dy) ** 2 + (L2 * dy) ** 2
+    np.testing.assert_allclose(e, q * np.log2(np.e) / 2, rtol=2e-5, atol=1e-6)
+
+
+def _brute_extent(mx, my, L0, L1, L2, E, ya, yb, n=4001):
+    """Exact min / max x of the ellipse over rows [ya, yb] by dense sampling
+    of dy plus the analytic band ends (float64)."""
+    hy = math.sqrt(E) / L2
+    a, b = max(ya - my, -hy), min(yb - my, hy)
+    if a > b:
+        return None
+    dy = np.concatenate([np.linspace(a, b, n), [a, b]])
+    h = np.sqrt(np.maximum(0.0, E - (L2 * dy) ** 2))
+    lo = (-L1 * dy - h) / L0
+    hi = (-L1 * dy + h) / L0
+    return mx + lo.min(), mx + hi.max()
+
+
+def test_span_matches_brute_force_extent():
+    """The widened span contains the exact extent of the ellipse over the
+    band and exceeds it by no more than the stated margins (a dropped term,
+    wrong sign or swapped factor in the extreme points fails this)."""
+    g = np.random.default_rng(3)
+    n = 1000
+    conic = []
+    for _ in range(n):
+        a, c = g.uniform(0.002, 0.5), g.uniform(0.002, 0.5)
+        b = g.uniform(-0.9, 0.9) * math.sqrt(a * c)
+        conic.append((a, b, c))
+    conic = np.array(conic, F32)
+    L0, L1, L2 = BN.cholesky_from_conic(conic)
+    o = g.uniform(0.01, 1.0, n).astype(F32)
+    E = BN.ellipse_level(o)
+    mx = g.uniform(-20, 120, n).astype(F32)
+    my = g.uniform(-20, 120, n).astype(F32)
+    ya = (g.integers(0, 4, n) * 32).astype(F32)
+    yb = ya + F32(31)
+    xl, xr, meet, ok = BN.ellipse_span(mx, my, L0, L1, L2, E, ya, yb)
+    checked = 0
+    for i in range(n):
+        ext = _brute_extent(float(mx[i]), float(my[i]), float(L0[i]), float(L1[i]), float(L2[i]), float(E[i]),
+                            float(ya[i]), float(yb[i]))
+        if ext is None:
+            # a band that misses the exact ellipse may still meet the widened one
+            continue
+        assert meet[i] and ok[i]
+        lo, hi = ext
+        assert xl[i] <= lo + 1e-9 and xr[i] >= hi - 1e-9
+        slack = 2.0 ** -6 + 2.0 ** -9 * max(abs(lo - float(mx[i])), abs(hi - float(mx[i]))) + 0.01
+        assert xl[i] >= lo - slack and xr[i] <= hi + slack
+        checked += 1
+    assert checked > 250
+
+
+def _workload_records(scene, cam):
+    pr = P.project(scene, cam)
+    mx, my, r, key = BN.records_f32(pr)
+    L = BN.cholesky_from_conic(pr["conic"].astype(F32))
+    o = pr["opacity"].astype(F32)
+    return pr, (mx, my, r, key), (L[0], L[1], L[2], o)
+
+
+@pytest.mark.parametrize("bw,bh", [(8, 8), (32, 32), (64, 32), (64, 64)])
+@pytest.mark.parametrize("seed", [5, 6])
+def test_ellipse_pairs_cover_blend_support(bw, bh, seed):
+    """Every pixel where the float64 blend test passes (q <= 9 and alpha >=
+    1/255) lies in a macro-tile paired with the gaussian, and the ellipse
+    pairs are a subset of the rectangle pairs."""
+    w = h = 96
+    sc, cam = _tiny_random(n=300, w=w, h=h, seed=seed)
+    pr, (mx, my, r, key), ell = _workload_records(sc, cam)
+    gw = -(-w // bw)
+    seg_e, _, ids_e, _ = BN.bin_pairs(mx, my, r, key, w, h, bw, bh, ellipse=ell)
+    seg_r, _, ids_r, _ = BN.bin_pairs(mx, my, r, key, w, h, bw, bh)
+    got = set(zip(seg_e.tolist(), ids_e.tolist()))
+    assert got <= set(zip(seg_r.tolist(), ids_r.tolist()))
+    ys, xs = np.mgrid[0:h, 0:w]
+    xs, ys = xs.ravel().astype(float), ys.ravel().astype(float)
+    need = set()
+    for i in np.nonzero(r > 0)[0]:
+        q, al = C.alpha_at(pr, np.array([i]), xs, ys)
+        hit = (q[0] <= 9.0) & (al[0] >= 1.0 / 255.0)
+        for x, y in zip(xs[hit].astype(int), ys[hit].astype(int)):
+            need.add(((y // bh) * gw + x // bw, int(i)))
+    assert need <= got
+    assert len(need) > 50
+
+
+def test_ellipse_reduces_macro_pairs():
+    scene, cams = tiny_workload()
+    pr, (mx, my, r, key), ell = _workload_records(scene, cams[0])
+    n_rect = len(BN.bin_pairs(mx, my, r, key, 256, 256, 32, 32)[0])
+    n_ell = len(BN.bin_pairs(mx, my, r, key, 256, 256, 32, 32, ellipse=ell)[0])
+    assert n_ell < n_rect
+
+
+def test_degenerate_factors_keep_the_rectangle():
+    mx = np.array([40.5], F32)
+    my = np.array([40.5], F32)
+    r = np.array([20])
+    key = np.array([1], np.uint32)
+    ell = (np.array([0.0], F32), np.array([0.0], F32), np.array([0.0], F32), np.array([0.5], F32))
+    a = BN.bin_pairs(mx, my, r, key, 128, 128, 32, 32, ellipse=ell)
+    b = BN.bin_pairs(mx, my, r, key, 128, 128, 32, 32)
+    np.testing.assert_array_equal(np.sort(a[0]), np.sort(b[0]))
