@@ -274,15 +274,20 @@ def roofline(stage_ms, stats0, n, pk, clock_mhz):
     """Roofline of the stage that takes the most time per step."""
     hbm_peak = pk["hbm_gbs"]
     K = 16
-    proj_bytes = n * (44 + 12 * K) + VIEWS * n * (16 + 48) + VIEWS * ((n + 31) // 32) * 4
+    vis = statistics.mean(s["n_visible"] for s in stats0)
+    vis_bits = VIEWS * ((n + 31) // 32) * 4
+    proj_bytes = n * (44 + 12 * K) + vis * (16 + 48) + vis_bits
     pairs = statistics.mean(s["n_pairs"] for s in stats0)
     evals = statistics.mean(s["raster_evals"] for s in stats0)
     alu_peak = 152 * FP32_LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12  # T FP32-pipe ops/s
     table = {
         "project": {"bound": "hbm", "units": proj_bytes, "peak": hbm_peak, "unit": "GB/s",
-                    "per_unit": "bytes: 236 read + 4 x 64 written + vis bits per gaussian"},
-        "partition": {"bound": "hbm", "units": VIEWS * n * 16 * 2 + pairs * 8, "peak": hbm_peak, "unit": "GB/s",
-                      "per_unit": "bytes: 16 per (view, gaussian) read by count and by fill + 8 per pair"},
+                    "per_unit": "bytes: 236 read per gaussian + 64 written per visible (view, gaussian) + "
+                                "visibility bits"},
+        "partition": {"bound": "hbm", "units": vis * 16 * 2 + vis_bits * 2 + pairs * 8, "peak": hbm_peak,
+                      "unit": "GB/s",
+                      "per_unit": "bytes: 16 per visible (view, gaussian) and the visibility bits, read by count "
+                                  "and by fill, + 8 written per pair"},
         "sort": {"bound": "hbm", "units": pairs * 16, "peak": hbm_peak, "unit": "GB/s",
                  "per_unit": "bytes: 8 read + 8 written per pair"},
         "raster": {"bound": "alu", "units": evals * RASTER_OPS_PER_EVAL, "peak": alu_peak, "unit": "Tops/s",
@@ -307,7 +312,7 @@ SERVE_RES = ((1280, 720), (1920, 1080), (3840, 2160))
 SERVE_RES_W = (0.3, 0.5, 0.2)
 
 
-def serving_run(higs, ctx, gscenes, seconds, seed=0):
+def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     """Poisson arrivals at each rate over the resident scenes; every request
     is a random orbit pose at a random resolution (weights 0.3/0.5/0.2).
     Returns one row per rate."""
@@ -315,7 +320,7 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0):
     import torch
     from paper_2606_00352_gb300 import scenes
     rng = np.random.default_rng(seed)
-    srv = higs.Server(ctx, max_inflight=4, max_views_per_launch=8, mem_budget_bytes=64 << 30)
+    srv = higs.Server(ctx, max_inflight=4, max_views_per_launch=8, mem_budget_bytes=64 << 30, opts=opts)
     sids = [srv.add_scene(g) for g in gscenes]
     pool = [torch.empty(3840 * 2160 * 3, device="cuda") for _ in range(48)]
     poses = {r: scenes.scene_orbit(N_POSES, r[0], r[1]) for r in SERVE_RES}
@@ -399,11 +404,14 @@ def gpu_arm(args):
     pk = peaks()
     tuned = None
     mw, mh = (int(x) for x in args.macro.split("x"))
-    opts = higs.Options(path=higs.PATH_HIGS, macro_w=mw, macro_h=mh, batch_cap=args.cap, flags=higs.FLAG_TIMING)
+    bin_test = higs.BIN_ELLIPSE if args.bin == "ellipse" else higs.BIN_RECT
+    opts = higs.Options(path=higs.PATH_HIGS, macro_w=mw, macro_h=mh, batch_cap=args.cap, bin_test=bin_test,
+                        flags=higs.FLAG_TIMING)
     if not args.skip_tune:
-        best, table = higs.autotune(gs, pose_batch(cams, 0, rank), higs.Options(), iters=3, stream=stream)
+        best, table = higs.autotune(gs, pose_batch(cams, 0, rank), higs.Options(bin_test=bin_test), iters=3,
+                                    stream=stream)
         opts = higs.Options(path=higs.PATH_HIGS, macro_w=best.macro_w, macro_h=best.macro_h,
-                            batch_cap=best.batch_cap, flags=higs.FLAG_TIMING)
+                            batch_cap=best.batch_cap, bin_test=bin_test, flags=higs.FLAG_TIMING)
         tuned = {"chosen": f"{best.macro_w}x{best.macro_h}/{best.batch_cap}",
                  "candidates_ms": {f"{r[0]}x{r[1]}/{r[2]}": round(r[3], 3) for r in table}}
 
@@ -434,7 +442,9 @@ def gpu_arm(args):
                                                                     sigma_range=sc_mod.CLUSTER_SIGMA,
                                                                     extent=sc_mod.EXTENT))
                  for k, n in enumerate((500_000, 2_000_000))]
-        serving = {"rows": serving_run(higs, ctx, small + [gs], seconds=1.5),
+        sopts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
+                             batch_cap=opts.batch_cap, bin_test=opts.bin_test)
+        serving = {"rows": serving_run(higs, ctx, small + [gs], seconds=1.5, opts=sopts),
                    "workload": "3 resident scenes (0.5M, 2M, 5.8M gaussians, 256 clusters, Zipf 1.4); Poisson "
                                "arrivals; random orbit pose at 1280x720 / 1920x1080 / 3840x2160 (0.3/0.5/0.2); "
                                "up to 4 launches in flight, up to 8 views per launch; latency submit -> completion"}
@@ -444,7 +454,7 @@ def gpu_arm(args):
         training = train_step_ms(higs, ctx)
 
     e2e_opts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
-                            batch_cap=opts.batch_cap)
+                            batch_cap=opts.batch_cap, bin_test=opts.bin_test)
     e2e_steps = max(3, min(args.steps, 10))
     e = time_e2e(higs, gs, cams, e2e_opts, e2e_steps, min(args.warmup, 3), rank, stream)
     e2e_t = max_over_ranks(e["seconds"], world)
@@ -462,7 +472,8 @@ def gpu_arm(args):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config() | {"macro_tile": f"{opts.macro_w}x{opts.macro_h}", "batch_cap": opts.batch_cap},
+        "config": workload_config() | {"macro_tile": f"{opts.macro_w}x{opts.macro_h}", "batch_cap": opts.batch_cap,
+                                       "bin_test": args.bin},
         "roofline": {k: v for k, v in rl[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
         | {"kernel": top, "traffic": None, "peak_source": pk["source"]},
         "stages": rl | {"merge": {"ms": round(stage_ms["merge"], 4)}},
@@ -505,6 +516,7 @@ def profile_case(args):
     path = higs.PATH_PLAIN if args.case == "1m-plain" else higs.PATH_HIGS
     mw, mh = (int(x) for x in args.macro.split("x"))
     opts = higs.Options(path=path, macro_w=mw, macro_h=mh, batch_cap=args.cap,
+                        bin_test=higs.BIN_ELLIPSE if args.bin == "ellipse" else higs.BIN_RECT,
                         flags=higs.FLAG_TIMING | (higs.FLAG_PROFILE if args.profile else 0))
     for k in range(args.warmup + args.steps):
         higs.render(gs, pose_batch(cams, k, 0), opts, state=st)
@@ -546,6 +558,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="count rasteriser phase cycles (profiling case)")
     ap.add_argument("--macro", default="8x4", choices=["4x4", "8x4", "8x8"], help="macro shape without autotuning")
     ap.add_argument("--cap", type=int, default=1024, help="batch cap B_r without autotuning")
+    ap.add_argument("--bin", default="ellipse", choices=["rect", "ellipse"], help="macro-tile binning test")
     args = ap.parse_args()
     if args.warmup < 3 and not args.oracle_steps and not args.case:
         args.warmup = 3

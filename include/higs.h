@@ -106,7 +106,14 @@ typedef struct {
 } hg_splat;
 
 enum { HG_PATH_HIGS = 0, HG_PATH_PLAIN = 1 };
-enum { HG_BIN_RECT = 0 };
+/* Gaussian-to-macro-tile test of the partitioning (Sec. 3.2, 4.3):
+   HG_BIN_RECT     the 3-sigma rectangle in integers,
+   HG_BIN_ELLIPSE  the rectangle refined per macro row band by the ellipse at
+                   the opacity-aware level of the blend test (float32 with a
+                   fixed operation order and margins; conservative, so the
+                   image is the same, with fewer pairs).
+   The plain per-tile path always uses the rectangle. */
+enum { HG_BIN_RECT = 0, HG_BIN_ELLIPSE = 1 };
 enum {
   HG_FLAG_ASYNC = 1,       /* do not synchronise or check the status word */
   HG_FLAG_TIMING = 2,      /* record per-stage CUDA events (hg_render_stats) */
@@ -123,7 +130,7 @@ typedef struct {
   int32_t macro_w;     /* render tiles per macro-tile in x: 4 or 8 (default 8) */
   int32_t macro_h;     /* render tiles per macro-tile in y: 4 or 8 (default 4) */
   int32_t batch_cap;   /* B_r, 32..2048 multiple of 32 (default 1024) */
-  int32_t bin_test;    /* HG_BIN_RECT */
+  int32_t bin_test;    /* HG_BIN_RECT or HG_BIN_ELLIPSE */
   float bg[3];         /* background colour added as C + T bg */
   int32_t save_for_backward;
   int32_t flags;       /* HG_FLAG_* */

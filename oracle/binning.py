@@ -29,11 +29,13 @@ so that it is reproducible bit for bit:
            clipped to +-(hy (1 + 2^-10) + 2^-6), hy = sqrt(E) / L2
     x span the extremes of (-L1 dy -+ sqrt(E - (L2 dy)^2)) / L0 over the dy
            range (at its ends or at dy = -+L1 sqrt(E) / (L2 sqrt(L1^2 + L2^2))),
-           widened by 2^-6 + 2^-10 |offset| pixels
+           widened by 2^-6 + 2^-10 |offset| pixels, clamped to +-2^30
     cols   [floor(ceil(xl) / Bx), floor(floor(xr) / Bx)] within the rectangle
 It is conservative for the blend test (q <= 9 and alpha >= 1/255, i.e.
 q log2(e) / 2 <= min(9 log2(e) / 2, log2(255 o))): the margins cover float32
-rounding.  Gaussians with degenerate factors keep their whole rectangle.
+rounding.  Gaussians with degenerate factors, and rectangles of one macro
+cell or of more than 64 cells (the test is stored as a 64-bit cell mask),
+keep their whole rectangle.
 
 Segments (Sec. 3.3): one per (view, macro-tile); the segment id is
 view * N_M + my * gx + mx.  Order inside a segment: ascending (key, id)
@@ -140,6 +142,10 @@ def ellipse_span(mx, my, L0, L1, L2, E, ya, yb):
     hi = np.where((-dyl >= a) & (-dyl <= b), np.maximum(hi, xhi(-dyl)), hi)
     xl = (mx + lo) - (np.abs(lo) * ELL_REL + ELL_PAD)
     xr = (mx + hi) + (np.abs(hi) * ELL_REL + ELL_PAD)
+    # far outside any image; keeps the integer conversion in range
+    lim = F32(2.0 ** 30)
+    xl = np.minimum(np.maximum(xl, -lim), lim)
+    xr = np.minimum(np.maximum(xr, -lim), lim)
     return xl, xr, meet, ok
 
 
@@ -174,6 +180,7 @@ def bin_pairs(mx32, my32, radius, key, width, height, bw, bh, seg_base: int = 0,
         seg = (np.repeat(ty0, cells) + k // np.maximum(nx, 1)) * gw + np.repeat(tx0, cells) + k % np.maximum(nx, 1)
         return seg + seg_base, np.asarray(key, np.uint32)[ids], ids, gw * gh
     L0, L1, L2, o = (np.asarray(v, F32) for v in ellipse)
+    refine = (cells > 1) & (cells <= 64)
     ny = np.where(cells > 0, ty1 - ty0 + 1, 0)
     g = np.repeat(np.arange(len(cells), dtype=np.int64), ny)
     row = np.repeat(ty0, ny) + (np.arange(int(ny.sum()), dtype=np.int64) - np.repeat(np.cumsum(ny) - ny, ny))
@@ -182,8 +189,9 @@ def bin_pairs(mx32, my32, radius, key, width, height, bw, bh, seg_base: int = 0,
     E = ellipse_level(o)[g]
     c0, c1, ok = ellipse_cols(np.asarray(mx32, F32)[g], np.asarray(my32, F32)[g], L0[g], L1[g], L2[g], E, ya, yb,
                               bw)
-    c0 = np.where(ok, np.maximum(c0, tx0[g]), tx0[g])
-    c1 = np.where(ok, np.minimum(c1, tx1[g]), tx1[g])
+    use = ok & refine[g]
+    c0 = np.where(use, np.maximum(c0, tx0[g]), tx0[g])
+    c1 = np.where(use, np.minimum(c1, tx1[g]), tx1[g])
     ids, seg = _cells_from_rows(g, row, c0, c1, gw)
     return seg + seg_base, np.asarray(key, np.uint32)[ids], ids, gw * gh
 

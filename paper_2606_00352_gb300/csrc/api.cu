@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "binning.cuh"
 #include "internal.h"
 
 using namespace hg;
@@ -241,7 +242,7 @@ static bool valid_opts(const hg_render_opts* o, std::string& why) {
                         (o->macro_w == 8 && o->macro_h == 8);
   if (!shape_ok) return why = "macro shape must be 8x4, 4x4 or 8x8", false;
   if (o->batch_cap < 32 || o->batch_cap > 2048 || (o->batch_cap & 31)) return why = "batch_cap", false;
-  if (o->bin_test != HG_BIN_RECT) return why = "bin_test", false;
+  if (o->bin_test != HG_BIN_RECT && o->bin_test != HG_BIN_ELLIPSE) return why = "bin_test", false;
   return true;
 }
 
@@ -329,6 +330,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   ENS(B_FC, sizeof(FrameCounters));
   ENS(B_VIEWS, sizeof(ViewDesc) * MAX_VIEWS);
   ENS(B_BIN, sizeof(uint4) * n * V);
+  ENS(B_DKEY, sizeof(uint32_t) * n * V);
   ENS(B_REC, sizeof(float4) * 3 * n * V);
   ENS(B_VIS, sizeof(uint32_t) * vis_words * V);
   if (o->flags & HG_FLAG_KEEP_SPLATS) ENS(B_SPLATS, sizeof(hg_splat) * n * V);
@@ -337,27 +339,30 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   if (timing) HG_TRY(record_stage(s->ev[0], st), "stage event 0");
   HG_TRY(cudaMemsetAsync(fc, 0, sizeof(FrameCounters), st), "memset counters");
   HG_TRY(cudaMemcpyAsync(views, s->views_host, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st), "upload views");
+  ProjectArgs pj{};
+  pj.n = n;
+  pj.views = views;
+  pj.n_views = V;
+  pj.vis_words = (long long)vis_words;
+  pj.bin = (uint4*)s->bufs[B_BIN].p;
+  pj.dkeys = (uint32_t*)s->bufs[B_DKEY].p;
+  pj.rec = (float4*)s->bufs[B_REC].p;
+  pj.vis = (uint32_t*)s->bufs[B_VIS].p;
+  pj.bin_mode = o->path == HG_PATH_PLAIN ? BIN_CLASSIC
+                                         : (o->bin_test == HG_BIN_ELLIPSE ? BIN_CELLS_ELLIPSE : BIN_CELLS_RECT);
+  pj.macro_w = o->macro_w;
+  pj.macro_h = o->macro_h;
+  pj.fc = fc;
   if (in.splats) {
-    HG_TRY(launch_splats_to_records(in.splats, n, V, (long long)vis_words, (uint4*)s->bufs[B_BIN].p,
-                                    (float4*)s->bufs[B_REC].p, (uint32_t*)s->bufs[B_VIS].p, st),
-           "splats to records");
+    HG_TRY(launch_splats_to_records(in.splats, n, V, (long long)vis_words, pj, st), "splats to records");
   } else {
-    ProjectArgs pa{};
-    pa.means = in.scene->arr[0];
-    pa.log_scales = in.scene->arr[1];
-    pa.quats = in.scene->arr[2];
-    pa.opacity_logits = in.scene->arr[3];
-    pa.sh = in.scene->arr[4];
-    pa.n = n;
-    pa.views = views;
-    pa.n_views = V;
-    pa.vis_words = (long long)vis_words;
-    pa.bin = (uint4*)s->bufs[B_BIN].p;
-    pa.rec = (float4*)s->bufs[B_REC].p;
-    pa.vis = (uint32_t*)s->bufs[B_VIS].p;
-    pa.splats = (o->flags & HG_FLAG_KEEP_SPLATS) ? (hg_splat*)s->bufs[B_SPLATS].p : nullptr;
-    pa.fc = fc;
-    HG_TRY(launch_project(pa, in.scene->deg, st), "project");
+    pj.means = in.scene->arr[0];
+    pj.log_scales = in.scene->arr[1];
+    pj.quats = in.scene->arr[2];
+    pj.opacity_logits = in.scene->arr[3];
+    pj.sh = in.scene->arr[4];
+    pj.splats = (o->flags & HG_FLAG_KEEP_SPLATS) ? (hg_splat*)s->bufs[B_SPLATS].p : nullptr;
+    HG_TRY(launch_project(pj, in.scene->deg, st), "project");
   }
   if (timing) HG_TRY(record_stage(s->ev[1], st), "stage event 1");
 
@@ -434,6 +439,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     }
     PartitionArgs pa{};
     pa.bin = (const uint4*)s->bufs[B_BIN].p;
+    pa.dkeys = (const uint32_t*)s->bufs[B_DKEY].p;
     pa.vis = (const uint32_t*)s->bufs[B_VIS].p;
     pa.n = n;
     pa.vis_words = (long long)vis_words;

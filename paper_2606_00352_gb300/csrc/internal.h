@@ -31,7 +31,7 @@ struct Buf {
 };
 
 enum BufId {
-  B_FC, B_VIEWS, B_BIN, B_REC, B_VIS, B_SPLATS,
+  B_FC, B_VIEWS, B_BIN, B_DKEY, B_REC, B_VIS, B_SPLATS,
   B_HIST, B_COLPRE, B_SEGTOT, B_SEGOFF, B_FIRSTB, B_TIERLIST, B_BIGTILES, B_BIGSEGS, B_BIGTF,
   B_KEYS, B_VALS, B_KEYS2, B_VALS2, B_BATCHES, B_BORDER, B_RANKC,
   B_PARTIAL, B_ACTIVE, B_CHAIN, B_MODE, B_TSTATE, B_TRANK, B_STOPPOS, B_FINAL, B_PREFIX, B_SEGHIST, B_LOOKBACK,

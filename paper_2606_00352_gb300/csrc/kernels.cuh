@@ -14,16 +14,20 @@ struct ProjectArgs {
   const ViewDesc* views;  // device
   int n_views;
   long long vis_words;    // ceil(n / 32)
-  uint4* bin;             // [V][n]
+  uint4* bin;             // [V][n] binning records (visible entries)
   float4* rec;            // [V][n][3]
   uint32_t* vis;          // [V][vis_words]
+  uint32_t* dkeys;        // [V][n] depth keys (cell binning records)
+  int bin_mode;           // BIN_CLASSIC, BIN_CELLS_RECT or BIN_CELLS_ELLIPSE
+  int macro_w, macro_h;   // render tiles per macro cell (cell binning records)
   hg_splat* splats;       // optional [V][n]
   FrameCounters* fc;
 };
 
 // Partition (count -> scan -> fill) and batch split of one frame.
 struct PartitionArgs {
-  const uint4* bin;
+  const uint4* bin;        // [V][n] cell binning records
+  const uint32_t* dkeys;   // [V][n] depth keys
   const uint32_t* vis;
   long long n;
   long long vis_words;
@@ -218,8 +222,8 @@ void note_launch(int n = 1);
 long long launches_issued();
 
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
-cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words, uint4* bin,
-                                     float4* rec, uint32_t* vis, cudaStream_t st);
+cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words,
+                                     const ProjectArgs& out, cudaStream_t st);
 cudaError_t launch_partition(const PartitionArgs& a, cudaStream_t st);
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
 cudaError_t launch_raster(const RasterArgs& a, cudaStream_t st);

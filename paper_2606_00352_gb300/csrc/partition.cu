@@ -12,8 +12,10 @@
 //           seg_off + column prefix + shared-memory cursor
 //   batches batch table {segment, start, count, rank} and the raster order
 //           (all rank-0 batches first, then rank 1, ...)
-// Binning test: the 3-sigma rectangle in integers, [floor(x0 - r / Bx),
-// floor((x0 + r) / Bx)] clamped to the macro grid (same for y).
+// Binning test: the cells of each (view, gaussian) come from its binning
+// record (binning.cuh: the 3-sigma rectangle, optionally refined by the
+// opacity-aware ellipse), made by the projection.
+#include "binning.cuh"
 #include "kernels.cuh"
 
 namespace hg {
@@ -22,39 +24,21 @@ namespace {
 
 constexpr int PART_THREADS = 512;
 
-__device__ __forceinline__ bool macro_rect(const uint4& r, int bw, int bh, int gx, int gy, int& x0, int& x1,
-                                           int& y0, int& y1) {
-  const int rad = (int)r.z;
-  if (rad <= 0) return false;
-  const int px = (int)floorf(__uint_as_float(r.x));
-  const int py = (int)floorf(__uint_as_float(r.y));
-  const int xl = px - rad, xh = px + rad, yl = py - rad, yh = py + rad;
-  x0 = xl < 0 ? 0 : xl / bw;
-  x1 = xh < 0 ? -1 : min(xh / bw, gx - 1);
-  y0 = yl < 0 ? 0 : yl / bh;
-  y1 = yh < 0 ? -1 : min(yh / bh, gy - 1);
-  return x0 <= x1 && y0 <= y1;
-}
-
 __global__ void __launch_bounds__(PART_THREADS) k_count(PartitionArgs a) {
   extern __shared__ uint32_t hist[];
   if (read_status(a.fc)) return;
   const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
   const ViewDesc& V = a.views[v];
-  const int nm = V.mgx * V.mgy, bw = a.macro_w * TILE, bh = a.macro_h * TILE;
+  const int nm = V.mgx * V.mgy;
   for (int m = tid; m < nm; m += PART_THREADS) hist[m] = 0;
   __syncthreads();
   const long long i_end = min(a.n, (long long)(b + 1) * BP);
   const uint32_t* vis = a.vis + (size_t)v * a.vis_words;
-  const uint4* bin = a.bin + (size_t)v * a.n;
   for (long long i = (long long)b * BP + tid; i < i_end; i += PART_THREADS) {
     const uint32_t word = vis[i >> 5];
     if (word == 0) continue;  // whole warp culled
     if (!((word >> (i & 31)) & 1u)) continue;
-    int x0, x1, y0, y1;
-    if (!macro_rect(bin[i], bw, bh, V.mgx, V.mgy, x0, x1, y0, y1)) continue;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) atomicAdd(&hist[y * V.mgx + x], 1u);
+    for_each_cell(a.bin[(size_t)v * a.n + i], V.mgx, [&](int m) { atomicAdd(&hist[m], 1u); });
   }
   __syncthreads();
   uint16_t* row = a.hist + (size_t)b * a.n_seg + V.seg_base;
@@ -209,26 +193,23 @@ __global__ void __launch_bounds__(PART_THREADS) k_fill(PartitionArgs a) {
   if (read_status(a.fc)) return;
   const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
   const ViewDesc& V = a.views[v];
-  const int nm = V.mgx * V.mgy, bw = a.macro_w * TILE, bh = a.macro_h * TILE;
+  const int nm = V.mgx * V.mgy;
   const uint32_t* pre = a.colpre + (size_t)b * a.n_seg + V.seg_base;
   for (int m = tid; m < nm; m += PART_THREADS) cursor[m] = a.seg_off[V.seg_base + m] + pre[m];
   __syncthreads();
   const long long i_end = min(a.n, (long long)(b + 1) * BP);
   const uint32_t* vis = a.vis + (size_t)v * a.vis_words;
-  const uint4* bin = a.bin + (size_t)v * a.n;
   for (long long i = (long long)b * BP + tid; i < i_end; i += PART_THREADS) {
     const uint32_t word = vis[i >> 5];
     if (word == 0) continue;
     if (!((word >> (i & 31)) & 1u)) continue;
-    const uint4 r = bin[i];
-    int x0, x1, y0, y1;
-    if (!macro_rect(r, bw, bh, V.mgx, V.mgy, x0, x1, y0, y1)) continue;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        const uint32_t pos = atomicAdd(&cursor[y * V.mgx + x], 1u);
-        a.keys[pos] = r.w;
-        a.vals[pos] = (uint32_t)i;
-      }
+    const size_t o = (size_t)v * a.n + i;
+    const uint32_t key = a.dkeys[o];
+    for_each_cell(a.bin[o], V.mgx, [&](int m) {
+      const uint32_t pos = atomicAdd(&cursor[m], 1u);
+      a.keys[pos] = key;
+      a.vals[pos] = (uint32_t)i;
+    });
   }
 }
 

@@ -4,13 +4,16 @@
 // arrays are staged into shared memory with TMA bulk copies.
 //
 // Outputs per (view, gaussian), index v * N + i:
-//   bin  uint4  {mx bits, my bits, radius, depth key}      radius 0 = culled
+//   bin  uint4  plain path: {mx bits, my bits, radius, depth key}; HiGS: the
+//               binning record of the macro cells (binning.cuh), with the
+//               depth key in dkeys
 //   rec  float4 x3 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, E}
 //        (E: the per-gaussian level of the blend test)
 //   vis  one bit per gaussian, written per warp (Sec. 4.2 visibility bitfield)
 // bin and rec are written for visible entries only.
 // l' are the Cholesky factors of the conic prescaled by sqrt(log2(e)/2), so the
 // rasteriser evaluates alpha = o exp2(-((l0' dx + l1' dy)^2 + (l2' dy)^2)).
+#include "binning.cuh"
 #include "blend.cuh"
 #include "kernels.cuh"
 
@@ -235,7 +238,13 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       const uint32_t ballot = __ballot_sync(0xffffffffu, vis);
       if (vis) {
         vbits |= 1ull << v;
-        a.bin[o] = make_uint4(__float_as_uint(mx), __float_as_uint(my), (uint32_t)rad, key);
+        if (a.bin_mode == BIN_CLASSIC) {
+          a.bin[o] = make_uint4(__float_as_uint(mx), __float_as_uint(my), (uint32_t)rad, key);
+        } else {
+          a.bin[o] = bin_cells(mx, my, rad, l0, l1, l2, op, a.macro_w * TILE, a.macro_h * TILE, V.mgx, V.mgy,
+                               a.bin_mode == BIN_CELLS_ELLIPSE);
+          a.dkeys[o] = key;
+        }
         float4* r = a.rec + o * 3;
         r[0] = make_float4(mx, my, l0, l1);
         r[1] = make_float4(l2, op, __int_as_float(rad), __uint_as_float(key));
@@ -303,29 +312,37 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
 }
 
 // Public splat records -> internal records (used by hg_render_splats).
-__global__ void k_splats_to_records(const hg_splat* sp, long long total, long long n, long long vis_words,
-                                    uint4* bin, float4* rec, uint32_t* vis) {
+__global__ void k_splats_to_records(const hg_splat* sp, long long total, long long n, ProjectArgs out) {
   long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = o < total;
   hg_splat s;
   bool on = false;
   if (valid) {
     s = sp[o];
+    const long long v = o / n;
+    const ViewDesc& V = out.views[v];
     on = s.radius > 0 && fabsf(s.mean2d[0]) < 1e7f && fabsf(s.mean2d[1]) < 1e7f;
-    float l0 = sqrtf(fmaxf(s.conic[0], 0.f));
-    float l1 = l0 > 0.f ? s.conic[1] / l0 : 0.f;
-    float l2 = sqrtf(fmaxf(s.conic[2] - l1 * l1, 0.f));
-    int rad = on ? min(s.radius, RADIUS_MAX) : 0;
-    bin[o] = make_uint4(__float_as_uint(s.mean2d[0]), __float_as_uint(s.mean2d[1]), (uint32_t)rad, s.depth_key);
-    rec[o * 3 + 0] = make_float4(s.mean2d[0], s.mean2d[1], l0 * CHOL_PRESCALE, l1 * CHOL_PRESCALE);
-    rec[o * 3 + 1] = make_float4(l2 * CHOL_PRESCALE, s.opacity, __int_as_float(rad), __uint_as_float(s.depth_key));
-    rec[o * 3 + 2] = make_float4(s.rgb[0], s.rgb[1], s.rgb[2], blend_level(s.opacity));
+    // Cholesky factors, each operation rounded as written (reproducible)
+    const float l0 = __fsqrt_rn(fmaxf(s.conic[0], 0.f));
+    const float l1 = l0 > 0.f ? __fdiv_rn(s.conic[1], l0) : 0.f;
+    const float l2 = __fsqrt_rn(fmaxf(__fsub_rn(s.conic[2], __fmul_rn(l1, l1)), 0.f));
+    const float L0 = __fmul_rn(l0, CHOL_PRESCALE), L1 = __fmul_rn(l1, CHOL_PRESCALE), L2 = __fmul_rn(l2, CHOL_PRESCALE);
+    const int rad = on ? min(s.radius, RADIUS_MAX) : 0;
+    if (out.bin_mode == BIN_CLASSIC)
+      out.bin[o] = make_uint4(__float_as_uint(s.mean2d[0]), __float_as_uint(s.mean2d[1]), (uint32_t)rad, s.depth_key);
+    else
+      out.bin[o] = bin_cells(s.mean2d[0], s.mean2d[1], rad, L0, L1, L2, s.opacity, out.macro_w * TILE,
+                             out.macro_h * TILE, V.mgx, V.mgy, out.bin_mode == BIN_CELLS_ELLIPSE);
+    out.dkeys[o] = s.depth_key;
+    out.rec[o * 3 + 0] = make_float4(s.mean2d[0], s.mean2d[1], L0, L1);
+    out.rec[o * 3 + 1] = make_float4(L2, s.opacity, __int_as_float(rad), __uint_as_float(s.depth_key));
+    out.rec[o * 3 + 2] = make_float4(s.rgb[0], s.rgb[1], s.rgb[2], blend_level(s.opacity));
   }
   // visibility words: the splat array is [V][n]; a warp's 32 entries map to
   // one word only when n is a multiple of 32, so set bits atomically.
   if (valid && on) {
     long long v = o / n, i = o % n;
-    atomicOr(&vis[v * vis_words + (i >> 5)], 1u << (i & 31));
+    atomicOr(&out.vis[v * out.vis_words + (i >> 5)], 1u << (i & 31));
   }
 }
 
@@ -352,12 +369,12 @@ cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words, uint4* bin,
-                                     float4* rec, uint32_t* vis, cudaStream_t st) {
+cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words,
+                                     const ProjectArgs& out, cudaStream_t st) {
   long long total = n * n_views;
-  cudaError_t e = cudaMemsetAsync(vis, 0, sizeof(uint32_t) * vis_words * n_views, st);
+  cudaError_t e = cudaMemsetAsync(out.vis, 0, sizeof(uint32_t) * vis_words * n_views, st);
   if (e != cudaSuccess || total == 0) return e;
-  k_splats_to_records<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, total, n, vis_words, bin, rec, vis);
+  k_splats_to_records<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, total, n, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       const uint4* ring4 = reinterpret_cast<const uint4*>(ring);
       uint32_t head = 0, tail = 0;
       bool all_done = false;
-      auto drain = [&](uint32_t n) {
+      auto drain = [&](uint32_t n, uint32_t n_real) {
         for (uint32_t i0 = 0; i0 < n; i0 += 8) {
           const uint4 q = ring4[((head + i0) & (RING - 1)) >> 3];
           const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
             blend(p0, ub, fpy - g0.y, g0, g1, g2);
             blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
           }
-          n_blend += 8;
+          n_blend += min(8u, n_real - i0);
           if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
             all_done = true;
             break;
@@ -230,13 +230,13 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           tail += __popc(m);
           __syncwarp();
         }
-        if (tail - head >= DRAIN) drain(DRAIN);
+        if (tail - head >= DRAIN) drain(DRAIN, DRAIN);
       }
       if (!all_done && tail > head) {
-        const uint32_t n8 = (tail - head + 7u) & ~7u;
-        if (lane < n8 - (tail - head)) ring[(tail + lane) & (RING - 1)] = (uint16_t)cap;
+        const uint32_t nr = tail - head, n8 = (nr + 7u) & ~7u;
+        if (lane < n8 - nr) ring[(tail + lane) & (RING - 1)] = (uint16_t)cap;
         __syncwarp();
-        drain(n8);
+        drain(n8, nr);
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
       if (chained) {

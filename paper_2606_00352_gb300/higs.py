@@ -20,6 +20,7 @@ HG_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "capacity",
           -5: "device timeout", -6: "busy", -7: "not found", -8: "cancelled", -9: "unsupported"}
 PATH_HIGS, PATH_PLAIN = 0, 1
+BIN_RECT, BIN_ELLIPSE = 0, 1
 FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT, FLAG_PROFILE = 1, 2, 4, 8, 16
 BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE = range(6)
 
@@ -198,6 +199,7 @@ class Options:
     macro_w: int = 8
     macro_h: int = 4
     batch_cap: int = 1024
+    bin_test: int = BIN_RECT
     bg: tuple = (0.0, 0.0, 0.0)
     save_for_backward: bool = False
     flags: int = 0
@@ -205,7 +207,7 @@ class Options:
     def struct(self) -> RenderOpts:
         o = RenderOpts()
         o.path, o.macro_w, o.macro_h, o.batch_cap, o.bin_test = (self.path, self.macro_w, self.macro_h,
-                                                                 self.batch_cap, 0)
+                                                                 self.batch_cap, self.bin_test)
         for i in range(3):
             o.bg[i] = float(self.bg[i])
         o.save_for_backward = int(self.save_for_backward)

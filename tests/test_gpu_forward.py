@@ -79,7 +79,19 @@ def test_projection_sh3_colour(lib, ctx):
 
 
 # ------------------------------------------------------------ discrete stages
-def _gate(lib, ctx, projs, cams, macro=(8, 4), cap=1024):
+def _oracle_views(projs, ellipse):
+    """Oracle binning inputs from the same float32 values the splats carry."""
+    views = []
+    for p in projs:
+        r = BN.records_f32(p)
+        if ellipse:
+            L = BN.cholesky_from_conic(p["conic"].astype(np.float32))
+            r = r + ((L[0], L[1], L[2], p["opacity"].astype(np.float32)),)
+        views.append(r)
+    return views
+
+
+def _gate(lib, ctx, projs, cams, macro=(8, 4), cap=1024, ellipse=False):
     """Render oracle records through hg_render_splats and compare pairs, keys
     and batch boundaries bit-exactly with the oracle's stages."""
     import torch
@@ -87,14 +99,16 @@ def _gate(lib, ctx, projs, cams, macro=(8, 4), cap=1024):
     rec = splat_records(projs, lib.SPLAT_DTYPE)
     d = lib.splats_to_device(rec)
     st = lib.State(ctx)
-    lib.render_splats(ctx, d, n, cams, lib.Options(macro_w=macro[0], macro_h=macro[1], batch_cap=cap), state=st)
+    opts = lib.Options(macro_w=macro[0], macro_h=macro[1], batch_cap=cap,
+                       bin_test=lib.BIN_ELLIPSE if ellipse else lib.BIN_RECT)
+    lib.render_splats(ctx, d, n, cams, opts, state=st)
     torch.cuda.synchronize()
     seg_off = st.read(lib.BUF_SEG_OFF).astype(np.int64)
     keys = st.read(lib.BUF_PAIR_KEYS)
     ids = st.read(lib.BUF_PAIR_IDS).astype(np.int64)
     bt = st.read(lib.BUF_BATCHES).reshape(-1, 3).astype(np.int64)
-    ref = BN.segments([BN.records_f32(p) for p in projs], [(c.width, c.height) for c in cams],
-                      macro[0] * 8, macro[1] * 8)
+    ref = BN.segments(_oracle_views(projs, ellipse), [(c.width, c.height) for c in cams], macro[0] * 8,
+                      macro[1] * 8)
     assert np.array_equal(seg_off, ref["seg_off"])
     assert np.array_equal(keys, ref["keys"])
     assert np.array_equal(ids, ref["ids"])
@@ -103,19 +117,33 @@ def _gate(lib, ctx, projs, cams, macro=(8, 4), cap=1024):
     return st.stats()
 
 
+@pytest.mark.parametrize("ellipse", [False, True])
 @pytest.mark.parametrize("macro", [(8, 4), (4, 4), (8, 8)])
 @pytest.mark.parametrize("cap", [32, 256, 1024])
-def test_discrete_stages_tiny(lib, ctx, macro, cap):
+def test_discrete_stages_tiny(lib, ctx, macro, cap, ellipse):
     scene, cams = scenes.tiny_workload()
-    _gate(lib, ctx, [P.project(scene, cams[0])], cams, macro, cap)
+    _gate(lib, ctx, [P.project(scene, cams[0])], cams, macro, cap, ellipse)
 
 
-def test_discrete_stages_multiview_mixed_resolution(lib, ctx):
+@pytest.mark.parametrize("ellipse", [False, True])
+def test_discrete_stages_multiview_mixed_resolution(lib, ctx, ellipse):
     scene = scenes.uniform_scene(20_000, seed=4)
     cams = [scenes.look_at((3, 0, 0), width=256, height=256),
             scenes.look_at((0, 3, 0.5), width=200, height=120),
             scenes.look_at((-2, -2, 1), width=97, height=61)]
-    _gate(lib, ctx, [P.project(scene, c) for c in cams], cams)
+    st = _gate(lib, ctx, [P.project(scene, c) for c in cams], cams, ellipse=ellipse)
+    assert st["n_pairs"] > 0
+
+
+def test_discrete_stages_ellipse_cluster_scene(lib, ctx):
+    """Ellipse binning of anisotropic, rotated gaussians with the full opacity
+    range (cluster scene, 1080p view): bit-exact pairs, order and batches."""
+    scene = scenes.cluster_scene(60_000, 16, 1.4, seed=3, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    cam = scenes.scene_orbit(8, 1920, 1080)[3]
+    pr = P.project(scene, cam)
+    st_e = _gate(lib, ctx, [pr], [cam], macro=(4, 4), ellipse=True)
+    st_r = _gate(lib, ctx, [pr], [cam], macro=(4, 4))
+    assert 0 < st_e["n_pairs"] < st_r["n_pairs"]
 
 
 def _synthetic_records(n, w, h, n_keys, seed, rad_max=3):
@@ -140,6 +168,8 @@ def test_discrete_stages_onesweep_and_ties(lib, ctx):
     assert st["seg_by_tier"][3] > 0 and st["n_sort_tiles"] > 1
     st2 = _gate(lib, ctx, [pr], [cam], macro=(4, 4), cap=2048)
     assert st2["seg_by_tier"][3] > 0
+    st3 = _gate(lib, ctx, [pr], [cam], macro=(4, 4), ellipse=True)
+    assert st3["seg_by_tier"][3] > 0
 
 
 def test_discrete_stages_all_tiers(lib, ctx):
@@ -184,6 +214,37 @@ def test_image_invariant_to_macro_shape_and_cap(lib, ctx, macro, cap, independen
     compare_image(imgs[0], ts[0], ref)
     if cap <= 64:
         assert (st.stats()["n_replays"] > 0) == independent
+
+
+@pytest.mark.parametrize("macro,cap", [((8, 4), 64), ((4, 4), 1024), ((8, 8), 256)])
+def test_image_ellipse_binning_equals_rect(lib, ctx, macro, cap):
+    """The ellipse test only drops gaussians that fail the blend test at
+    every pixel of the macro-tile, and chained batches composite in exact
+    depth order, so the image is the same bits as with the rectangle test;
+    both match the oracle."""
+    scene = scenes.cluster_scene(40_000, 8, 1.2, seed=9, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    cam = scenes.scene_orbit(8, 320, 200)[1]
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    out = {}
+    for b in (lib.BIN_RECT, lib.BIN_ELLIPSE):
+        st = lib.State(ctx)
+        imgs, ts = render_np(lib, gs, [cam], macro_w=macro[0], macro_h=macro[1], batch_cap=cap, bin_test=b, state=st)
+        out[b] = (imgs[0], ts[0], st.stats()["n_pairs"])
+    assert np.array_equal(out[lib.BIN_RECT][0], out[lib.BIN_ELLIPSE][0])
+    assert np.array_equal(out[lib.BIN_RECT][1], out[lib.BIN_ELLIPSE][1])
+    assert out[lib.BIN_ELLIPSE][2] < out[lib.BIN_RECT][2]
+    ref = C.render(P.project(scene, cam))
+    compare_image(out[lib.BIN_ELLIPSE][0], out[lib.BIN_ELLIPSE][1], ref)
+
+
+def test_image_ellipse_binning_independent_batches(lib, ctx):
+    scene = scenes.uniform_scene(30_000, seed=2)
+    scene.log_scales += np.float32(0.7)
+    cam = scenes.look_at((3, 0, 0), width=192, height=136)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    imgs, ts = render_np(lib, gs, [cam], macro_w=8, macro_h=4, batch_cap=64, bin_test=lib.BIN_ELLIPSE,
+                         flags=lib.FLAG_INDEPENDENT)
+    compare_image(imgs[0], ts[0], C.render(P.project(scene, cam)))
 
 
 def test_image_background_and_multiview(lib, ctx):
