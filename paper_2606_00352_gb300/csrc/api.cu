@@ -331,7 +331,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   ENS(B_VIEWS, sizeof(ViewDesc) * MAX_VIEWS);
   ENS(B_BIN, sizeof(uint4) * n * V);
   ENS(B_DKEY, sizeof(uint32_t) * n * V);
-  ENS(B_REC, sizeof(float4) * 3 * n * V);
+  ENS(B_REC, sizeof(float4) * REC_F4 * n * V);
   ENS(B_VIS, sizeof(uint32_t) * vis_words * V);
   if (o->flags & HG_FLAG_KEEP_SPLATS) ENS(B_SPLATS, sizeof(hg_splat) * n * V);
   FrameCounters* fc = (FrameCounters*)s->bufs[B_FC].p;

@@ -136,12 +136,12 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
     const ViewDesc& V = a.views[v];
     const int mloc = (int)seg - V.seg_base;
     const int mtx0 = (mloc % V.mgx) * MW, mty0 = (mloc / V.mgx) * MH;
-    const float4* rec_v = a.rec + (size_t)v * a.n * 3;
+    const float4* rec_v = a.rec + (size_t)v * a.n * REC_F4;
     if (tid == 0) mbar_arrive_expect_tx(&bar, count * 48u);
     __syncthreads();
     for (uint32_t j = tid; j < count; j += BT) {
       const uint32_t id = a.vals[start + j];
-      tma_load_1d(s_rec + (size_t)j * 3, rec_v + (size_t)id * 3, 48u, &bar);
+      tma_load_1d(s_rec + (size_t)j * 3, rec_v + (size_t)id * REC_F4, 48u, &bar);
     }
     for (uint32_t j = tid; j < count * NG; j += BT) s_grad[j] = 0.f;
     if (!mbar_wait_bounded(&bar, phase)) {

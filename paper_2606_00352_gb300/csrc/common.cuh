@@ -20,6 +20,9 @@ constexpr float CHOL_PRESCALE = 0.84932180028801906868f;
 // q <= 9 in prescaled units: 9 log2(e) / 2
 constexpr float SUPPORT_E = 6.49212768400033546357f;
 constexpr int MAX_VIEWS = 64;
+// Raster records: 48 bytes of data at a 64-byte stride in global memory, so
+// that a record never straddles two 64-byte DRAM access chunks.
+constexpr int REC_F4 = 4;
 constexpr int RADIUS_MAX = 1 << 20;
 constexpr uint32_t SPIN_LIMIT = 1u << 24;  // bounded device waits
 

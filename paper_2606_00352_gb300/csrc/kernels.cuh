@@ -15,7 +15,7 @@ struct ProjectArgs {
   int n_views;
   long long vis_words;    // ceil(n / 32)
   uint4* bin;             // [V][n] binning records (visible entries)
-  float4* rec;            // [V][n][3]
+  float4* rec;            // [V][n][REC_F4]
   uint32_t* vis;          // [V][vis_words]
   uint32_t* dkeys;        // [V][n] depth keys (cell binning records)
   int bin_mode;           // BIN_CLASSIC, BIN_CELLS_RECT or BIN_CELLS_ELLIPSE
@@ -83,7 +83,7 @@ struct SortArgs {
 };
 
 struct RasterArgs {
-  const float4* rec;          // [V][n][3]
+  const float4* rec;          // [V][n][REC_F4]
   long long n;
   const ViewDesc* views;
   int n_views;
@@ -136,7 +136,7 @@ struct MergeArgs {
 };
 
 struct BackwardArgs {
-  const float4* rec;          // forward records [V][n][3]
+  const float4* rec;          // forward records [V][n][REC_F4]
   long long n;
   const ViewDesc* views;
   int n_views;

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
     pixel_init(p0, in0);
     pixel_init(p1, in1);
     const uint32_t r0 = a.first_batch[seg], r1 = a.first_batch[seg + 1];
-    const float4* rec_v = a.rec + (size_t)v * a.n * 3;
+    const float4* rec_v = a.rec + (size_t)v * a.n * REC_F4;
     // batches rendered in order from the exact entering transmittance: their
     // result is the per-tile state
     uint32_t g = r0;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
         bool ov = false;
         if (j < bt.z) {
           const uint32_t id = a.vals[bt.y + j];
-          const float4* rp = rec_v + (size_t)id * 3;
+          const float4* rp = rec_v + (size_t)id * REC_F4;
           g0 = rp[0];
           g1 = rp[1];
           g2 = rp[2];

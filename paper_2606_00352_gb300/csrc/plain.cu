@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TILE_PX) k_plain_raster(PlainArgs a, const uin
     if (__syncthreads_count(pixel_live(p)) == 0) break;
     const uint32_t j = base + tid;
     if (j < rg.y) {
-      const float4* rp = a.rec + (size_t)vals[j] * 3;
+      const float4* rp = a.rec + (size_t)vals[j] * REC_F4;
       s_rec[tid * 3 + 0] = rp[0];
       s_rec[tid * 3 + 1] = rp[1];
       s_rec[tid * 3 + 2] = rp[2];

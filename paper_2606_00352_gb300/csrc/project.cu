@@ -7,7 +7,7 @@
 //   bin  uint4  plain path: {mx bits, my bits, radius, depth key}; HiGS: the
 //               binning record of the macro cells (binning.cuh), with the
 //               depth key in dkeys
-//   rec  float4 x3 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, E}
+//   rec  float4 x4 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, E} {0}
 //        (E: the per-gaussian level of the blend test)
 //   vis  one bit per gaussian, written per warp (Sec. 4.2 visibility bitfield)
 // bin and rec are written for visible entries only.
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
                                a.bin_mode == BIN_CELLS_ELLIPSE);
           a.dkeys[o] = key;
         }
-        float4* r = a.rec + o * 3;
+        float4* r = a.rec + o * REC_F4;
         r[0] = make_float4(mx, my, l0, l1);
         r[1] = make_float4(l2, op, __int_as_float(rad), __uint_as_float(key));
       }
@@ -301,7 +301,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       const float cg = fmaxf(acc[v][1] + 0.5f, 0.f);
       const float cbl = fmaxf(acc[v][2] + 0.5f, 0.f);
       const long long o = (long long)(v0 + v) * a.n + gi;
-      if ((vbits >> (v0 + v)) & 1ull) a.rec[o * 3 + 2] = make_float4(cr, cg, cbl, blend_level(op));
+      if ((vbits >> (v0 + v)) & 1ull) {
+        a.rec[o * REC_F4 + 2] = make_float4(cr, cg, cbl, blend_level(op));
+        a.rec[o * REC_F4 + 3] = make_float4(0.f, 0.f, 0.f, 0.f);  // stride padding (whole 64-byte writes)
+      }
       if (keep) {
         a.splats[o].rgb[0] = cr;
         a.splats[o].rgb[1] = cg;
@@ -334,9 +337,10 @@ __global__ void k_splats_to_records(const hg_splat* sp, long long total, long lo
       out.bin[o] = bin_cells(s.mean2d[0], s.mean2d[1], rad, L0, L1, L2, s.opacity, out.macro_w * TILE,
                              out.macro_h * TILE, V.mgx, V.mgy, out.bin_mode == BIN_CELLS_ELLIPSE);
     out.dkeys[o] = s.depth_key;
-    out.rec[o * 3 + 0] = make_float4(s.mean2d[0], s.mean2d[1], L0, L1);
-    out.rec[o * 3 + 1] = make_float4(L2, s.opacity, __int_as_float(rad), __uint_as_float(s.depth_key));
-    out.rec[o * 3 + 2] = make_float4(s.rgb[0], s.rgb[1], s.rgb[2], blend_level(s.opacity));
+    out.rec[o * REC_F4 + 0] = make_float4(s.mean2d[0], s.mean2d[1], L0, L1);
+    out.rec[o * REC_F4 + 1] = make_float4(L2, s.opacity, __int_as_float(rad), __uint_as_float(s.depth_key));
+    out.rec[o * REC_F4 + 2] = make_float4(s.rgb[0], s.rgb[1], s.rgb[2], blend_level(s.opacity));
+    out.rec[o * REC_F4 + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   // visibility words: the splat array is [V][n]; a warp's 32 entries map to
   // one word only when n is a multiple of 32, so set bits atomically.

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     const ViewDesc& V = a.views[v];
     const int mloc = (int)seg - V.seg_base;
     const int mtx0 = (mloc % V.mgx) * MW, mty0 = (mloc / V.mgx) * MH;  // macro origin (tiles)
-    const float4* rec_v = a.rec + (size_t)v * a.n * 3;
+    const float4* rec_v = a.rec + (size_t)v * a.n * REC_F4;
     long long t_start = a.profile ? clock64() : 0;
 
     // gather the batch records: one bulk copy of 48 bytes per gaussian
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     __syncthreads();
     for (uint32_t j = tid; j < count; j += RT) {
       const uint32_t id = a.vals[start + j];
-      tma_load_1d(s_rec + (size_t)j * 3, rec_v + (size_t)id * 3, 48u, &bar);
+      tma_load_1d(s_rec + (size_t)j * 3, rec_v + (size_t)id * REC_F4, 48u, &bar);
     }
     if (!mbar_wait_bounded(&bar, phase)) {
       set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
