@@ -22,6 +22,7 @@ float32 scene parameters:
                     exact-termination replay, used to pin the invariance
                     "any macro shape or batch cap gives the same image".
   * ``grad``      - analytic FP64 gradient of 0.5*||C - C_target||^2.
+  * ``train``     - the L2 loss and the Adam step of the differentiable path.
 
 Every function names the passage it follows; readings of silent or
 ambiguous passages are listed in the repository's design notes.
