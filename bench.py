@@ -386,33 +386,47 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     return rows
 
 
-def train_step_ms(higs, ctx, steps=5):
-    """Forward (saving what the backward needs) + backward of 4 views at
-    1080p of the 1M-gaussian scene, with 0.5 ||C - C*||^2 upstream."""
+def train_step_ms(higs, ctx, steps=10):
+    """Densification-free optimisation steps on the 1M-gaussian scene, 4
+    views at 1080p, against the render of a perturbed copy (means + N(0,
+    1e-3), opacity logits + N(0, 0.1)): forward (saving what the backward
+    needs), L2 loss, backward, Adam, each timed with CUDA events."""
     import torch
     from paper_2606_00352_gb300 import scenes
     scene = scenes.scene_1m()
-    gs = higs.GpuScene.from_scene(ctx, scene)
     cams = scenes.scene_orbit(32, WIDTH, HEIGHT)[:VIEWS]
-    st = higs.State(ctx)
-    opts = higs.Options(save_for_backward=True)
-    target = torch.rand(VIEWS * WIDTH * HEIGHT * 3, device="cuda")
-    times = []
+    target_gs = higs.GpuScene.from_scene(ctx, scenes.perturbed(scene))
+    target, _ = higs.render(target_gs, cams, higs.Options(), with_T=False)
+    target_gs.close()
+    dev = torch.device("cuda", ctx.device)
+    params = [torch.as_tensor(x, device=dev).contiguous()
+              for x in (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh)]
+    tr = higs.Trainer(ctx, params, scene.sh_degree, cams, target)
+    stream = torch.cuda.current_stream()
+    times, losses = [], []
     for k in range(steps + 2):
-        torch.cuda.synchronize()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record()
-        rgb, _ = higs.render(gs, cams, opts, state=st, with_T=False)
-        e1.record()
-        higs.render_backward(st, gs, rgb - target)
-        e2.record()
-        e2.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        rgb, _ = higs.render(tr.scene, cams, tr.opts, state=tr.state, with_T=False)
+        ev[1].record(stream)
+        higs.l2_loss(ctx, rgb, tr.target, tr.dl, tr.loss)
+        ev[2].record(stream)
+        higs.render_backward(tr.state, tr.scene, tr.dl, out=tr.grads)
+        ev[3].record(stream)
+        tr.t += 1
+        higs.adam_step(tr.scene, tr.grads, tr.m, tr.v, tr.t, tr.lr)
+        ev[4].record(stream)
+        ev[4].synchronize()
+        losses.append(float(tr.loss.item()))
         if k >= 2:
-            times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
-    return {"forward_ms": round(statistics.median(t[0] for t in times), 3),
-            "backward_ms": round(statistics.median(t[1] for t in times), 3),
-            "workload": "1M-gaussian SH-3 scene (64 clusters, Zipf 1.2), 4 views at 1920x1080, "
-                        "forward with saved prefixes + hg_render_backward"}
+            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    tr.close()
+    med = [round(statistics.median(t[i] for t in times), 3) for i in range(4)]
+    return {"forward_ms": med[0], "loss_ms": med[1], "backward_ms": med[2], "adam_ms": med[3],
+            "step_ms": round(sum(med), 3), "loss_first": round(losses[0], 3), "loss_last": round(losses[-1], 3),
+            "workload": "1M-gaussian SH-3 scene (64 clusters, Zipf 1.2), 4 views at 1920x1080, target = render "
+                        "of a perturbed copy; forward with saved prefixes + hg_l2_loss + hg_render_backward + "
+                        "hg_adam_step (3DGS learning rates)"}
 
 
 def gpu_arm(args):

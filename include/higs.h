@@ -200,11 +200,51 @@ hg_status hg_render_splats(hg_ctx* ctx, const hg_splat* d_splats, int64_t n,
  * as out_rgb) of the frame saved in `state` (rendered with
  * save_for_backward), write dL/d(parameter) into the device arrays (same
  * shapes as the scene arrays; they are overwritten, not accumulated).  The
- * per-batch partials become a prefix scan (Sec. 6) and every batch is
- * replayed back to front from its per-(pixel, batch) stop position. */
+ * forward saved the (C, T) entering every (batch, tile) (the prefix of the
+ * Eq. 1 scan, Sec. 6) and the final colours; every batch is replayed from
+ * its prefix with the forward's arithmetic, so the suffix colour behind a
+ * gaussian is C_final - C_<=i. */
 hg_status hg_render_backward(hg_state* state, const float* dL_drgb,
                              float* d_means, float* d_log_scales, float* d_quats,
                              float* d_opacity_logits, float* d_sh, void* stream);
+
+/* ---------------------------------------------------------- optimisation
+ * One densification-free optimisation step of the differentiable path
+ * (Sec. 6) is: hg_render with save_for_backward, hg_l2_loss, then
+ * hg_render_backward with its dL/dC, then hg_adam_step.  All four are
+ * stream-ordered and run only this library's kernels. */
+
+/* L2 photometric loss L = 1/2 sum_i (rgb_i - target_i)^2 over n floats and
+ * its gradient dL/d rgb_i = rgb_i - target_i (float32).  rgb, target and
+ * dL_drgb are device arrays of n floats (dL_drgb may alias neither input);
+ * *loss (device double) receives L.  The sum is accumulated in double in a
+ * fixed order, so the result is deterministic.  Scratch for the reduction
+ * is allocated through the context's allocator on the first call: make that
+ * call outside CUDA graph capture.  Calls on one context must be
+ * stream-serialised (they share the scratch).
+ * Errors: HG_ERR_INVALID_ARG, HG_ERR_OOM, HG_ERR_CUDA. */
+hg_status hg_l2_loss(hg_ctx* ctx, const float* rgb, const float* target, int64_t n,
+                     float* dL_drgb, double* loss, void* stream);
+
+typedef struct {
+  float lr[5];        /* learning rate per group: means, log_scales, quats,
+                         opacity_logits, sh */
+  float beta1, beta2; /* moment decay rates, in [0, 1) */
+  float eps;          /* denominator guard, >= 0 */
+  int32_t step;       /* 1-based step count t of this update */
+} hg_adam_opts;
+
+/* One Adam step (Kingma and Ba) on every parameter array of `scene`, in
+ * place: m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+ * p <- p - lr m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps), all five groups
+ * in one kernel.  grads / m / v are device arrays with the shapes of the
+ * scene arrays (float32, [n][3], [n][3], [n][4], [n], [n][K][3]); m and v are
+ * updated in place and start at zero.  With a borrowed scene the caller's
+ * parameter tensors are updated.
+ * Errors: HG_ERR_INVALID_ARG (null buffer, step < 1, beta outside [0, 1)),
+ *  HG_ERR_CUDA. */
+hg_status hg_adam_step(hg_scene* scene, const float* const grads[5], float* const m[5],
+                       float* const v[5], const hg_adam_opts* opts, void* stream);
 
 void hg_state_free(hg_state* state);
 

@@ -140,6 +140,10 @@ extern "C" void hg_ctx_destroy(hg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->internal) hg_state_free(ctx->internal);
+  if (ctx->loss_scratch) {
+    cudaDeviceSynchronize();
+    ctx_free(ctx, ctx->loss_scratch, LOSS_SCRATCH_BYTES, nullptr);
+  }
   delete ctx;
 }
 

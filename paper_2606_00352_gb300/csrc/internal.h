@@ -12,6 +12,7 @@ struct hg_ctx {
   bool has_alloc = false;
   int sms = 0;
   hg_state* internal = nullptr;  // workspace used when the caller passes no state
+  void* loss_scratch = nullptr;   // hg_l2_loss block partials + counter (allocated on first use)
 };
 
 struct hg_scene {
@@ -78,6 +79,10 @@ void hg_set_error(const std::string& s);
 hg_status hg_cuda_status(cudaError_t e, const char* where);
 void* ctx_alloc(hg_ctx* ctx, size_t bytes, cudaStream_t st);
 void ctx_free(hg_ctx* ctx, void* p, size_t bytes, cudaStream_t st);
+
+// hg_l2_loss: fixed grid and its scratch (block partials + finish counter)
+constexpr int LOSS_BLOCKS = 304;
+constexpr size_t LOSS_SCRATCH_BYTES = sizeof(double) * LOSS_BLOCKS + 256;
 hg_status ws_ensure(hg_state* s, int id, size_t bytes, cudaStream_t st);
 hg_status state_create(hg_ctx* ctx, hg_state** out);
 hg_status build_views(hg_state* s, const hg_camera* cams, int V, const hg_render_opts* o, hg::FrameGeom& g);

@@ -21,7 +21,7 @@ namespace hg {
 
 namespace {
 
-constexpr int PROJ_THREADS = 256;
+constexpr int PROJ_THREADS = 128;  // 7 CTAs per SM: more staged copies in flight than 3 x 256
 
 template <int DEG>
 struct ProjSmem {

@@ -30,7 +30,13 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_graph_launch", "hg_graph_set_cameras", "hg_graph_sync", "hg_graph_kernels", "hg_graph_destroy",
            "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward", "hg_autotune",
            "hg_serve_create", "hg_serve_add_scene", "hg_serve_submit", "hg_serve_poll", "hg_serve_wait",
-           "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats", "hg_serve_destroy"]
+           "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats", "hg_serve_destroy", "hg_l2_loss",
+           "hg_adam_step"]
+
+
+class AdamOpts(C.Structure):
+    _fields_ = [("lr", C.c_float * 5), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32)]
 
 
 class HgError(RuntimeError):
@@ -144,6 +150,11 @@ def load(path: str = LIB_PATH):
                                 C.POINTER(RenderOpts), C.POINTER(TuneResult), C.c_int, C.POINTER(C.c_int), C.c_void_p]
     lib.hg_render_backward.restype = C.c_int
     lib.hg_render_backward.argtypes = [C.c_void_p] + [C.c_void_p] * 7
+    lib.hg_l2_loss.restype = C.c_int
+    lib.hg_l2_loss.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hg_adam_step.restype = C.c_int
+    lib.hg_adam_step.argtypes = [C.c_void_p, C.c_void_p * 5, C.c_void_p * 5, C.c_void_p * 5, C.POINTER(AdamOpts),
+                                 C.c_void_p]
     lib.hg_segmented_sort_noalloc.restype = C.c_int
     lib.hg_segmented_sort_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p]
@@ -371,18 +382,86 @@ def segmented_sort_noalloc(seg_off, keys, vals, keys_out, vals_out, stream=None)
                                                 C.c_void_p(vals_out.data_ptr()), _stream_ptr(stream)))
 
 
-def render_backward(state: State, scene: GpuScene, dl_drgb, stream=None):
+def render_backward(state: State, scene: GpuScene, dl_drgb, stream=None, out=None):
     """hg_render_backward for the frame saved in `state`: returns device
-    tensors (d_means, d_log_scales, d_quats, d_opacity_logits, d_sh)."""
+    tensors (d_means, d_log_scales, d_quats, d_opacity_logits, d_sh), written
+    into `out` when given."""
     import torch
     dev = torch.device("cuda", scene.ctx.device)
     n, k = scene.n, (scene.sh_degree + 1) ** 2
-    outs = [torch.empty((n, 3), device=dev), torch.empty((n, 3), device=dev), torch.empty((n, 4), device=dev),
-            torch.empty((n,), device=dev), torch.empty((n, k, 3), device=dev)]
+    outs = out if out is not None else [torch.empty((n, 3), device=dev), torch.empty((n, 3), device=dev),
+                                        torch.empty((n, 4), device=dev), torch.empty((n,), device=dev),
+                                        torch.empty((n, k, 3), device=dev)]
     g = dl_drgb.contiguous().to(torch.float32)
     check(scene.ctx.lib.hg_render_backward(state.h, C.c_void_p(g.data_ptr()),
                                            *[C.c_void_p(o.data_ptr()) for o in outs], _stream_ptr(stream)))
     return tuple(outs)
+
+
+def l2_loss(ctx: Context, rgb, target, dl_drgb=None, loss=None, stream=None):
+    """hg_l2_loss: returns (loss as a device float64 tensor of one element,
+    dL/d rgb as a device float32 tensor)."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    rgb = rgb.contiguous()
+    target = target.contiguous()
+    if dl_drgb is None:
+        dl_drgb = torch.empty_like(rgb)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
+    check(ctx.lib.hg_l2_loss(ctx.h, C.c_void_p(rgb.data_ptr()), C.c_void_p(target.data_ptr()), rgb.numel(),
+                             C.c_void_p(dl_drgb.data_ptr()), C.c_void_p(loss.data_ptr()), _stream_ptr(stream)))
+    return loss, dl_drgb
+
+
+def adam_step(scene: GpuScene, grads, m, v, step: int, lr, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """hg_adam_step on the scene's parameter arrays (five groups: means,
+    log_scales, quats, opacity_logits, sh); lr is a number or five numbers."""
+    lrs = list(lr) if hasattr(lr, "__len__") else [lr] * 5
+    o = AdamOpts((C.c_float * 5)(*lrs), beta1, beta2, eps, step)
+    arr = C.c_void_p * 5
+    check(scene.ctx.lib.hg_adam_step(scene.h, arr(*[x.data_ptr() for x in grads]), arr(*[x.data_ptr() for x in m]),
+                                     arr(*[x.data_ptr() for x in v]), C.byref(o), _stream_ptr(stream)))
+
+
+class Trainer:
+    """Densification-free optimisation of a scene against target images
+    (Sec. 6): per step hg_render (saving for the backward), hg_l2_loss,
+    hg_render_backward and hg_adam_step, all on one stream.  The parameters
+    are the caller's tensors (a borrowed scene), updated in place."""
+
+    # 3DGS-style learning rates: means, log_scales, quats, opacity logits, SH
+    DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3)
+
+    def __init__(self, ctx: Context, params, sh_degree: int, cams, target, opts: Options | None = None,
+                 lr=DEFAULT_LR, stream=None):
+        import torch
+        self.ctx, self.cams, self.stream = ctx, list(cams), stream
+        self.params = [p.contiguous() for p in params]
+        self.scene = GpuScene(ctx, *self.params, sh_degree=sh_degree, borrow=True)
+        self.opts = Options(**{**(opts or Options()).__dict__, "save_for_backward": True})
+        self.target = target.contiguous()
+        self.state = State(ctx)
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.lr, self.t = lr, 0
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.target.device)
+        self.dl = torch.empty_like(self.target)
+        self.grads = [torch.empty_like(p) for p in self.params]
+
+    def step(self):
+        """One optimisation step; returns the loss of the rendered frame as a
+        device tensor (reading it synchronises)."""
+        rgb, _ = render(self.scene, self.cams, self.opts, state=self.state, stream=self.stream, with_T=False)
+        l2_loss(self.ctx, rgb, self.target, self.dl, self.loss, stream=self.stream)
+        render_backward(self.state, self.scene, self.dl, stream=self.stream, out=self.grads)
+        self.t += 1
+        adam_step(self.scene, self.grads, self.m, self.v, self.t, self.lr, stream=self.stream)
+        return self.loss
+
+    def close(self):
+        self.state.close()
+        self.scene.close()
 
 
 class _RenderFn:
