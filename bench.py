@@ -439,6 +439,7 @@ def gpu_arm(args):
     cams = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)
     ctx = higs.Context(torch.cuda.current_device())
     gs = higs.GpuScene.from_scene(ctx, scene)
+    scene16 = scene if not args.skip_plain else None
     del scene
     stream = torch.cuda.Stream()
     pk = peaks()
@@ -464,6 +465,19 @@ def gpu_arm(args):
     stage_ms = {k: statistics.mean(s["ms_" + k] for s in stats) for k in
                 ("project", "partition", "sort", "raster", "merge")}
     top, rl = roofline(stage_ms, stats, gs.n, pk, clocks.get("sm_mhz") or pk["sm_max_mhz"])
+
+    # the same workload with the SH coefficients stored in half precision
+    # (float32 arithmetic): 140 instead of 236 bytes read per gaussian
+    gs16 = higs.GpuScene.from_scene(ctx, scene16, sh_storage=higs.SH_F16) if scene16 is not None else None
+    sh_f16 = None
+    if gs16 is not None:
+        hsteps = max(3, min(args.steps, 10))
+        hms, hstats, _ = time_graph(higs, gs16, cams, opts, hsteps, min(args.warmup, 3), rank, world, stream)
+        hvalue, hms = job_throughput(hms, hsteps * VIEWS, world)
+        sh_f16 = {"value": round(hvalue, 2), "unit": UNIT, "ms_per_step": round(hms / hsteps, 3),
+                  "project_ms": round(statistics.mean(s_["ms_project"] for s_ in hstats), 4)}
+        gs16.close()
+    del scene16
 
     plain = None
     if not args.skip_plain:
@@ -522,6 +536,7 @@ def gpu_arm(args):
         "gpu_launches": int(kernels * args.steps),
         "clocks": clocks,
         "plain_path": plain,
+        "sh_f16": sh_f16,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "frame_stats": {
             "pairs_per_step": int(statistics.mean(s["n_pairs"] for s in s0)),

@@ -81,8 +81,16 @@ typedef struct {
   const float* log_scales;
   const float* quats;
   const float* opacity_logits;
-  const float* sh;
+  const void* sh;     /* [n][(deg+1)^2][3] of the element type sh_storage */
+  int32_t sh_storage; /* HG_SH_F32, HG_SH_F16 or HG_SH_BF16 */
+  int32_t pad;
 } hg_scene_desc;
+
+/* Storage type of the SH coefficients (the projection computes in float32
+ * either way; half storage halves the bytes the projection reads per
+ * gaussian at degree 3, 236 -> 140).  Scenes with half SH render and serve;
+ * hg_render_backward and hg_adam_step need float32 SH. */
+enum { HG_SH_F32 = 0, HG_SH_F16 = 1, HG_SH_BF16 = 2 };
 
 /* Pinhole camera: world->camera 4x4 row-major (x right, y down, z forward),
  * focal lengths and principal point in pixels; pixel (i, j) has its centre

@@ -25,11 +25,13 @@ so that it is reproducible bit for bit:
              of log2 from frexp (z = m 2^k, m in [0.5, 1)):
              lb(z) = k + (B m + A), A = -475/256, B = 123/64, a line above
              log2(m) on [0.5, 1] (log2 m <= B m + A - 0.00098; gap <= 0.105)
-    band   rows [ya, yb] of the macro row; dy range [ya - my, yb - my]
-           clipped to +-(hy (1 + 2^-10) + 2^-6), hy = sqrt(E) / L2
-    x span the extremes of (-L1 dy -+ sqrt(E - (L2 dy)^2)) / L0 over the dy
-           range (at its ends or at dy = -+L1 sqrt(E) / (L2 sqrt(L1^2 + L2^2))),
-           widened by 2^-6 + 2^-10 |offset| pixels, clamped to +-2^30
+    band   rows [ya, yb] of the macro row; it meets the ellipse when
+           [ya - my, yb - my] meets +-(hy (1 + 2^-10) + 2^-6), hy = sqrt(E) / L2
+    x span the extremes of (-L1 dy -+ sqrt(E - (L2 dy)^2)) / L0 over the
+           band's part of [-hy, hy]: at the ellipse's leftmost / rightmost
+           point when the band holds it, else at the band end nearer to it
+           (the edges are convex / concave), widened by 2^-6 + 2^-10 |offset|
+           pixels, clamped to +-2^30 (see ellipse_span for the op order)
     cols   [floor(ceil(xl) / Bx), floor(floor(xr) / Bx)] within the rectangle
 It is conservative for the blend test (q <= 9 and alpha >= 1/255, i.e.
 q log2(e) / 2 <= min(9 log2(e) / 2, log2(255 o))): the margins cover float32
@@ -110,36 +112,51 @@ def ellipse_span(mx, my, L0, L1, L2, E, ya, yb):
     """x span [xl, xr] (pixel-centre coordinates, widened) of the ellipse
     over the rows [ya, yb] (float32 arrays, one entry per (gaussian, band)).
     Returns (xl, xr, meet, ok): meet = False when the band misses the
-    ellipse, ok = False for degenerate factors."""
+    ellipse, ok = False for degenerate factors.
+
+    Per gaussian: sE = sqrt(E), hy = sE / L2 (the ellipse's y half-extent),
+    the leftmost point at dy_l = L1 sE / (L2 sqrt(L1^2 + L2^2)) (the rightmost
+    at -dy_l) and its offset x_l = (-L1 dy_l - h(dy_l)) / L0, x_r = -x_l,
+    h(dy) = sqrt(max(0, E - (L2 dy)^2)).  Per band: the band meets the
+    ellipse when it meets [-hy', hy'] (hy' = hy (1 + 2^-10) + 2^-6); the
+    left edge (-L1 dy - h(dy)) / L0 is convex in dy, so over the band's part
+    [a, b] of [-hy, hy] its minimum is at dy_l when dy_l is in [a, b], else at
+    the end nearer to dy_l (likewise the right edge, concave, with -dy_l).  A
+    band that meets only the widened range is evaluated at the tip (a = b =
+    -+hy).  Divisions by L0 and L2 are products with their reciprocals."""
     mx, my, L0, L1, L2, E = (np.asarray(v, F32) for v in (mx, my, L0, L1, L2, E))
     ya, yb = np.asarray(ya, F32), np.asarray(yb, F32)
     ok = (L0 > 0) & (L2 > 0)
     L0s = np.where(ok, L0, F32(1))
     L2s = np.where(ok, L2, F32(1))
     live = E > 0
-    sE = np.sqrt(np.maximum(E, F32(0)))
-    hy = sE / L2s
+    Ep = np.maximum(E, F32(0))
+    sE = np.sqrt(Ep)
+    iL0 = F32(1) / L0s
+    iL2 = F32(1) / L2s
+    hy = sE * iL2
     hyw = hy * F32(1.0 + 2.0 ** -10) + ELL_PAD
-    a = np.maximum(ya - my, -hyw)
-    b = np.minimum(yb - my, hyw)
-    meet = live & (a <= b)
+    ra, rb = ya - my, yb - my
+    meet = live & (np.maximum(ra, -hyw) <= np.minimum(rb, hyw))
 
     def half(dy):
         t = L2s * dy
-        return np.sqrt(np.maximum(F32(0), E - t * t))
+        return np.sqrt(np.maximum(F32(0), Ep - t * t))
 
-    def xlo(dy):
-        return (-L1 * dy - half(dy)) / L0s
-
-    def xhi(dy):
-        return (-L1 * dy + half(dy)) / L0s
-
-    lo = np.minimum(xlo(a), xlo(b))
-    hi = np.maximum(xhi(a), xhi(b))
     nrm = np.sqrt(L1 * L1 + L2s * L2s)
     dyl = (L1 * sE) / (L2s * nrm)
-    lo = np.where((dyl >= a) & (dyl <= b), np.minimum(lo, xlo(dyl)), lo)
-    hi = np.where((-dyl >= a) & (-dyl <= b), np.maximum(hi, xhi(-dyl)), hi)
+    x_l = (-L1 * dyl - half(dyl)) * iL0
+    x_r = (L1 * dyl + half(dyl)) * iL0
+    a = np.maximum(ra, -hy)
+    b = np.minimum(rb, hy)
+    tip = np.where(rb < -hy, -hy, hy)
+    inside = a <= b
+    a = np.where(inside, a, tip)
+    b = np.where(inside, b, tip)
+    dlo = np.where(dyl < a, a, b)
+    lo = np.where((dyl >= a) & (dyl <= b), x_l, (-L1 * dlo - half(dlo)) * iL0)
+    dhi = np.where(-dyl < a, a, b)
+    hi = np.where((-dyl >= a) & (-dyl <= b), x_r, (-L1 * dhi + half(dhi)) * iL0)
     xl = (mx + lo) - (np.abs(lo) * ELL_REL + ELL_PAD)
     xr = (mx + hi) + (np.abs(hi) * ELL_REL + ELL_PAD)
     # far outside any image; keeps the integer conversion in range

@@ -149,7 +149,8 @@ extern "C" void hg_ctx_destroy(hg_ctx* ctx) {
 
 // ---------------------------------------------------------------- scenes
 extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_scene** out) {
-  if (!ctx || !d || !out || d->n < 0 || d->sh_degree < 0 || d->sh_degree > 3) {
+  if (!ctx || !d || !out || d->n < 0 || d->sh_degree < 0 || d->sh_degree > 3 || d->sh_storage < HG_SH_F32 ||
+      d->sh_storage > HG_SH_BF16) {
     hg_set_error("hg_create_scene: bad arguments");
     return HG_ERR_INVALID_ARG;
   }
@@ -167,13 +168,15 @@ extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_sce
   s->n = d->n;
   s->deg = d->sh_degree;
   const int K = (d->sh_degree + 1) * (d->sh_degree + 1);
-  const float* src[5] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
+  s->sh_storage = d->sh_storage;
+  const void* src[5] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
   const size_t per[5] = {3, 3, 4, 1, (size_t)K * 3};
+  const size_t esz[5] = {4, 4, 4, 4, d->sh_storage == HG_SH_F32 ? 4u : 2u};
   bool aligned = true;
   for (int i = 0; i < 5; ++i) aligned = aligned && (((uintptr_t)src[i]) & 15) == 0;
   s->owned = !(d->borrow && aligned);
   for (int i = 0; i < 5; ++i) {
-    s->bytes[i] = per[i] * sizeof(float) * (size_t)d->n;
+    s->bytes[i] = per[i] * esz[i] * (size_t)d->n;
     if (s->owned) {
       s->arr[i] = (float*)ctx_alloc(ctx, s->bytes[i], nullptr);
       if (!s->arr[i]) {
@@ -189,7 +192,7 @@ extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_sce
         }
       }
     } else {
-      s->arr[i] = const_cast<float*>(src[i]);
+      s->arr[i] = (float*)const_cast<void*>(src[i]);
     }
   }
   *out = s;
@@ -365,6 +368,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pj.quats = in.scene->arr[2];
     pj.opacity_logits = in.scene->arr[3];
     pj.sh = in.scene->arr[4];
+    pj.sh_storage = in.scene->sh_storage;
     pj.splats = (o->flags & HG_FLAG_KEEP_SPLATS) ? (hg_splat*)s->bufs[B_SPLATS].p : nullptr;
     HG_TRY(launch_project(pj, in.scene->deg, st), "project");
   }

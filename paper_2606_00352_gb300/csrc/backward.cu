@@ -520,6 +520,10 @@ extern "C" hg_status hg_render_backward(hg_state* s, const float* dL_drgb, float
     hg_set_error("hg_render_backward: the frame was not rendered on the HiGS path with save_for_backward");
     return HG_ERR_INVALID_ARG;
   }
+  if (s->scene->sh_storage != HG_SH_F32) {
+    hg_set_error("hg_render_backward: the scene stores its SH in half precision (training needs float32)");
+    return HG_ERR_INVALID_ARG;
+  }
   cudaSetDevice(s->ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   const FrameGeom& g = s->geom;

@@ -32,8 +32,9 @@ __device__ __forceinline__ bool macro_rect(int px, int py, int rad, int bw, int 
 //          from z = m 2^k, m in [0.5, 1) (A = -475/256, B = 123/64: a line
 //          above log2 on [0.5, 1]), an upper bound of the blend-test level
 //   band   rows [ya, yb]: the x extremes of the ellipse
-//          (L0 dx + L1 dy)^2 + (L2 dy)^2 <= E over the band, at the band
-//          ends or at the leftmost / rightmost points, widened by
+//          (L0 dx + L1 dy)^2 + (L2 dy)^2 <= E over the band's part of
+//          [-hy, hy], at the leftmost / rightmost point when the band holds
+//          it, else at the band end nearer to it, widened by
 //          2^-6 + 2^-10 |offset| pixels
 constexpr float ELL_A = -475.f / 256.f;
 constexpr float ELL_B = 123.f / 64.f;
@@ -55,24 +56,54 @@ __device__ __forceinline__ float ell_half(float L2, float E, float dy) {
   return __fsqrt_rn(fmaxf(0.f, __fsub_rn(E, __fmul_rn(t, t))));
 }
 
-// x span of the ellipse over rows [ya, yb]; false when the band misses it.
-__device__ __forceinline__ bool ell_span(float mx, float my, float L0, float L1, float L2, float E, float ya,
-                                         float yb, float& xl, float& xr) {
-  const float sE = __fsqrt_rn(fmaxf(E, 0.f));
-  const float hy = __fdiv_rn(sE, L2);
-  const float hyw = __fadd_rn(__fmul_rn(hy, 1.f + ELL_REL), ELL_PAD);
-  const float a = fmaxf(__fsub_rn(ya, my), -hyw);
-  const float b = fminf(__fsub_rn(yb, my), hyw);
-  if (!(E > 0.f) || !(a <= b)) return false;
-  const float nL1 = -L1;
-  auto xlo = [&](float dy) { return __fdiv_rn(__fsub_rn(__fmul_rn(nL1, dy), ell_half(L2, E, dy)), L0); };
-  auto xhi = [&](float dy) { return __fdiv_rn(__fadd_rn(__fmul_rn(nL1, dy), ell_half(L2, E, dy)), L0); };
-  float lo = fminf(xlo(a), xlo(b));
-  float hi = fmaxf(xhi(a), xhi(b));
+// Per-gaussian part of the ellipse test (L0, L2 > 0): the y half-extent hy
+// (and hy widened), the leftmost point dyl with its x offset xl_ext (the
+// rightmost is at -dyl, offset xr_ext), reciprocals of L0.
+struct EllGauss {
+  float E, hy, hyw, dyl, x_l, x_r, iL0;
+};
+
+__device__ __forceinline__ EllGauss ell_gauss(float L0, float L1, float L2, float E) {
+  EllGauss g;
+  g.E = fmaxf(E, 0.f);
+  const float sE = __fsqrt_rn(g.E);
+  g.iL0 = __fdiv_rn(1.f, L0);
+  const float iL2 = __fdiv_rn(1.f, L2);
+  g.hy = __fmul_rn(sE, iL2);
+  g.hyw = __fadd_rn(__fmul_rn(g.hy, 1.f + ELL_REL), ELL_PAD);
   const float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(L1, L1), __fmul_rn(L2, L2)));
-  const float dyl = __fdiv_rn(__fmul_rn(L1, sE), __fmul_rn(L2, nrm));
-  if (dyl >= a && dyl <= b) lo = fminf(lo, xlo(dyl));
-  if (-dyl >= a && -dyl <= b) hi = fmaxf(hi, xhi(-dyl));
+  g.dyl = __fdiv_rn(__fmul_rn(L1, sE), __fmul_rn(L2, nrm));
+  const float h = ell_half(L2, g.E, g.dyl);
+  const float t = __fmul_rn(-L1, g.dyl);
+  g.x_l = __fmul_rn(__fsub_rn(t, h), g.iL0);
+  g.x_r = __fmul_rn(__fadd_rn(__fmul_rn(L1, g.dyl), h), g.iL0);
+  return g;
+}
+
+// x span of the ellipse over rows [ya, yb]; false when the band misses it.
+// The left edge (-L1 dy - h(dy)) / L0 is convex in dy: over the band's part
+// [a, b] of [-hy, hy] its minimum is at dyl when dyl is in [a, b], else at
+// the end nearer to dyl (the right edge likewise with -dyl).
+__device__ __forceinline__ bool ell_span(const EllGauss& g, float mx, float my, float L1, float L2, float ya,
+                                         float yb, bool live, float& xl, float& xr) {
+  const float ra = __fsub_rn(ya, my), rb = __fsub_rn(yb, my);
+  if (!live || !(fmaxf(ra, -g.hyw) <= fminf(rb, g.hyw))) return false;
+  float a = fmaxf(ra, -g.hy), b = fminf(rb, g.hy);
+  if (!(a <= b)) a = b = rb < -g.hy ? -g.hy : g.hy;  // meets only the widened range: the tip
+  const float nL1 = -L1;
+  float lo, hi;
+  if (g.dyl >= a && g.dyl <= b) {
+    lo = g.x_l;
+  } else {
+    const float d = g.dyl < a ? a : b;
+    lo = __fmul_rn(__fsub_rn(__fmul_rn(nL1, d), ell_half(L2, g.E, d)), g.iL0);
+  }
+  if (-g.dyl >= a && -g.dyl <= b) {
+    hi = g.x_r;
+  } else {
+    const float d = -g.dyl < a ? a : b;
+    hi = __fmul_rn(__fadd_rn(__fmul_rn(nL1, d), ell_half(L2, g.E, d)), g.iL0);
+  }
   xl = __fsub_rn(__fadd_rn(mx, lo), __fadd_rn(__fmul_rn(fabsf(lo), ELL_REL), ELL_PAD));
   xr = __fadd_rn(__fadd_rn(mx, hi), __fadd_rn(__fmul_rn(fabsf(hi), ELL_REL), ELL_PAD));
   xl = fminf(fmaxf(xl, -ELL_LIM), ELL_LIM);
@@ -95,10 +126,11 @@ __device__ __forceinline__ uint4 bin_cells(float mx, float my, int rad, float L0
   unsigned long long m = cells == 64 ? ~0ull : ((1ull << cells) - 1ull);
   if (ellipse && cells > 1 && L0 > 0.f && L2 > 0.f) {
     const float E = ell_level(o);
+    const EllGauss g = ell_gauss(L0, L1, L2, E);
     m = 0;
     for (int y = y0; y <= y1; ++y) {
       float xl, xr;
-      if (!ell_span(mx, my, L0, L1, L2, E, (float)(y * bh), (float)(y * bh + bh - 1), xl, xr)) continue;
+      if (!ell_span(g, mx, my, L1, L2, (float)(y * bh), (float)(y * bh + bh - 1), E > 0.f, xl, xr)) continue;
       const int c0 = max(x0, floordiv((int)ceilf(xl), bw));
       const int c1 = min(x1, floordiv((int)floorf(xr), bw));
       if (c0 > c1) continue;

@@ -20,6 +20,7 @@ struct hg_scene {
   int64_t n = 0;
   int deg = 0;
   bool owned = true;
+  int sh_storage = HG_SH_F32;  // element type of arr[4]
   float* arr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // means, log_scales, quats, logits, sh
   size_t bytes[5] = {0, 0, 0, 0, 0};
 };

@@ -9,7 +9,8 @@ struct ProjectArgs {
   const float* log_scales;
   const float* quats;
   const float* opacity_logits;
-  const float* sh;
+  const void* sh;         // element type sh_storage (HG_SH_*)
+  int sh_storage;
   long long n;
   const ViewDesc* views;  // device
   int n_views;

@@ -13,6 +13,9 @@
 // bin and rec are written for visible entries only.
 // l' are the Cholesky factors of the conic prescaled by sqrt(log2(e)/2), so the
 // rasteriser evaluates alpha = o exp2(-((l0' dx + l1' dy)^2 + (l2' dy)^2)).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "binning.cuh"
 #include "blend.cuh"
 #include "kernels.cuh"
@@ -23,31 +26,37 @@ namespace {
 
 constexpr int PROJ_THREADS = 128;  // 7 CTAs per SM: more staged copies in flight than 3 x 256
 
-template <int DEG>
+__device__ __forceinline__ float sh_f(float x) { return x; }
+__device__ __forceinline__ float sh_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float sh_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// SH coefficients are staged in their storage type SHT and converted when
+// used (float32 arithmetic either way).
+template <int DEG, typename SHT>
 struct ProjSmem {
   static constexpr int K = (DEG + 1) * (DEG + 1);
   float means[PROJ_THREADS * 3];
   float scales[PROJ_THREADS * 3];
   float4 quats[PROJ_THREADS];
   float logits[PROJ_THREADS];
-  float sh[PROJ_THREADS * K * 3];
+  alignas(16) SHT sh[PROJ_THREADS * K * 3];
   uint64_t bar;
   ViewDesc views[1];  // [n_views], sized at launch
 };
 
-template <int DEG>
+template <int DEG, typename SHT>
 __host__ __device__ constexpr size_t proj_smem_bytes(int n_views) {
-  return sizeof(ProjSmem<DEG>) + sizeof(ViewDesc) * (size_t)(n_views > 1 ? n_views - 1 : 0);
+  return sizeof(ProjSmem<DEG, SHT>) + sizeof(ViewDesc) * (size_t)(n_views > 1 ? n_views - 1 : 0);
 }
 
 // SH colour of one band for up to VG views: acc[v] += sum_m Y_lm(d_v) c_lm.
-template <int L, int VG>
-__device__ __forceinline__ void sh_band(const float* __restrict__ sh_g, const float (&d)[VG][3], float (&acc)[VG][3],
+template <int L, int VG, typename SHT>
+__device__ __forceinline__ void sh_band(const SHT* __restrict__ sh_g, const float (&d)[VG][3], float (&acc)[VG][3],
                                         int nv) {
   constexpr int B = 2 * L + 1, OFF = L * L;
   float c[B * 3];
 #pragma unroll
-  for (int k = 0; k < B * 3; ++k) c[k] = sh_g[OFF * 3 + k];
+  for (int k = 0; k < B * 3; ++k) c[k] = sh_f(sh_g[OFF * 3 + k]);
 #pragma unroll
   for (int v = 0; v < VG; ++v) {
     if (v >= nv) break;
@@ -102,12 +111,13 @@ __device__ __forceinline__ void sh_band(const float* __restrict__ sh_g, const fl
 // views, each band's coefficients read from shared memory once per group.
 // Culled (view, gaussian) entries write nothing: consumers test the
 // visibility bits first.
-template <int DEG>
+template <int DEG, typename SHT>
 __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int VG = 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ProjSmem<DEG>& s = *reinterpret_cast<ProjSmem<DEG>*>(smem_raw);
+  ProjSmem<DEG, SHT>& s = *reinterpret_cast<ProjSmem<DEG, SHT>*>(smem_raw);
+  const SHT* sh_in = reinterpret_cast<const SHT*>(a.sh);
   const int tid = threadIdx.x;
   const long long i0 = (long long)blockIdx.x * PROJ_THREADS;
   const int cnt = (int)min((long long)PROJ_THREADS, a.n - i0);
@@ -123,13 +133,13 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
     __syncthreads();
     if (tid == 0) {
       const uint32_t b3 = PROJ_THREADS * 12, b4 = PROJ_THREADS * 16, b1 = PROJ_THREADS * 4,
-                     bsh = PROJ_THREADS * K * 12;
+                     bsh = PROJ_THREADS * K * 3 * (uint32_t)sizeof(SHT);
       mbar_arrive_expect_tx(&s.bar, 2 * b3 + b4 + b1 + bsh);
       tma_load_1d(s.means, a.means + i0 * 3, b3, &s.bar);
       tma_load_1d(s.scales, a.log_scales + i0 * 3, b3, &s.bar);
       tma_load_1d(s.quats, a.quats + i0 * 4, b4, &s.bar);
       tma_load_1d(s.logits, a.opacity_logits + i0, b1, &s.bar);
-      tma_load_1d(s.sh, a.sh + i0 * K * 3, bsh, &s.bar);
+      tma_load_1d(s.sh, sh_in + i0 * K * 3, bsh, &s.bar);
     }
   } else {
     for (int j = tid; j < cnt * 3; j += PROJ_THREADS) {
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       s.quats[j] = reinterpret_cast<const float4*>(a.quats)[i0 + j];
       s.logits[j] = a.opacity_logits[i0 + j];
     }
-    for (int j = tid; j < cnt * K * 3; j += PROJ_THREADS) s.sh[j] = a.sh[i0 * K * 3 + j];
+    for (int j = tid; j < cnt * K * 3; j += PROJ_THREADS) s.sh[j] = sh_in[i0 * K * 3 + j];
   }
   // the view table, while the copies are in flight
   {
@@ -273,7 +283,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   }
 
   // view-dependent colour: max(0, SH(d) + 0.5), d = normalise(mean - campos)
-  const float* sh_g = s.sh + tid * K * 3;
+  const SHT* sh_g = s.sh + tid * K * 3;
   const bool keep = a.splats != nullptr && valid;
   for (int v0 = 0; v0 < nv; v0 += VG) {
     const int g = min(VG, nv - v0);
@@ -290,10 +300,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       d[v][2] = dz * dn;
       acc[v][0] = acc[v][1] = acc[v][2] = 0.f;
     }
-    sh_band<0, VG>(sh_g, d, acc, g);
-    if (DEG >= 1) sh_band<1, VG>(sh_g, d, acc, g);
-    if (DEG >= 2) sh_band<2, VG>(sh_g, d, acc, g);
-    if (DEG >= 3) sh_band<3, VG>(sh_g, d, acc, g);
+    sh_band<0, VG, SHT>(sh_g, d, acc, g);
+    if (DEG >= 1) sh_band<1, VG, SHT>(sh_g, d, acc, g);
+    if (DEG >= 2) sh_band<2, VG, SHT>(sh_g, d, acc, g);
+    if (DEG >= 3) sh_band<3, VG, SHT>(sh_g, d, acc, g);
 #pragma unroll
     for (int v = 0; v < VG; ++v) {
       if (v >= g) break;
@@ -352,16 +362,25 @@ __global__ void k_splats_to_records(const hg_splat* sp, long long total, long lo
 
 }  // namespace
 
-template <int DEG>
-static cudaError_t launch_project_deg(const ProjectArgs& a, cudaStream_t st) {
-  size_t sm = proj_smem_bytes<DEG>(a.n_views);
-  cudaError_t e = cudaFuncSetAttribute(k_project<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <int DEG, typename SHT>
+static cudaError_t launch_project_t(const ProjectArgs& a, cudaStream_t st) {
+  size_t sm = proj_smem_bytes<DEG, SHT>(a.n_views);
+  cudaError_t e = cudaFuncSetAttribute(k_project<DEG, SHT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   long long blocks = (a.n + PROJ_THREADS - 1) / PROJ_THREADS;
   if (blocks == 0) return cudaSuccess;
-  k_project<DEG><<<(unsigned)blocks, PROJ_THREADS, sm, st>>>(a);
+  k_project<DEG, SHT><<<(unsigned)blocks, PROJ_THREADS, sm, st>>>(a);
   note_launch();
   return cudaGetLastError();
+}
+
+template <int DEG>
+static cudaError_t launch_project_deg(const ProjectArgs& a, cudaStream_t st) {
+  switch (a.sh_storage) {
+    case HG_SH_F16: return launch_project_t<DEG, __half>(a, st);
+    case HG_SH_BF16: return launch_project_t<DEG, __nv_bfloat16>(a, st);
+    default: return launch_project_t<DEG, float>(a, st);
+  }
 }
 
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st) {

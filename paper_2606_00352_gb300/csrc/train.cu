@@ -130,6 +130,10 @@ extern "C" hg_status hg_adam_step(hg_scene* scene, const float* const grads[5], 
     hg_set_error("hg_adam_step: bad arguments");
     return HG_ERR_INVALID_ARG;
   }
+  if (scene->sh_storage != HG_SH_F32) {
+    hg_set_error("hg_adam_step: the scene stores its SH in half precision (training needs float32)");
+    return HG_ERR_INVALID_ARG;
+  }
   AdamArgs a{};
   const long long k3 = (long long)(scene->deg + 1) * (scene->deg + 1) * 3;
   const long long counts[5] = {scene->n * 3, scene->n * 3, scene->n * 4, scene->n, scene->n * k3};

@@ -48,7 +48,11 @@ class HgError(RuntimeError):
 class SceneDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("borrow", C.c_int32),
                 ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
-                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("sh_storage", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+SH_F32, SH_F16, SH_BF16 = 0, 1, 2
 
 
 class CameraC(C.Structure):
@@ -250,30 +254,36 @@ class Context:
 
 class GpuScene:
     """Device-resident scene (hg_create_scene).  Arrays are torch CUDA tensors
-    (float32, contiguous); borrow=True keeps references instead of copying."""
+    (float32, contiguous; SH in the storage type sh_storage, converted with
+    round-to-nearest-even when given in another type); borrow=True keeps
+    references instead of copying."""
 
     def __init__(self, ctx: Context, means, log_scales, quats, opacity_logits, sh, sh_degree: int,
-                 borrow: bool = False):
+                 borrow: bool = False, sh_storage: int = SH_F32):
         import torch
         dev = torch.device("cuda", ctx.device)
 
-        def t(x):
-            x = torch.as_tensor(x, dtype=torch.float32, device=dev)
+        def t(x, dtype=torch.float32):
+            x = torch.as_tensor(x, device=dev)
+            if x.dtype != dtype:
+                x = x.to(torch.float32).to(dtype)
             return x.contiguous()
-        self.tensors = [t(means), t(log_scales), t(quats), t(opacity_logits), t(sh)]
+        sh_t = {SH_F32: torch.float32, SH_F16: torch.float16, SH_BF16: torch.bfloat16}[sh_storage]
+        self.tensors = [t(means), t(log_scales), t(quats), t(opacity_logits), t(sh, sh_t)]
         n = self.tensors[0].shape[0]
-        d = SceneDesc(n, sh_degree, int(borrow), *[x.data_ptr() for x in self.tensors])
+        d = SceneDesc(n, sh_degree, int(borrow), *[x.data_ptr() for x in self.tensors], sh_storage, 0)
         h = C.c_void_p()
         torch.cuda.synchronize(dev)
         check(ctx.lib.hg_create_scene(ctx.h, C.byref(d), C.byref(h)))
         self.h, self.ctx, self.n, self.sh_degree, self.borrow = h, ctx, n, sh_degree, borrow
+        self.sh_storage = sh_storage
         if not borrow:
             self.tensors = None
 
     @classmethod
-    def from_scene(cls, ctx: Context, scene, borrow: bool = False):
+    def from_scene(cls, ctx: Context, scene, borrow: bool = False, sh_storage: int = SH_F32):
         return cls(ctx, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
-                   scene.sh_degree, borrow)
+                   scene.sh_degree, borrow, sh_storage)
 
     def close(self):
         if self.h:

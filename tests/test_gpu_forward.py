@@ -247,6 +247,33 @@ def test_image_ellipse_binning_independent_batches(lib, ctx):
     compare_image(imgs[0], ts[0], C.render(P.project(scene, cam)))
 
 
+def _round_sh(sh, storage):
+    """The coefficients a half-precision scene stores (round to nearest even)."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(sh, np.float32))
+    return (t.to(torch.float16) if storage == "f16" else t.to(torch.bfloat16)).to(torch.float32).numpy()
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_half_precision_sh_storage(lib, ctx, storage):
+    """SH stored in half precision, float32 arithmetic: the image equals the
+    oracle's on the same rounded coefficients (Sec. 4.2 colour), and the
+    training entry points refuse the scene."""
+    import torch
+    scene = scenes.cluster_scene(30_000, 8, 1.2, seed=12, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    cams = scenes.scene_orbit(8, 320, 200)[2:4]
+    code = lib.SH_F16 if storage == "f16" else lib.SH_BF16
+    gs = lib.GpuScene.from_scene(ctx, scene, sh_storage=code)
+    st = lib.State(ctx)
+    imgs, ts = render_np(lib, gs, cams, state=st, save_for_backward=True)
+    ref_scene = scene.copy()
+    ref_scene.sh = _round_sh(scene.sh, storage)
+    for v, cam in enumerate(cams):
+        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)))
+    with pytest.raises(lib.HgError):
+        lib.render_backward(st, gs, torch.zeros(sum(c.width * c.height for c in cams) * 3, device="cuda"))
+
+
 def test_image_background_and_multiview(lib, ctx):
     scene = scenes.uniform_scene(8000, seed=6)
     cams = [scenes.look_at((3, 0, 0), width=128, height=128),
