@@ -179,11 +179,11 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       px = s.means[tid * 3 + 0];
       py = s.means[tid * 3 + 1];
       pz = s.means[tid * 3 + 2];
-      sx = expf(s.scales[tid * 3 + 0]);
-      sy = expf(s.scales[tid * 3 + 1]);
-      sz = expf(s.scales[tid * 3 + 2]);
+      sx = __expf(s.scales[tid * 3 + 0]);
+      sy = __expf(s.scales[tid * 3 + 1]);
+      sz = __expf(s.scales[tid * 3 + 2]);
       q = s.quats[tid];
-      op = 1.f / (1.f + expf(-s.logits[tid]));
+      op = __fdividef(1.f, 1.f + __expf(-s.logits[tid]));
     }
     // rotation of the normalised quaternion (w, x, y, z), times the scales
     const float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       const float tx = fmaf(V.vm[0], px, fmaf(V.vm[1], py, fmaf(V.vm[2], pz, V.vm[3])));
       const float ty = fmaf(V.vm[4], px, fmaf(V.vm[5], py, fmaf(V.vm[6], pz, V.vm[7])));
       bool vis = valid && tz > 0.2f;
-      const float itz = 1.f / tz;
+      const float itz = __fdividef(1.f, tz);
       const float limx = 1.3f * V.tan_x, limy = 1.3f * V.tan_y;
       const float ux = fminf(fmaxf(tx * itz, -limx), limx);
       const float uy = fminf(fmaxf(ty * itz, -limy), limy);
@@ -227,11 +227,12 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       const float det = ca * cc - cb * cb;
       vis = vis && det > 0.f;
       const float mid = 0.5f * (ca + cc);
-      const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-      const float rr = ceilf(3.f * sqrtf(lam));
+      const float dq = fmaxf(0.1f, mid * mid - det);
+      const float lam = mid + dq * rsqrtf(dq);
+      const float rr = ceilf(3.f * (lam * rsqrtf(lam)));
       int rad = (int)fminf(rr, (float)RADIUS_MAX);
-      const float mx = fmaf(V.fx, __fdiv_rn(tx, tz), V.cx - 0.5f);
-      const float my = fmaf(V.fy, __fdiv_rn(ty, tz), V.cy - 0.5f);
+      const float mx = fmaf(V.fx, tx * itz, V.cx - 0.5f);
+      const float my = fmaf(V.fy, ty * itz, V.cy - 0.5f);
       vis = vis && rad > 0 && fabsf(mx) < 1e7f && fabsf(my) < 1e7f;
       if (vis) {
         const int x0 = (int)floorf(mx), y0 = (int)floorf(my);
