@@ -96,43 +96,69 @@ __device__ __forceinline__ void blend(PixelAcc& p, float ubase, float dy, const 
 // Per-gaussian level E of the blend test (stored in the record's g2.w).
 __device__ __forceinline__ float blend_level(float o) { return fminf(SUPPORT_E, log2f(255.f * o)); }
 
-// Largest prescaled q a pixel can have and still pass the blend test:
-// alpha >= 1/255 needs o 2^-e >= 1/255, i.e. e <= log2(255 o), and the
-// support is e <= SUPPORT_E.  Slightly enlarged so that float32 rounding in
-// the blend can never pass a pixel this level excludes; negative = nothing.
-__device__ __forceinline__ float support_level(float o) {
-  if (!(o >= ALPHA_MIN)) return -1.f;
-  const float lv = fminf(SUPPORT_E, log2f(255.f * o));
-  return lv * 1.0001f + 1e-4f;
+// Tile-mask geometry of one gaussian (Alg. 1 phase 1, the opacity-threshold
+// ellipse of Sec. 4.5).  The blend test passes only where
+// e = (l0' dx + l1' dy)^2 + (l2' dy)^2 <= E, E = g2.w the record's level.
+// Masks only need to be conservative, so this uses fast approximate
+// arithmetic (rsqrt, fast reciprocal) with margins far above its error: the
+// level is enlarged by 2^-10 relative + 2^-12, the y extent and the row spans
+// by 0.02 px + 2^-10 of the offset.  Computed once per gaussian: the y half
+// extent hy, the leftmost point dyl with its offset x_l (rightmost at -dyl,
+// offset x_r).
+struct MaskGauss {
+  float E, hy, hyw, dyl, x_l, x_r, il0, l1, l2;
+  bool live, ok;
+};
+
+__device__ __forceinline__ float fast_sqrt0(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
+
+__device__ __forceinline__ MaskGauss mask_gauss(const float4& g0, const float4& g1, const float4& g2) {
+  MaskGauss m;
+  m.live = g2.w >= 0.f;
+  m.E = fmaf(g2.w, 1.f + 1.f / 1024.f, 1.f / 4096.f);
+  m.l1 = g0.w;
+  m.l2 = g1.x;
+  m.ok = g0.z > 0.f && g1.x > 0.f;
+  if (!m.ok || !m.live) return m;
+  const float sE = fast_sqrt0(m.E);
+  m.il0 = __fdividef(1.f, g0.z);
+  const float il2 = __fdividef(1.f, g1.x);
+  m.hy = sE * il2;
+  m.hyw = fmaf(m.hy, 1.f + 1.f / 1024.f, 0.02f);
+  m.dyl = m.l1 * sE * il2 * rsqrtf(fmaf(m.l1, m.l1, m.l2 * m.l2));
+  const float t = m.l2 * m.dyl;
+  const float h = fast_sqrt0(fmaf(-t, t, m.E));
+  m.x_l = (-m.l1 * m.dyl - h) * m.il0;
+  m.x_r = (m.l1 * m.dyl + h) * m.il0;
+  return m;
 }
 
-// x-range (pixel-centre coordinates) covered by the ellipse
-// (l0 dx + l1 dy)^2 + (l2 dy)^2 <= E over the rows y in [ya, yb]; false if
-// the rows miss it.  The left edge -(l1 dy + s(dy)) / l0 is convex in dy and
-// the right edge concave, so their extremes lie at the band's ends or at the
-// ellipse's leftmost / rightmost points.  Widened by 0.01 px.
-__device__ __forceinline__ bool ellipse_row_span(const float4& g0, const float4& g1, float E, float ya, float yb,
-                                                 float& xl, float& xr) {
-  const float l0 = g0.z, l1 = g0.w, l2 = g1.x;
-  if (!(l0 > 0.f) || !(l2 > 0.f)) {  // degenerate factors: keep the whole band
-    xl = -1e6f;
-    xr = 1e6f;
-    return true;
+// x span (pixel-centre coordinates) of the gaussian's mask ellipse over the
+// rows [ya, yb]; false when the rows miss it.  The left edge
+// (-l1 dy - h(dy)) / l0 is convex in dy: over the rows' part [a, b] of
+// [-hy, hy] its minimum is at dyl when dyl is in [a, b], else at the end
+// nearer to dyl (the right edge, concave, likewise with -dyl).
+__device__ __forceinline__ bool mask_row_span(const MaskGauss& m, float mx, float my, float ya, float yb, float& xl,
+                                              float& xr) {
+  const float ra = ya - my, rb = yb - my;
+  if (!(fmaxf(ra, -m.hyw) <= fminf(rb, m.hyw))) return false;
+  float a = fmaxf(ra, -m.hy), b = fminf(rb, m.hy);
+  if (!(a <= b)) a = b = rb < -m.hy ? -m.hy : m.hy;
+  float lo, hi;
+  if (m.dyl >= a && m.dyl <= b) {
+    lo = m.x_l;
+  } else {
+    const float d = m.dyl < a ? a : b, t = m.l2 * d;
+    lo = (-m.l1 * d - fast_sqrt0(fmaf(-t, t, m.E))) * m.il0;
   }
-  const float sE = sqrtf(E);
-  const float hy = sE / l2;
-  const float a = fmaxf(ya - g0.y, -hy), b = fminf(yb - g0.y, hy);
-  if (a > b) return false;
-  const float il0 = 1.f / l0;
-  const float nrm = sqrtf(fmaf(l1, l1, l2 * l2));
-  const float dyl = l1 * sE / (l2 * nrm);  // leftmost point of the ellipse
-  auto half = [&](float dy) { return sqrtf(fmaxf(0.f, fmaf(-(l2 * dy), l2 * dy, E))); };
-  float lo = fminf((-l1 * a - half(a)) * il0, (-l1 * b - half(b)) * il0);
-  float hi = fmaxf((-l1 * a + half(a)) * il0, (-l1 * b + half(b)) * il0);
-  if (dyl >= a && dyl <= b) lo = fminf(lo, (-l1 * dyl - half(dyl)) * il0);
-  if (-dyl >= a && -dyl <= b) hi = fmaxf(hi, (l1 * dyl + half(-dyl)) * il0);
-  xl = fmaxf(g0.x + lo - 0.01f, -1e6f);
-  xr = fminf(g0.x + hi + 0.01f, 1e6f);
+  if (-m.dyl >= a && -m.dyl <= b) {
+    hi = m.x_r;
+  } else {
+    const float d = -m.dyl < a ? a : b, t = m.l2 * d;
+    hi = (-m.l1 * d + fast_sqrt0(fmaf(-t, t, m.E))) * m.il0;
+  }
+  xl = fmaxf(mx + lo - fmaf(fabsf(lo), 1.f / 1024.f, 0.02f), -1e6f);
+  xr = fminf(mx + hi + fmaf(fabsf(hi), 1.f / 1024.f, 0.02f), 1e6f);
   return xl <= xr;
 }
 

@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 
 // Phase 1 of a processing unit: every warp takes mini-batches of 32 staged
 // gaussians, computes each gaussian's render-tile mask inside the macro-tile
-// (3-sigma rectangle refined by the opacity-aware ellipse per tile row) and
+// (3-sigma rectangle refined by the ellipse of the blend test per tile row) and
 // transposes the 32 x M bit matrix so that s_mask[k * M + t] holds, for tile
 // t, the bits of the mini-batch-k gaussians that overlap it.
 template <int MW, int MH>
@@ -41,28 +41,23 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
     const uint32_t j = (uint32_t)k * 32 + lane;
     unsigned long long gm = 0;
     if (j < count) {
-      const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1];
+      const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
       int x0, x1, y0, y1;
       tile_rect(g0, g1, x0, x1, y0, y1);
       x0 = max(max(x0, mtx0), 0) - mtx0;
       x1 = min(min(x1, mtx0 + MW - 1), V.tiles_x - 1) - mtx0;
       y0 = max(max(y0, mty0), 0) - mty0;
       y1 = min(min(y1, mty0 + MH - 1), V.tiles_y - 1) - mty0;
-      if (x0 <= x1 && y0 <= y1) {
-        const float E = support_level(g1.y);
+      const MaskGauss mg = mask_gauss(g0, g1, g2);
+      if (x0 <= x1 && y0 <= y1 && mg.live) {
         for (int y = y0; y <= y1; ++y) {
           int c0 = x0, c1 = x1;
-          if (E < 0.f) {
-            c1 = c0 - 1;
-          } else {
+          if (mg.ok) {
             float xl, xr;
             const float ya = (float)((mty0 + y) * TILE);
-            if (!ellipse_row_span(g0, g1, E, ya, ya + (float)(TILE - 1), xl, xr)) {
-              c1 = c0 - 1;
-            } else {
-              c0 = max(c0, floordiv((int)ceilf(xl), TILE) - mtx0);
-              c1 = min(c1, floordiv((int)floorf(xr), TILE) - mtx0);
-            }
+            if (!mask_row_span(mg, g0.x, g0.y, ya, ya + (float)(TILE - 1), xl, xr)) continue;
+            c0 = max(c0, floordiv((int)ceilf(xl), TILE) - mtx0);
+            c1 = min(c1, floordiv((int)floorf(xr), TILE) - mtx0);
           }
           if (c0 <= c1) gm |= (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
         }
