@@ -30,8 +30,6 @@ namespace {
 
 constexpr int BW = 8;
 constexpr int BT = BW * 32;
-constexpr int BRING = 64;
-constexpr int BDRAIN = 32;
 constexpr int NG = 9;  // d mean2d x,y, d conic A,B,C, d opacity, d rgb
 
 // Sum 16 per-lane values over the warp; lane l receives the total of value
@@ -107,7 +105,6 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead;
   __shared__ uint8_t s_q[64];
-  __shared__ uint16_t s_ring[BW * BRING];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -194,20 +191,14 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
         v1 = make_float3(a.dl_drgb[o * 3 + 0], a.dl_drgb[o * 3 + 1], a.dl_drgb[o * 3 + 2]);
       }
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
-      uint16_t* ring = s_ring + warp * BRING;
-      uint32_t head = 0, tail = 0;
-      bool all_done = !__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1));
-      for (int k = 0; k < K && !all_done; ++k) {
-        const uint32_t m = s_mask[k * M + t];
-        if (m) {
-          if ((m >> lane) & 1u) ring[(tail + __popc(m & lanemask_lt())) & (BRING - 1)] = (uint16_t)(k * 32 + lane);
-          tail += __popc(m);
-          __syncwarp();
-        }
-        while (tail - head >= BDRAIN || (k == K - 1 && tail > head)) {
-          const uint32_t n = min(tail - head, (uint32_t)BDRAIN);
-          for (uint32_t i = 0; i < n; ++i) {
-            const uint32_t j = ring[(head + i) & (BRING - 1)];
+      // the tile's gaussians in depth order: set bits of its mini-batch masks
+      if (__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
+        for (int k = 0; k < K; ++k) {
+          uint32_t m = s_mask[k * M + t];
+          if (!m) continue;
+          do {
+            const uint32_t j = (uint32_t)k * 32 + (__ffs(m) - 1);
+            m &= m - 1;
             const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
             const float cA = g0.z * g0.z * k2, cB = g0.z * g0.w * k2, cC = (g0.w * g0.w + g1.x * g1.x) * k2;
             const float dx = fpx - g0.x;
@@ -223,13 +214,8 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
               const int idx = (lane >> 1) & 15;
               if ((lane & 1) == 0 && idx < NG && tot != 0.f) atomicAdd(&s_grad[j * NG + idx], tot);
             }
-          }
-          head += n;
-          __syncwarp();
-          if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
-            all_done = true;
-            break;
-          }
+          } while (m);
+          if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
         }
       }
     }

@@ -16,9 +16,11 @@
 //           or done.  If the wait gives up, the unit renders from T = 1 (an
 //           independent partial) and the merge composites it by Eq. 1 with
 //           replay.
-//   phase 2 warps claim tiles from the queue; a warp blends the tile's 64
-//           pixels (two per lane) front to back over the set mask bits, with
-//           a unanimous-vote early out when every pixel has stopped
+//   phase 2 warps claim tiles from the queue, longest first; a warp blends
+//           the tile's 64 pixels (two per lane) front to back over the set
+//           bits of the tile's mini-batch masks (warp-uniform words, so the
+//           gaussians are taken straight from the masks), with a unanimous
+//           vote per mini-batch as the early out when every pixel has stopped
 //   store   chained: the new per-tile state; unchained: the partial
 //           (r, g, b, +-T) with streaming stores (T negated when the pixel
 //           stopped inside the batch)
@@ -31,8 +33,6 @@ namespace hg {
 namespace {
 
 constexpr int RW = 8;  // warps per CTA
-constexpr int DRAIN = 32;    // gaussians blended per drain of the scheduling buffer
-constexpr uint32_t RING = 64;  // scheduling buffer capacity per warp (2 x DRAIN)
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
@@ -40,12 +40,11 @@ template <int MW, int MH, bool SAVE>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* s_rec = reinterpret_cast<float4*>(smem_raw);                       // [cap + 1][3]
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)(cap + 1) * 3);  // [cap/32][M]
+  float4* s_rec = reinterpret_cast<float4*>(smem_raw);                       // [cap][3]
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);   // [cap/32][M]
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
-  __shared__ __align__(16) uint16_t s_ring[RW * RING];
   __shared__ unsigned long long s_active, s_blended;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -53,8 +52,6 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     mbar_init(&bar, 1);
     mbar_fence_init();
   }
-  // null record (blend level -1: never passes the blend test) for padding
-  if (tid < 3) s_rec[(size_t)cap * 3 + tid] = make_float4(0.f, 0.f, 0.f, tid == 2 ? -1.f : 0.f);
   __syncthreads();
   if (read_status(a.fc)) return;
   const uint32_t n_units = a.fc->n_batches;
@@ -192,51 +189,22 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       }
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
       uint32_t n_blend = 0;
-      // scheduling buffer (Alg. 2): indices of the tile's gaussians from
-      // successive mini-batches accumulate in a per-warp ring and are
-      // drained DRAIN at a time.  Drains start at multiples of DRAIN, so
-      // every group of 8 indices is one aligned 16-byte shared load; the
-      // last drain is padded to a multiple of 8 with the null record (index
-      // cap), which never passes the blend test.
-      uint16_t* ring = s_ring + warp * RING;
-      const uint4* ring4 = reinterpret_cast<const uint4*>(ring);
-      uint32_t head = 0, tail = 0;
-      bool all_done = false;
-      auto drain = [&](uint32_t n, uint32_t n_real) {
-        for (uint32_t i0 = 0; i0 < n; i0 += 8) {
-          const uint4 q = ring4[((head + i0) & (RING - 1)) >> 3];
-          const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t j = (w4[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
-            const float ub = g0.z * (fpx - g0.x);
-            blend(p0, ub, fpy - g0.y, g0, g1, g2);
-            blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
-          }
-          n_blend += min(8u, n_real - i0);
-          if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
-            all_done = true;
-            break;
-          }
-        }
-        head += n;
-        __syncwarp();
-      };
-      for (int k = 0; k < K && !all_done; ++k) {
-        const uint32_t m = s_mask[k * M + t];
-        if (m) {
-          if ((m >> lane) & 1u) ring[(tail + __popc(m & lanemask_lt())) & (RING - 1)] = (uint16_t)(k * 32 + lane);
-          tail += __popc(m);
-          __syncwarp();
-        }
-        if (tail - head >= DRAIN) drain(DRAIN, DRAIN);
-      }
-      if (!all_done && tail > head) {
-        const uint32_t nr = tail - head, n8 = (nr + 7u) & ~7u;
-        if (lane < n8 - nr) ring[(tail + lane) & (RING - 1)] = (uint16_t)cap;
-        __syncwarp();
-        drain(n8, nr);
+      // gaussians of this tile in depth order: the set bits of its per
+      // mini-batch masks (warp-uniform), blended directly; the unanimous
+      // early-out vote runs once per mini-batch
+      for (int k = 0; k < K; ++k) {
+        uint32_t m = s_mask[k * M + t];
+        if (!m) continue;
+        n_blend += __popc(m);
+        do {
+          const uint32_t j = (uint32_t)k * 32 + (__ffs(m) - 1);
+          m &= m - 1;
+          const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
+          const float ub = g0.z * (fpx - g0.x);
+          blend(p0, ub, fpy - g0.y, g0, g1, g2);
+          blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+        } while (m);
+        if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
       if (chained) {
@@ -274,7 +242,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 template <int MW, int MH, bool SAVE>
 cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) {
   constexpr int M = MW * MH;
-  const size_t sm = (size_t)(cap + 1) * 48 + (size_t)((cap + 31) / 32) * M * 4;
+  const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 4;
   cudaError_t e =
       cudaFuncSetAttribute(k_raster<MW, MH, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
