@@ -324,7 +324,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   if (s->cap_batches == 0) s->cap_batches = s->cap_pairs / o->batch_cap + g.S + 64;
   s->cap_batches = std::max(s->cap_batches, (size_t)g.S + 64);
   if (s->cap_tiles == 0) s->cap_tiles = s->cap_pairs / OS_TILE + 16;
-  if (s->cap_big_segs == 0) s->cap_big_segs = std::min<size_t>((size_t)g.S, s->cap_pairs / TIER2_MAX + 16);
+  if (s->cap_big_segs == 0) s->cap_big_segs = std::min<size_t>((size_t)g.S, s->cap_pairs / TIER3_MAX + 16);
   s->cap_big_segs = std::max<size_t>(s->cap_big_segs, 16);
   if (s->cap_plain_pairs == 0) s->cap_plain_pairs = (size_t)std::max<long long>(1 << 20, 8 * n * V);
   if (s->cap_plain_tiles == 0) s->cap_plain_tiles = s->cap_plain_pairs / OS_TILE + 16;
@@ -422,7 +422,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ENS(B_SEGTOT, sizeof(uint32_t) * g.S);
     ENS(B_SEGOFF, sizeof(uint32_t) * (g.S + 1));
     ENS(B_FIRSTB, sizeof(uint32_t) * (g.S + 1));
-    ENS(B_TIERLIST, sizeof(uint32_t) * 5 * (size_t)g.S);
+    ENS(B_TIERLIST, sizeof(uint32_t) * N_TIERS * (size_t)g.S);
     ENS(B_BIGTILES, sizeof(uint4) * s->cap_tiles);
     ENS(B_BIGSEGS, sizeof(uint32_t) * s->cap_big_segs);
     ENS(B_BIGTF, sizeof(uint32_t) * s->cap_big_segs);
@@ -668,11 +668,7 @@ extern "C" hg_status hg_render_stats(hg_state* s, hg_frame_stats* out) {
   out->n_segments = s->geom.S;
   out->n_batches = f.n_batches;
   out->max_segment = f.max_seg;
-  out->seg_by_tier[0] = f.tier_count[0];
-  out->seg_by_tier[1] = f.tier_count[1];
-  out->seg_by_tier[2] = f.tier_count[2];
-  out->seg_by_tier[3] = f.tier_count[3];
-  out->seg_by_tier[4] = f.tier_count[4];
+  for (int t = 0; t < N_TIERS; ++t) out->seg_by_tier[t] = f.tier_count[t];
   out->n_sort_tiles = f.n_big_tiles;
   out->n_replays = (int64_t)f.replays;
   out->raster_evals = (int64_t)f.raster_evals;

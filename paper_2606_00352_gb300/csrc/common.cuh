@@ -48,7 +48,7 @@ struct FrameCounters {
   uint32_t n_big_tiles;
   uint32_t n_big_segs;
   uint32_t max_seg;
-  uint32_t tier_count[5];
+  uint32_t tier_count[6];
   uint32_t n_visible;
   uint32_t raster_claim;
   uint32_t merge_claim;

@@ -43,7 +43,7 @@ struct PartitionArgs {
   uint32_t* seg_tot;      // [S]
   uint32_t* seg_off;      // [S + 1]
   uint32_t* first_batch;  // [S + 1]
-  uint32_t* tier_list;    // [5][S] segment ids per sort tier
+  uint32_t* tier_list;    // [N_TIERS][S] segment ids per sort tier
   uint4* big_tiles;       // onesweep tiles {seg, start, count, tile index in segment}
   uint32_t* big_segs;     // [S] big segment ids
   uint32_t* big_tile_first; // [S] first tile of each big segment
@@ -61,6 +61,10 @@ struct PartitionArgs {
 constexpr int TIER0_MAX = 1024;    // 128 threads x 8
 constexpr int TIER1_MAX = 4096;    // 256 threads x 16
 constexpr int TIER2_MAX = 8192;    // 512 threads x 16
+constexpr int TIER3_MAX = 16384;   // 512 threads x 16, two halves then a merge
+// tiers: <= 1K, <= 4K, <= 8K, <= 16K (shared memory), onesweep, empty / one pair
+constexpr int N_TIERS = 6;
+constexpr int TIER_OS = 4, TIER_NONE = 5;
 constexpr int OS_THREADS = 512;    // onesweep tile: 512 threads x 16 items
 constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
@@ -72,7 +76,7 @@ struct SortArgs {
   uint32_t* keys_alt;
   uint32_t* vals_alt;
   const uint32_t* seg_off;
-  const uint32_t* tier_list;  // [5][S]
+  const uint32_t* tier_list;  // [N_TIERS][S]
   int n_seg;
   const uint4* big_tiles;
   const uint32_t* big_segs;

@@ -70,11 +70,12 @@ __global__ void __launch_bounds__(1024) k_colscan(PartitionArgs a) {
 }
 
 __device__ __forceinline__ int seg_tier(uint32_t n) {
-  if (n <= 1) return 4;
+  if (n <= 1) return TIER_NONE;
   if (n <= (uint32_t)TIER0_MAX) return 0;
   if (n <= (uint32_t)TIER1_MAX) return 1;
   if (n <= (uint32_t)TIER2_MAX) return 2;
-  return 3;
+  if (n <= (uint32_t)TIER3_MAX) return 3;
+  return TIER_OS;
 }
 
 __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
   for (int j = tid; j < MAX_RANKS; j += NT) rank_hist[j] = 0;
   if (tid == 0) rank_last = 0;
   __syncthreads();
-  uint32_t c_pairs = 0, c_batches = 0, c_tier[5] = {0, 0, 0, 0, 0}, c_tiles = 0, mx = 0;
+  uint32_t c_pairs = 0, c_batches = 0, c_tier[N_TIERS] = {}, c_tiles = 0, mx = 0;
   for (int s = s0; s < s1; ++s) {
     const uint32_t n = a.seg_tot[s];
     const uint32_t nb = (n + cap - 1) / cap;
@@ -98,18 +99,18 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
     c_batches += nb;
     const int t = seg_tier(n);
     c_tier[t]++;
-    if (t == 3) c_tiles += (n + OS_TILE - 1) / OS_TILE;
+    if (t == TIER_OS) c_tiles += (n + OS_TILE - 1) / OS_TILE;
     mx = max(mx, n);
     if (nb > 0) {
       atomicAdd(&rank_hist[min(nb, (uint32_t)MAX_RANKS - 1)], 1u);
       if (nb > (uint32_t)MAX_RANKS - 1) atomicAdd(&rank_last, nb - (MAX_RANKS - 1));
     }
   }
-  uint32_t t_pairs, t_batches, t_tier[5], t_tiles;
+  uint32_t t_pairs, t_batches, t_tier[N_TIERS], t_tiles;
   const uint32_t o_pairs = block_excl_scan(c_pairs, tmp, &t_pairs);
   const uint32_t o_batches = block_excl_scan(c_batches, tmp, &t_batches);
-  uint32_t o_tier[5];
-  for (int t = 0; t < 5; ++t) o_tier[t] = block_excl_scan(c_tier[t], tmp, &t_tier[t]);
+  uint32_t o_tier[N_TIERS];
+  for (int t = 0; t < N_TIERS; ++t) o_tier[t] = block_excl_scan(c_tier[t], tmp, &t_tier[t]);
   const uint32_t o_tiles = block_excl_scan(c_tiles, tmp, &t_tiles);
   // max segment
   uint32_t m = mx;
@@ -123,14 +124,14 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   }
   const bool over = t_pairs > a.cap_pairs || t_batches > a.cap_batches || t_tiles > a.cap_tiles ||
-                    t_tier[3] > a.cap_big_segs;
+                    t_tier[TIER_OS] > a.cap_big_segs;
   if (tid == 0) {
     a.fc->n_pairs = t_pairs;
     a.fc->n_batches = t_batches;
     a.fc->n_big_tiles = t_tiles;
-    a.fc->n_big_segs = t_tier[3];
+    a.fc->n_big_segs = t_tier[TIER_OS];
     a.fc->max_seg = m;
-    for (int t = 0; t < 5; ++t) a.fc->tier_count[t] = t_tier[t];
+    for (int t = 0; t < N_TIERS; ++t) a.fc->tier_count[t] = t_tier[t];
     if (over) set_status(a.fc, HG_ERR_CAPACITY);
   }
   if (over) return;
@@ -160,17 +161,17 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
     c_excl += cnt[k];
   }
   // per-segment outputs
-  uint32_t p = o_pairs, bo = o_batches, tl = o_tiles, ot[5];
-  for (int t = 0; t < 5; ++t) ot[t] = o_tier[t];
+  uint32_t p = o_pairs, bo = o_batches, tl = o_tiles, ot[N_TIERS];
+  for (int t = 0; t < N_TIERS; ++t) ot[t] = o_tier[t];
   for (int s = s0; s < s1; ++s) {
     const uint32_t n = a.seg_tot[s];
     a.seg_off[s] = p;
     a.first_batch[s] = bo;
     const int t = seg_tier(n);
-    if (t < 3) {
+    if (t < TIER_OS) {
       a.tier_list[(size_t)t * S + ot[t]] = s;
-    } else if (t == 3) {
-      const uint32_t bi = ot[3];
+    } else if (t == TIER_OS) {
+      const uint32_t bi = ot[TIER_OS];
       a.big_segs[bi] = s;
       a.big_tile_first[bi] = tl;
       const uint32_t nt = (n + OS_TILE - 1) / OS_TILE;

@@ -2,7 +2,9 @@
 // (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
 //   * segments of <= 8K pairs: one CTA sorts the segment in shared memory
 //     (tiers <= 1K / 4K / 8K pairs), over the digits of (key - min key);
-//   * larger segments: a segment-local onesweep (one kernel per 8-bit digit
+//   * segments of 8K..16K pairs: one CTA sorts the two halves in shared
+//     memory the same way and merges them (merge path) into the output;
+//   * larger segments (> 16K): a segment-local onesweep (one kernel per 8-bit digit
 //     pass, decoupled look-back across the segment's tiles, tiles claimed in
 //     order through an atomic counter so every awaited predecessor is
 //     running), preceded by one histogram kernel for all four digits.
@@ -40,26 +42,93 @@ __device__ __forceinline__ void sort_run_by_val(uint32_t* vals, int a, int b) {
   }
 }
 
-// One CTA per segment (grid-stride over the tier's list).  The segment's n
-// pairs are spread evenly over the warps (rows = ceil(n / NT) item slots per
-// thread), the tail of the last rows padded with key 0xffffffff and digit
-// 255 so that padding always ranks after the real pairs; the digit passes
-// cover the bits of (key - min key), the only bits that order the segment.
+// Sorts the n pairs of a shared-memory region ascending by (key, id): LSD
+// radix passes over the digits of (key - kmin) that can vary, the region's
+// n pairs spread evenly over the warps (rows = ceil(n / NT) item slots per
+// thread; slots [n, rows * NT) must hold key 0xffffffff and get digit 255,
+// so padding always ranks after the real pairs), then runs of equal keys
+// re-sorted by id (the fill order is data-dependent).
+template <int NT, int IPT>
+__device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int passes,
+                                            RankSmem<NT>& rank) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rows = (n + NT - 1) / NT;  // <= IPT
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = 8 * pass;
+    uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (i >= rows) break;
+      const int e = warp * 32 * rows + i * 32 + lane;
+      k[i] = keys[e];
+      v[i] = vals[e];
+      d[i] = e < n ? ((k[i] - kmin) >> shift) & 0xffu : 0xffu;
+    }
+    block_rank_rows<NT, IPT>(d, p, rank, rows);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (i >= rows) break;
+      keys[p[i]] = k[i];
+      vals[p[i]] = v[i];
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < n; j += NT) {
+    const uint32_t kk = keys[j];
+    if ((j == 0 || keys[j - 1] != kk) && j + 1 < n && keys[j + 1] == kk) {
+      int e = j + 1;
+      while (e < n && keys[e] == kk) ++e;
+      sort_run_by_val(vals, j, e);
+    }
+  }
+  __syncthreads();
+}
+
+// Block-wide min and max of one value per thread (red: [2][NT / 32]).
+template <int NT>
+__device__ __forceinline__ void block_min_max(uint32_t& mn, uint32_t& mx, uint32_t (*red)[NT / 32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    red[0][warp] = mn;
+    red[1][warp] = mx;
+  }
+  __syncthreads();
+  mn = 0xffffffffu;
+  mx = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+    mn = min(mn, red[0][w]);
+    mx = max(mx, red[1][w]);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int radix_passes(uint32_t kmin, uint32_t kmax) {
+  const uint32_t span = kmax - kmin;
+  return span ? (32 - __clz(span) + 7) / 8 : 0;
+}
+
+// One CTA per segment (grid-stride over the tier's list): the segment is
+// loaded into shared memory, sorted there (sort_region) and written back.
 template <int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
-  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<NT, IPT>& s = *reinterpret_cast<BlockSortSmem<NT, IPT>*>(smem_raw);
   if (read_status(a.fc)) return;
   const uint32_t count = a.fc->tier_count[tier];
   const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const uint32_t seg = list[idx];
     const uint32_t start = a.seg_off[seg];
     const int n = (int)(a.seg_off[seg + 1] - start);
-    const int rows = (n + NT - 1) / NT;  // <= IPT for the segments of this tier
-    const int used = rows * NT;
+    const int used = ((n + NT - 1) / NT) * NT;
     uint32_t kmin = 0xffffffffu, kmax = 0;
     for (int j = tid; j < used; j += NT) {
       uint32_t k = 0xffffffffu, v = 0xffffffffu;
@@ -72,59 +141,96 @@ __global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
       s.keys[j] = k;
       s.vals[j] = v;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    }
-    if (lane == 0) {
-      s.red[0][warp] = kmin;
-      s.red[1][warp] = kmax;
-    }
-    __syncthreads();
-    kmin = 0xffffffffu;
-    kmax = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      kmin = min(kmin, s.red[0][w]);
-      kmax = max(kmax, s.red[1][w]);
-    }
-    const uint32_t span = kmax - kmin;
-    const int passes = span ? (32 - __clz(span) + 7) / 8 : 0;
-    for (int pass = 0; pass < passes; ++pass) {
-      const int shift = 8 * pass;
-      uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
-#pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        if (i >= rows) break;
-        const int e = warp * 32 * rows + i * 32 + lane;
-        k[i] = s.keys[e];
-        v[i] = s.vals[e];
-        d[i] = e < n ? ((k[i] - kmin) >> shift) & 0xffu : 0xffu;
-      }
-      block_rank_rows<NT, IPT>(d, p, s.rank, rows);
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        if (i >= rows) break;
-        s.keys[p[i]] = k[i];
-        s.vals[p[i]] = v[i];
-      }
-      __syncthreads();
-    }
-    // equal keys: order by id
-    for (int j = tid; j < n; j += NT) {
-      uint32_t kk = s.keys[j];
-      if ((j == 0 || s.keys[j - 1] != kk) && j + 1 < n && s.keys[j + 1] == kk) {
-        int e = j + 1;
-        while (e < n && s.keys[e] == kk) ++e;
-        sort_run_by_val(s.vals, j, e);
-      }
-    }
-    __syncthreads();
+    block_min_max<NT>(kmin, kmax, s.red);
+    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_passes(kmin, kmax), s.rank);
     for (int j = tid; j < n; j += NT) {
       a.keys[start + j] = s.keys[j];
       a.vals[start + j] = s.vals[j];
+    }
+    __syncthreads();
+  }
+}
+
+// Segments of 8K..16K pairs: the two halves are sorted in their own
+// shared-memory regions of NT * IPT slots (sort_region), then merged by the
+// merge path straight into the output: thread t finds, by binary search on
+// its output diagonal, how many of its first outputs come from each half
+// and merges its run of ceil(n / NT) outputs.  Pairs of a segment are
+// distinct gaussians, so (key, id) is a strict order.
+template <int NT, int IPT>
+struct MergeSortSmem {
+  uint32_t keys[2 * NT * IPT];
+  uint32_t vals[2 * NT * IPT];
+  RankSmem<NT> rank;
+  uint32_t red[2][NT / 32];
+};
+
+__device__ __forceinline__ bool pair_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT) k_block_merge_sort(SortArgs a, int tier) {
+  constexpr int H = NT * IPT;  // one half's region
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MergeSortSmem<NT, IPT>& s = *reinterpret_cast<MergeSortSmem<NT, IPT>*>(smem_raw);
+  if (read_status(a.fc)) return;
+  const uint32_t count = a.fc->tier_count[tier];
+  const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
+  const int tid = threadIdx.x;
+  for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const uint32_t seg = list[idx];
+    const uint32_t start = a.seg_off[seg];
+    const int n = (int)(a.seg_off[seg + 1] - start);
+    const int hA = (n + 1) / 2, hB = n - hA;
+    const int usedA = ((hA + NT - 1) / NT) * NT, usedB = ((hB + NT - 1) / NT) * NT;
+    uint32_t kmin = 0xffffffffu, kmax = 0;
+    for (int j = tid; j < usedA; j += NT) {
+      uint32_t k = 0xffffffffu, v = 0xffffffffu;
+      if (j < hA) {
+        k = a.keys[start + j];
+        v = a.vals[start + j];
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+      }
+      s.keys[j] = k;
+      s.vals[j] = v;
+    }
+    for (int j = tid; j < usedB; j += NT) {
+      uint32_t k = 0xffffffffu, v = 0xffffffffu;
+      if (j < hB) {
+        k = a.keys[start + hA + j];
+        v = a.vals[start + hA + j];
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+      }
+      s.keys[H + j] = k;
+      s.vals[H + j] = v;
+    }
+    block_min_max<NT>(kmin, kmax, s.red);
+    const int passes = radix_passes(kmin, kmax);
+    sort_region<NT, IPT>(s.keys, s.vals, hA, kmin, passes, s.rank);
+    sort_region<NT, IPT>(s.keys + H, s.vals + H, hB, kmin, passes, s.rank);
+    const uint32_t *ka = s.keys, *va = s.vals, *kb = s.keys + H, *vb = s.vals + H;
+    const int per = (n + NT - 1) / NT;
+    const int d0 = min(n, tid * per), d1 = min(n, d0 + per);
+    // i = number of A pairs among the first d0 outputs
+    int lo = max(0, d0 - hB), hi = min(d0, hA);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (pair_less(kb[d0 - mid - 1], vb[d0 - mid - 1], ka[mid], va[mid]))
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    int ia = lo, ib = d0 - lo;
+    for (int d = d0; d < d1; ++d) {
+      const bool takeA = ib >= hB || (ia < hA && pair_less(ka[ia], va[ia], kb[ib], vb[ib]));
+      const uint32_t k = takeA ? ka[ia] : kb[ib], v = takeA ? va[ia] : vb[ib];
+      ia += takeA;
+      ib += !takeA;
+      a.keys[start + d] = k;
+      a.vals[start + d] = v;
     }
     __syncthreads();
   }
@@ -369,11 +475,23 @@ template cudaError_t launch_onesweep<unsigned long long, 8>(const OsTileView&, u
                                                             uint32_t*, size_t, uint32_t*, int, int,
                                                             FrameCounters*, cudaStream_t, bool*);
 
+template <int NT, int IPT>
+static cudaError_t launch_merge_tier(const SortArgs& a, int tier, cudaStream_t st) {
+  size_t sm = sizeof(MergeSortSmem<NT, IPT>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_block_merge_sort<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_block_merge_sort<NT, IPT><<<num_sms(), NT, sm, st>>>(a, tier);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
   cudaError_t e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
   if ((e = launch_tier<256, 16>(a, 1, 4, st)) != cudaSuccess) return e;
   if ((e = launch_tier<512, 16>(a, 2, 2, st)) != cudaSuccess) return e;
+  if ((e = launch_merge_tier<512, 16>(a, 3, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   bool alt = false;
   e = launch_onesweep<uint32_t, 4>(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist,

@@ -88,7 +88,7 @@ class TuneResult(C.Structure):
 class FrameStats(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_gaussians", C.c_int64), ("n_visible", C.c_int64),
                 ("n_pairs", C.c_int64), ("n_segments", C.c_int64), ("n_batches", C.c_int64),
-                ("max_segment", C.c_int64), ("seg_by_tier", C.c_int64 * 5), ("n_sort_tiles", C.c_int64),
+                ("max_segment", C.c_int64), ("seg_by_tier", C.c_int64 * 6), ("n_sort_tiles", C.c_int64),
                 ("n_replays", C.c_int64), ("raster_evals", C.c_int64), ("status", C.c_int32),
                 ("pad", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
                 ("ms_sort", C.c_float), ("ms_raster", C.c_float), ("ms_merge", C.c_float),

@@ -165,25 +165,26 @@ def test_discrete_stages_onesweep_and_ties(lib, ctx):
     cam = scenes.look_at((3, 0, 0), width=130, height=70)
     pr = _synthetic_records(300_000, 130, 70, 3000, seed=0)
     st = _gate(lib, ctx, [pr], [cam])
-    assert st["seg_by_tier"][3] > 0 and st["n_sort_tiles"] > 1
+    assert st["seg_by_tier"][4] > 0 and st["n_sort_tiles"] > 1
     st2 = _gate(lib, ctx, [pr], [cam], macro=(4, 4), cap=2048)
-    assert st2["seg_by_tier"][3] > 0
+    assert st2["seg_by_tier"][4] > 0
     st3 = _gate(lib, ctx, [pr], [cam], macro=(4, 4), ellipse=True)
-    assert st3["seg_by_tier"][3] > 0
+    assert st3["seg_by_tier"][4] > 0
 
 
 def test_discrete_stages_all_tiers(lib, ctx):
     cam = scenes.look_at((3, 0, 0), width=640, height=96)
     g = np.random.default_rng(5)
     parts = []
-    for n, w in ((400, 64), (3000, 128), (6000, 256), (40000, 512)):
+    for n, w in ((400, 64), (3000, 128), (6000, 256), (12000, 384), (40000, 512)):
         p = _synthetic_records(n, 64, 32, 500, seed=int(g.integers(1 << 30)))
         p["mean2d"][:, 0] += w - 64  # one macro column per density
         parts.append(p)
     pr = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if k != "n"}
     pr["n"] = len(pr["radius"])
     st = _gate(lib, ctx, [pr], [cam])
-    assert all(st["seg_by_tier"][t] > 0 for t in range(4))
+    # <= 1K, <= 4K, <= 8K, <= 16K (halves + merge) and onesweep
+    assert all(st["seg_by_tier"][t] > 0 for t in range(5))
 
 
 # ------------------------------------------------------------ images
