@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rec = reinterpret_cast<float4*>(smem_raw);
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);
-  float* s_grad = reinterpret_cast<float*>(s_mask + (size_t)((cap + 31) / 32) * M);
+  uint32_t* s_top = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);
+  uint32_t* s_bot = s_top + (size_t)((cap + 31) / 32) * M;
+  float* s_grad = reinterpret_cast<float*>(s_bot + (size_t)((cap + 31) / 32) * M);
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead;
   __shared__ uint8_t s_q[64];
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
     }
     phase ^= 1u;
     const int K = (int)((count + 31) / 32);
-    build_tile_masks<MW, MH>(s_rec, s_mask, count, V, mtx0, mty0, BW);
+    build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, BW);
     if (warp == 0) {
       int qn = 0;
 #pragma unroll
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       // the tile's gaussians in depth order: set bits of its mini-batch masks
       if (__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
         for (int k = 0; k < K; ++k) {
-          uint32_t m = s_mask[k * M + t];
+          uint32_t m = s_top[k * M + t] | s_bot[k * M + t];
           if (!m) continue;
           do {
             const uint32_t j = (uint32_t)k * 32 + (__ffs(m) - 1);
@@ -454,7 +455,7 @@ template <int MW, int MH>
 cudaError_t launch_bwd_shape(const BackwardArgs& a, cudaStream_t st) {
   constexpr int M = MW * MH;
   const int cap = a.batch_cap;
-  const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 4 + (size_t)cap * NG * 4;
+  const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 8 + (size_t)cap * NG * 4;
   cudaError_t e = cudaFuncSetAttribute(k_raster_bwd<MW, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1, dev = 0, sms = 0;

@@ -4,8 +4,9 @@
 //   load    the batch's gaussian ids, then one TMA bulk copy per gaussian
 //           gathers its 48-byte record into shared memory (one mbarrier)
 //   phase 1 each warp takes mini-batches of 32 gaussians, computes the
-//           gaussian's render-tile mask inside the macro-tile and transposes
-//           the 32 x M bit matrix with a shuffle butterfly (per-tile masks)
+//           gaussian's render-tile masks inside the macro-tile, one for the
+//           top and one for the bottom half of each tile, and transposes the
+//           32 x M bit matrices with a shuffle butterfly (per-tile masks)
 //   queue   warp 0 ORs the masks per tile and compacts the active tiles
 //   chain   (exact termination) the unit of rank k waits, with a bounded
 //           spin, until rank k-1 of the same macro-tile has finished; it then
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s_rec = reinterpret_cast<float4*>(smem_raw);                       // [cap][3]
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);   // [cap/32][M]
+  uint32_t* s_top = reinterpret_cast<uint32_t*>(s_rec + (size_t)cap * 3);    // [cap/32][M] top halves
+  uint32_t* s_bot = s_top + (size_t)((cap + 31) / 32) * M;                   // [cap/32][M] bottom halves
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 
     // phase 1: per-gaussian tile masks, transposed to per-tile masks
     const int K = (int)((count + 31) / 32);
-    build_tile_masks<MW, MH>(s_rec, s_mask, count, V, mtx0, mty0, RW);
+    build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, RW);
     __syncthreads();
 
     // tile work queue (warp 0), longest first: a tile's work is about the
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         const int t = h * 32 + lane;
         uint32_t n = 0;
         if (t < M)
-          for (int k = 0; k < K; ++k) n += __popc(s_mask[k * M + t]);
+          for (int k = 0; k < K; ++k) n += __popc(s_top[k * M + t]) + __popc(s_bot[k * M + t]);
         // key: count above, tile index below (distinct keys, ties by index)
         key[h] = n ? ((n << 6) | (uint32_t)(63 - t)) : 0u;
         act |= (unsigned long long)__ballot_sync(0xffffffffu, n != 0) << (h * 32);
@@ -193,20 +195,27 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       // mini-batch masks (warp-uniform), blended directly; the unanimous
       // early-out vote runs once per mini-batch
       for (int k = 0; k < K; ++k) {
-        uint32_t m = s_mask[k * M + t];
+        const uint32_t mt = s_top[k * M + t], mb = s_bot[k * M + t];
+        uint32_t m = mt | mb;
         if (!m) continue;
-        n_blend += __popc(m);
+        n_blend += __popc(mt) + __popc(mb);  // half-tiles evaluated (32 pixels each)
         do {
-          const uint32_t j = (uint32_t)k * 32 + (__ffs(m) - 1);
-          m &= m - 1;
+          const uint32_t bit = m & (0u - m);
+          m ^= bit;
+          const uint32_t j = (uint32_t)k * 32 + (__ffs(bit) - 1);
           const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
           const float ub = g0.z * (fpx - g0.x);
-          blend(p0, ub, fpy - g0.y, g0, g1, g2);
-          blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+          // a half the gaussian cannot reach is skipped (its blend is a no-op)
+          if (mt & bit) {
+            blend(p0, ub, fpy - g0.y, g0, g1, g2);
+            if (mb & bit) blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+          } else {
+            blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+          }
         } while (m);
         if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
       }
-      if (lane == 0) evals += (unsigned long long)n_blend * 64ull;
+      if (lane == 0) evals += (unsigned long long)n_blend * 32ull;
       if (chained) {
         float4* st = a.tile_state + (size_t)gt * TILE_PX;
         st[lane] = pixel_state(p0);
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 template <int MW, int MH, bool SAVE>
 cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) {
   constexpr int M = MW * MH;
-  const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 4;
+  const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 8;
   cudaError_t e =
       cudaFuncSetAttribute(k_raster<MW, MH, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;

@@ -27,19 +27,22 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 }
 
 // Phase 1 of a processing unit: every warp takes mini-batches of 32 staged
-// gaussians, computes each gaussian's render-tile mask inside the macro-tile
-// (3-sigma rectangle refined by the ellipse of the blend test per tile row) and
-// transposes the 32 x M bit matrix so that s_mask[k * M + t] holds, for tile
-// t, the bits of the mini-batch-k gaussians that overlap it.
+// gaussians, computes each gaussian's render-tile masks inside the macro-tile
+// for the top (rows 0-3) and bottom (rows 4-7) half of every tile (3-sigma
+// rectangle refined by the ellipse of the blend test per half-tile row band)
+// and transposes the 32 x M bit matrices, so that s_top[k * M + t] and
+// s_bot[k * M + t] hold, for tile t, the bits of the mini-batch-k gaussians
+// that can pass the blend test in its top / bottom half.
 template <int MW, int MH>
-__device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* s_mask, uint32_t count,
-                                                 const ViewDesc& V, int mtx0, int mty0, int n_warps) {
+__device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* s_top, uint32_t* s_bot,
+                                                 uint32_t count, const ViewDesc& V, int mtx0, int mty0,
+                                                 int n_warps) {
   constexpr int M = MW * MH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int K = (int)((count + 31) / 32);
   for (int k = warp; k < K; k += n_warps) {
     const uint32_t j = (uint32_t)k * 32 + lane;
-    unsigned long long gm = 0;
+    unsigned long long gt = 0, gb = 0;
     if (j < count) {
       const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
       int x0, x1, y0, y1;
@@ -50,25 +53,41 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
       y1 = min(min(y1, mty0 + MH - 1), V.tiles_y - 1) - mty0;
       const MaskGauss mg = mask_gauss(g0, g1, g2);
       if (x0 <= x1 && y0 <= y1 && mg.live) {
+        const unsigned long long full = ((1ull << (x1 - x0 + 1)) - 1ull) << x0;
         for (int y = y0; y <= y1; ++y) {
-          int c0 = x0, c1 = x1;
-          if (mg.ok) {
-            float xl, xr;
-            const float ya = (float)((mty0 + y) * TILE);
-            if (!mask_row_span(mg, g0.x, g0.y, ya, ya + (float)(TILE - 1), xl, xr)) continue;
-            c0 = max(c0, floordiv((int)ceilf(xl), TILE) - mtx0);
-            c1 = min(c1, floordiv((int)floorf(xr), TILE) - mtx0);
+          if (!mg.ok) {
+            gt |= full << (y * MW);
+            gb |= full << (y * MW);
+            continue;
           }
-          if (c0 <= c1) gm |= (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
+          const float ya = (float)((mty0 + y) * TILE);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float xl, xr;
+            const float yh = ya + (float)(h * (TILE / 2));
+            if (!mask_row_span(mg, g0.x, g0.y, yh, yh + (float)(TILE / 2 - 1), xl, xr)) continue;
+            const int c0 = max(x0, floordiv((int)ceilf(xl), TILE) - mtx0);
+            const int c1 = min(x1, floordiv((int)floorf(xr), TILE) - mtx0);
+            if (c0 > c1) continue;
+            const unsigned long long bits = (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
+            if (h == 0)
+              gt |= bits;
+            else
+              gb |= bits;
+          }
         }
       }
     }
-    // TransposeMasks: lane t receives the 32-gaussian mask of tile t
-    const uint32_t lo = transpose32((uint32_t)gm, lane);
-    if (lane < M) s_mask[k * M + lane] = lo;
+    // TransposeMasks: lane t receives the 32-gaussian masks of tile t
+    const uint32_t tlo = transpose32((uint32_t)gt, lane), blo = transpose32((uint32_t)gb, lane);
+    if (lane < M) {
+      s_top[k * M + lane] = tlo;
+      s_bot[k * M + lane] = blo;
+    }
     if (M > 32) {
-      const uint32_t hi = transpose32((uint32_t)(gm >> 32), lane);
-      s_mask[k * M + 32 + lane] = hi;
+      const uint32_t thi = transpose32((uint32_t)(gt >> 32), lane), bhi = transpose32((uint32_t)(gb >> 32), lane);
+      s_top[k * M + 32 + lane] = thi;
+      s_bot[k * M + 32 + lane] = bhi;
     }
   }
 }
