@@ -467,16 +467,24 @@ def gpu_arm(args):
     top, rl = roofline(stage_ms, stats, gs.n, pk, clocks.get("sm_mhz") or pk["sm_max_mhz"])
 
     # the same workload with the SH coefficients stored in half precision
-    # (float32 arithmetic): 140 instead of 236 bytes read per gaussian
-    gs16 = higs.GpuScene.from_scene(ctx, scene16, sh_storage=higs.SH_F16) if scene16 is not None else None
-    sh_f16 = None
-    if gs16 is not None:
-        hsteps = max(3, min(args.steps, 10))
-        hms, hstats, _ = time_graph(higs, gs16, cams, opts, hsteps, min(args.warmup, 3), rank, world, stream)
-        hvalue, hms = job_throughput(hms, hsteps * VIEWS, world)
-        sh_f16 = {"value": round(hvalue, 2), "unit": UNIT, "ms_per_step": round(hms / hsteps, 3),
-                  "project_ms": round(statistics.mean(s_["ms_project"] for s_ in hstats), 4)}
-        gs16.close()
+    # (236 -> 140 bytes read per gaussian) or in the 32-byte packed form
+    # (236 -> 76), float32 arithmetic either way; PSNR of the first pose batch
+    # against the float32-SH render
+    sh_variants = {}
+    if scene16 is not None:
+        ref_img, _ = higs.render(gs, pose_batch(cams, 0, rank), opts, with_T=False, stream=stream)
+        ref_img = ref_img.clone()
+        for name, code in (("sh_f16", higs.SH_F16), ("sh_codec32", higs.SH_CODEC32)):
+            gsv = higs.GpuScene.from_scene(ctx, scene16, sh_storage=code)
+            hsteps = max(3, min(args.steps, 10))
+            hms, hstats, _ = time_graph(higs, gsv, cams, opts, hsteps, min(args.warmup, 3), rank, world, stream)
+            hvalue, hms = job_throughput(hms, hsteps * VIEWS, world)
+            img, _ = higs.render(gsv, pose_batch(cams, 0, rank), opts, with_T=False, stream=stream)
+            mse = float(((img - ref_img) ** 2).mean().item())
+            sh_variants[name] = {"value": round(hvalue, 2), "unit": UNIT, "ms_per_step": round(hms / hsteps, 3),
+                                 "project_ms": round(statistics.mean(s_["ms_project"] for s_ in hstats), 4),
+                                 "psnr_db_vs_f32_sh": round(10 * math.log10(1.0 / max(mse, 1e-30)), 1)}
+            gsv.close()
     del scene16
 
     plain = None
@@ -536,7 +544,7 @@ def gpu_arm(args):
         "gpu_launches": int(kernels * args.steps),
         "clocks": clocks,
         "plain_path": plain,
-        "sh_f16": sh_f16,
+        "sh_storage_variants": sh_variants or None,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "frame_stats": {
             "pairs_per_step": int(statistics.mean(s["n_pairs"] for s in s0)),

@@ -88,9 +88,20 @@ typedef struct {
 
 /* Storage type of the SH coefficients (the projection computes in float32
  * either way; half storage halves the bytes the projection reads per
- * gaussian at degree 3, 236 -> 140).  Scenes with half SH render and serve;
- * hg_render_backward and hg_adam_step need float32 SH. */
-enum { HG_SH_F32 = 0, HG_SH_F16 = 1, HG_SH_BF16 = 2 };
+ * gaussian at degree 3, 236 -> 140).  HG_SH_CODEC32 is the 32-byte packed
+ * representation of Sec. 4.2 (degree 3 only; YCoCg-R, square-root gamma,
+ * 10/8/8 bits for the DC basis and 6/4/4 for the others, per-channel
+ * 99.5th-percentile scales): `sh` then points to float32 coefficients in
+ * device memory, which hg_create_scene encodes (the scene always owns the
+ * codes; 236 -> 76 bytes per gaussian).  Scenes with half or packed SH
+ * render and serve; hg_render_backward and hg_adam_step need float32 SH. */
+enum { HG_SH_F32 = 0, HG_SH_F16 = 1, HG_SH_BF16 = 2, HG_SH_CODEC32 = 3 };
+
+/* The packed SH of a HG_SH_CODEC32 scene: scales_host[16][3] receives the
+ * per-channel scales s (Y, Co, Cg per basis), codes_host (may be NULL)
+ * n * 8 uint32 code words.  Synchronous.
+ * Errors: HG_ERR_INVALID_ARG (not a packed-SH scene), HG_ERR_CUDA. */
+hg_status hg_scene_sh_codec(const hg_scene* scene, float* scales_host, uint32_t* codes_host);
 
 /* Pinhole camera: world->camera 4x4 row-major (x right, y down, z forward),
  * focal lengths and principal point in pixels; pixel (i, j) has its centre

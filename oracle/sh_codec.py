@@ -13,14 +13,19 @@ Reading, for the 16 bases k of degree-3 SH with RGB coefficients (R, G, B):
              B = t - Co/2, R = B + Co)
   scales     s[k][c] = the 99.5th percentile of |value| over the scene's
              gaussians, for basis k and channel c in (Y, Co, Cg); 0 -> 1
-  quantise   x = clamp(v / s, -1, 1); g = sign(x) sqrt(|x|);
-             q = round-half-even(g * Qc) with Qc = 2^(bits-1) - 1
-  bits       basis 0 (DC): Y 10, Co 8, Cg 8; bases 1..15: Y 6, Co 4, Cg 4
-             (26 + 15 * 14 = 236 of 256 bits)
+  quantise   bases 1..15: x = clamp(v / s, -1, 1); g = sign(x) sqrt(|x|);
+             q = round-half-even(g * Qc), Qc = 2^(bits-1) - 1, with
+             Y 6 bits, Co 4, Cg 4
+             basis 0 (DC, large and off-centre, where square-root steps are
+             coarsest): Y as a float16 (16 bits, round to nearest even);
+             Co, Cg linear: q = round-half-even(clamp(v / s, -1, 1) * 4095),
+             13 bits each
+  bits       42 + 15 * 14 = 252 of 256
   layout     the fields in order k = 0..15, c = Y, Co, Cg, each as a
              two's-complement field, packed from bit 0 of word 0 upwards
              into 8 little-endian uint32 words; unused high bits are 0
-  decode     g = q / Qc; v = sign(g) g^2 s; then the inverse transform
+  decode     bases 1..15: g = q / Qc, v = sign(g) g^2 s; DC: the float16,
+             and v = q / 4095 s; then the inverse transform
 
 Encoding arithmetic is float32 with each operation rounded (v / s, sqrt,
 g * Qc, round), so an implementation doing the same float32 operations
@@ -32,7 +37,8 @@ import numpy as np
 
 F32 = np.float32
 N_BASES = 16
-BITS = [(10, 8, 8)] + [(6, 4, 4)] * 15
+BITS = [(16, 13, 13)] + [(6, 4, 4)] * 15
+DC_LINEAR_Q = 4095
 PERCENTILE = 99.5
 
 
@@ -71,6 +77,11 @@ def quantise(v32, s32, bits):
     return np.rint(g * q_max).astype(np.int64)
 
 
+def quantise_linear(v32, s32):
+    x = np.clip(np.asarray(v32, F32) / F32(s32), F32(-1), F32(1))
+    return np.rint(x * F32(DC_LINEAR_Q)).astype(np.int64)
+
+
 def dequantise(q, s, bits):
     q_max = 2 ** (bits - 1) - 1
     g = np.asarray(q, np.float64) / q_max
@@ -86,8 +97,11 @@ def encode(sh, s):
     for k in range(N_BASES):
         for c in range(3):
             b = BITS[k][c]
-            q = quantise(ycc[:, k, c], s[k][c], b)
-            field = (q & ((1 << b) - 1)).astype(np.uint64)
+            if k == 0 and c == 0:
+                field = ycc[:, 0, 0].astype(np.float16).view(np.uint16).astype(np.uint64)
+            else:
+                q = quantise_linear(ycc[:, k, c], s[k][c]) if k == 0 else quantise(ycc[:, k, c], s[k][c], b)
+                field = (q & ((1 << b) - 1)).astype(np.uint64)
             w, o = divmod(pos, 32)
             words[:, w] |= (field << np.uint64(o)) & np.uint64(0xFFFFFFFF)
             if o + b > 32:
@@ -110,8 +124,12 @@ def decode(codes, s):
             if o + b > 32:
                 field |= codes[:, w + 1] << np.uint64(32 - o)
             field &= np.uint64((1 << b) - 1)
+            if k == 0 and c == 0:
+                ycc[:, 0, 0] = field.astype(np.uint16).view(np.float16).astype(np.float64)
+                pos += b
+                continue
             q = field.astype(np.int64)
             q = np.where(q >= (1 << (b - 1)), q - (1 << b), q)
-            ycc[:, k, c] = dequantise(q, s[k][c], b)
+            ycc[:, k, c] = q / DC_LINEAR_Q * float(s[k][c]) if k == 0 else dequantise(q, s[k][c], b)
             pos += b
     return ycocg_r_inverse(ycc)

@@ -12,6 +12,7 @@
 
 #include "binning.cuh"
 #include "internal.h"
+#include "sh_codec.cuh"
 
 using namespace hg;
 
@@ -150,7 +151,7 @@ extern "C" void hg_ctx_destroy(hg_ctx* ctx) {
 // ---------------------------------------------------------------- scenes
 extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_scene** out) {
   if (!ctx || !d || !out || d->n < 0 || d->sh_degree < 0 || d->sh_degree > 3 || d->sh_storage < HG_SH_F32 ||
-      d->sh_storage > HG_SH_BF16) {
+      d->sh_storage > HG_SH_CODEC32 || (d->sh_storage == HG_SH_CODEC32 && d->sh_degree != 3)) {
     hg_set_error("hg_create_scene: bad arguments");
     return HG_ERR_INVALID_ARG;
   }
@@ -171,12 +172,30 @@ extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_sce
   s->sh_storage = d->sh_storage;
   const void* src[5] = {d->means, d->log_scales, d->quats, d->opacity_logits, d->sh};
   const size_t per[5] = {3, 3, 4, 1, (size_t)K * 3};
+  const bool codec = d->sh_storage == HG_SH_CODEC32;
   const size_t esz[5] = {4, 4, 4, 4, d->sh_storage == HG_SH_F32 ? 4u : 2u};
   bool aligned = true;
   for (int i = 0; i < 5; ++i) aligned = aligned && (((uintptr_t)src[i]) & 15) == 0;
-  s->owned = !(d->borrow && aligned);
+  s->owned = !(d->borrow && aligned) || codec;
   for (int i = 0; i < 5; ++i) {
-    s->bytes[i] = per[i] * esz[i] * (size_t)d->n;
+    s->bytes[i] = codec && i == 4 ? sizeof(uint32_t) * SH_CODEC_WORDS * (size_t)d->n : per[i] * esz[i] * (size_t)d->n;
+    if (codec && i == 4) {
+      // packed SH: encoded here from the float32 coefficients
+      s->arr[i] = (float*)ctx_alloc(ctx, s->bytes[i], nullptr);
+      s->sh_scale = (float*)ctx_alloc(ctx, sizeof(float) * 2 * SH_CODEC_CH, nullptr);
+      if (!s->arr[i] || !s->sh_scale) {
+        hg_destroy_scene(s);
+        hg_set_error("hg_create_scene: allocation failed");
+        return HG_ERR_OOM;
+      }
+      const hg_status r = sh_codec_encode(ctx, (const float*)src[i], d->n, (uint32_t*)s->arr[i], s->sh_scale,
+                                          s->sh_scale + SH_CODEC_CH);
+      if (r != HG_OK) {
+        hg_destroy_scene(s);
+        return r;
+      }
+      continue;
+    }
     if (s->owned) {
       s->arr[i] = (float*)ctx_alloc(ctx, s->bytes[i], nullptr);
       if (!s->arr[i]) {
@@ -203,7 +222,20 @@ extern "C" void hg_destroy_scene(hg_scene* s) {
   if (!s) return;
   if (s->owned)
     for (int i = 0; i < 5; ++i) ctx_free(s->ctx, s->arr[i], s->bytes[i], nullptr);
+  if (s->sh_scale) ctx_free(s->ctx, s->sh_scale, sizeof(float) * 2 * SH_CODEC_CH, nullptr);
   delete s;
+}
+
+extern "C" hg_status hg_scene_sh_codec(const hg_scene* s, float* scales_host, uint32_t* codes_host) {
+  if (!s || !scales_host || s->sh_storage != HG_SH_CODEC32 || !s->sh_scale) {
+    hg_set_error("hg_scene_sh_codec: not a packed-SH scene");
+    return HG_ERR_INVALID_ARG;
+  }
+  cudaSetDevice(s->ctx->device);
+  cudaError_t e = cudaMemcpy(scales_host, s->sh_scale, sizeof(float) * SH_CODEC_CH, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && codes_host && s->n > 0)
+    e = cudaMemcpy(codes_host, s->arr[4], s->bytes[4], cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? HG_OK : hg_cuda_status(e, "hg_scene_sh_codec");
 }
 
 extern "C" int64_t hg_scene_size(const hg_scene* s) { return s ? s->n : 0; }
@@ -369,6 +401,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pj.opacity_logits = in.scene->arr[3];
     pj.sh = in.scene->arr[4];
     pj.sh_storage = in.scene->sh_storage;
+    pj.sh_scale2 = in.scene->sh_scale ? in.scene->sh_scale + SH_CODEC_CH : nullptr;
     pj.splats = (o->flags & HG_FLAG_KEEP_SPLATS) ? (hg_splat*)s->bufs[B_SPLATS].p : nullptr;
     HG_TRY(launch_project(pj, in.scene->deg, st), "project");
   }

@@ -21,6 +21,7 @@ struct hg_scene {
   int deg = 0;
   bool owned = true;
   int sh_storage = HG_SH_F32;  // element type of arr[4]
+  float* sh_scale = nullptr;   // packed SH: device [2][48] (s, s / Q^2)
   float* arr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // means, log_scales, quats, logits, sh
   size_t bytes[5] = {0, 0, 0, 0, 0};
 };

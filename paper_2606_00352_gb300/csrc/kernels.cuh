@@ -11,6 +11,7 @@ struct ProjectArgs {
   const float* opacity_logits;
   const void* sh;         // element type sh_storage (HG_SH_*)
   int sh_storage;
+  const float* sh_scale2; // packed SH: s / Q^2 per channel (device, 48), else null
   long long n;
   const ViewDesc* views;  // device
   int n_views;

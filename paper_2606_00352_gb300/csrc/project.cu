@@ -19,6 +19,7 @@
 #include "binning.cuh"
 #include "blend.cuh"
 #include "kernels.cuh"
+#include "sh_codec.cuh"
 
 namespace hg {
 
@@ -30,18 +31,59 @@ __device__ __forceinline__ float sh_f(float x) { return x; }
 __device__ __forceinline__ float sh_f(__half x) { return __half2float(x); }
 __device__ __forceinline__ float sh_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
-// SH coefficients are staged in their storage type SHT and converted when
-// used (float32 arithmetic either way).
+// Tag of the 32-byte packed SH representation (sh_codec.cuh).
+struct ShCodec32 {};
+
+// SH coefficients are staged in their storage form and converted when used
+// (float32 arithmetic either way): PER elements of type T per gaussian.
+template <int DEG, typename SHT>
+struct ShStage {
+  using T = SHT;
+  static constexpr int PER = (DEG + 1) * (DEG + 1) * 3;
+};
+template <int DEG>
+struct ShStage<DEG, ShCodec32> {
+  using T = uint32_t;
+  static constexpr int PER = SH_CODEC_WORDS;
+};
+
 template <int DEG, typename SHT>
 struct ProjSmem {
-  static constexpr int K = (DEG + 1) * (DEG + 1);
   float means[PROJ_THREADS * 3];
   float scales[PROJ_THREADS * 3];
   float4 quats[PROJ_THREADS];
   float logits[PROJ_THREADS];
-  alignas(16) SHT sh[PROJ_THREADS * K * 3];
+  alignas(16) typename ShStage<DEG, SHT>::T sh[PROJ_THREADS * ShStage<DEG, SHT>::PER];
+  float sh_scale2[SH_CODEC_CH];  // packed SH: s / Q^2 per channel
   uint64_t bar;
   ViewDesc views[1];  // [n_views], sized at launch
+};
+
+// The coefficients of band L: converted from the staged type, or decoded
+// from the 32-byte packed form.
+template <int L, typename SHT>
+struct BandLoad {
+  template <typename T>
+  __device__ static void run(const T* g, float* c, const float*) {
+    constexpr int B = 2 * L + 1, OFF = L * L;
+#pragma unroll
+    for (int k = 0; k < B * 3; ++k) c[k] = sh_f(g[OFF * 3 + k]);
+  }
+};
+
+template <int K0, int N>
+__device__ __forceinline__ void codec_bases(const uint32_t* w, const float* s2, float* c) {
+  if constexpr (N > 0) {
+    sh_codec_basis<K0>(w, s2, c[0], c[1], c[2]);
+    codec_bases<K0 + 1, N - 1>(w, s2, c + 3);
+  }
+}
+
+template <int L>
+struct BandLoad<L, ShCodec32> {
+  __device__ static void run(const uint32_t* w, float* c, const float* s2) {
+    codec_bases<L * L, 2 * L + 1>(w, s2, c);
+  }
 };
 
 template <int DEG, typename SHT>
@@ -50,13 +92,12 @@ __host__ __device__ constexpr size_t proj_smem_bytes(int n_views) {
 }
 
 // SH colour of one band for up to VG views: acc[v] += sum_m Y_lm(d_v) c_lm.
-template <int L, int VG, typename SHT>
-__device__ __forceinline__ void sh_band(const SHT* __restrict__ sh_g, const float (&d)[VG][3], float (&acc)[VG][3],
-                                        int nv) {
-  constexpr int B = 2 * L + 1, OFF = L * L;
+template <int L, int VG, typename SHT, typename T>
+__device__ __forceinline__ void sh_band(const T* __restrict__ sh_g, const float (&d)[VG][3], float (&acc)[VG][3],
+                                        int nv, const float* s2) {
+  constexpr int B = 2 * L + 1;
   float c[B * 3];
-#pragma unroll
-  for (int k = 0; k < B * 3; ++k) c[k] = sh_f(sh_g[OFF * 3 + k]);
+  BandLoad<L, SHT>::run(sh_g, c, s2);
 #pragma unroll
   for (int v = 0; v < VG; ++v) {
     if (v >= nv) break;
@@ -117,7 +158,9 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   constexpr int VG = 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ProjSmem<DEG, SHT>& s = *reinterpret_cast<ProjSmem<DEG, SHT>*>(smem_raw);
-  const SHT* sh_in = reinterpret_cast<const SHT*>(a.sh);
+  using ST = typename ShStage<DEG, SHT>::T;
+  constexpr int PER = ShStage<DEG, SHT>::PER;
+  const ST* sh_in = reinterpret_cast<const ST*>(a.sh);
   const int tid = threadIdx.x;
   const long long i0 = (long long)blockIdx.x * PROJ_THREADS;
   const int cnt = (int)min((long long)PROJ_THREADS, a.n - i0);
@@ -133,13 +176,13 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
     __syncthreads();
     if (tid == 0) {
       const uint32_t b3 = PROJ_THREADS * 12, b4 = PROJ_THREADS * 16, b1 = PROJ_THREADS * 4,
-                     bsh = PROJ_THREADS * K * 3 * (uint32_t)sizeof(SHT);
+                     bsh = PROJ_THREADS * PER * (uint32_t)sizeof(ST);
       mbar_arrive_expect_tx(&s.bar, 2 * b3 + b4 + b1 + bsh);
       tma_load_1d(s.means, a.means + i0 * 3, b3, &s.bar);
       tma_load_1d(s.scales, a.log_scales + i0 * 3, b3, &s.bar);
       tma_load_1d(s.quats, a.quats + i0 * 4, b4, &s.bar);
       tma_load_1d(s.logits, a.opacity_logits + i0, b1, &s.bar);
-      tma_load_1d(s.sh, sh_in + i0 * K * 3, bsh, &s.bar);
+      tma_load_1d(s.sh, sh_in + i0 * PER, bsh, &s.bar);
     }
   } else {
     for (int j = tid; j < cnt * 3; j += PROJ_THREADS) {
@@ -150,9 +193,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       s.quats[j] = reinterpret_cast<const float4*>(a.quats)[i0 + j];
       s.logits[j] = a.opacity_logits[i0 + j];
     }
-    for (int j = tid; j < cnt * K * 3; j += PROJ_THREADS) s.sh[j] = sh_in[i0 * K * 3 + j];
+    for (int j = tid; j < cnt * PER; j += PROJ_THREADS) s.sh[j] = sh_in[i0 * PER + j];
   }
-  // the view table, while the copies are in flight
+  // the view table (and the packed-SH scales), while the copies are in flight
+  if (a.sh_scale2 && tid < SH_CODEC_CH) s.sh_scale2[tid] = a.sh_scale2[tid];
   {
     const int words = nv * (int)(sizeof(ViewDesc) / 4);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(a.views);
@@ -284,7 +328,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   }
 
   // view-dependent colour: max(0, SH(d) + 0.5), d = normalise(mean - campos)
-  const SHT* sh_g = s.sh + tid * K * 3;
+  const ST* sh_g = s.sh + tid * PER;
   const bool keep = a.splats != nullptr && valid;
   for (int v0 = 0; v0 < nv; v0 += VG) {
     const int g = min(VG, nv - v0);
@@ -301,10 +345,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       d[v][2] = dz * dn;
       acc[v][0] = acc[v][1] = acc[v][2] = 0.f;
     }
-    sh_band<0, VG, SHT>(sh_g, d, acc, g);
-    if (DEG >= 1) sh_band<1, VG, SHT>(sh_g, d, acc, g);
-    if (DEG >= 2) sh_band<2, VG, SHT>(sh_g, d, acc, g);
-    if (DEG >= 3) sh_band<3, VG, SHT>(sh_g, d, acc, g);
+    sh_band<0, VG, SHT>(sh_g, d, acc, g, s.sh_scale2);
+    if (DEG >= 1) sh_band<1, VG, SHT>(sh_g, d, acc, g, s.sh_scale2);
+    if (DEG >= 2) sh_band<2, VG, SHT>(sh_g, d, acc, g, s.sh_scale2);
+    if (DEG >= 3) sh_band<3, VG, SHT>(sh_g, d, acc, g, s.sh_scale2);
 #pragma unroll
     for (int v = 0; v < VG; ++v) {
       if (v >= g) break;
@@ -380,6 +424,9 @@ static cudaError_t launch_project_deg(const ProjectArgs& a, cudaStream_t st) {
   switch (a.sh_storage) {
     case HG_SH_F16: return launch_project_t<DEG, __half>(a, st);
     case HG_SH_BF16: return launch_project_t<DEG, __nv_bfloat16>(a, st);
+    case HG_SH_CODEC32:
+      if (DEG != 3) return cudaErrorInvalidValue;
+      return launch_project_t<DEG, ShCodec32>(a, st);
     default: return launch_project_t<DEG, float>(a, st);
   }
 }

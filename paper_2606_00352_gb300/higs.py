@@ -31,7 +31,7 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward", "hg_autotune",
            "hg_serve_create", "hg_serve_add_scene", "hg_serve_submit", "hg_serve_poll", "hg_serve_wait",
            "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats", "hg_serve_destroy", "hg_l2_loss",
-           "hg_adam_step"]
+           "hg_adam_step", "hg_scene_sh_codec"]
 
 
 class AdamOpts(C.Structure):
@@ -52,7 +52,7 @@ class SceneDesc(C.Structure):
                 ("pad", C.c_int32)]
 
 
-SH_F32, SH_F16, SH_BF16 = 0, 1, 2
+SH_F32, SH_F16, SH_BF16, SH_CODEC32 = 0, 1, 2, 3
 
 
 class CameraC(C.Structure):
@@ -154,6 +154,8 @@ def load(path: str = LIB_PATH):
                                 C.POINTER(RenderOpts), C.POINTER(TuneResult), C.c_int, C.POINTER(C.c_int), C.c_void_p]
     lib.hg_render_backward.restype = C.c_int
     lib.hg_render_backward.argtypes = [C.c_void_p] + [C.c_void_p] * 7
+    lib.hg_scene_sh_codec.restype = C.c_int
+    lib.hg_scene_sh_codec.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hg_l2_loss.restype = C.c_int
     lib.hg_l2_loss.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hg_adam_step.restype = C.c_int
@@ -268,7 +270,8 @@ class GpuScene:
             if x.dtype != dtype:
                 x = x.to(torch.float32).to(dtype)
             return x.contiguous()
-        sh_t = {SH_F32: torch.float32, SH_F16: torch.float16, SH_BF16: torch.bfloat16}[sh_storage]
+        sh_t = {SH_F32: torch.float32, SH_F16: torch.float16, SH_BF16: torch.bfloat16,
+                SH_CODEC32: torch.float32}[sh_storage]
         self.tensors = [t(means), t(log_scales), t(quats), t(opacity_logits), t(sh, sh_t)]
         n = self.tensors[0].shape[0]
         d = SceneDesc(n, sh_degree, int(borrow), *[x.data_ptr() for x in self.tensors], sh_storage, 0)
@@ -279,6 +282,14 @@ class GpuScene:
         self.sh_storage = sh_storage
         if not borrow:
             self.tensors = None
+
+    def sh_codec(self):
+        """Packed SH of a SH_CODEC32 scene: (scales [16][3], codes [n][8])."""
+        scales = np.zeros((16, 3), np.float32)
+        codes = np.zeros((self.n, 8), np.uint32)
+        check(self.ctx.lib.hg_scene_sh_codec(self.h, scales.ctypes.data_as(C.c_void_p),
+                                             codes.ctypes.data_as(C.c_void_p)))
+        return scales, codes
 
     @classmethod
     def from_scene(cls, ctx: Context, scene, borrow: bool = False, sh_storage: int = SH_F32):

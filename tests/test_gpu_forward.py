@@ -275,6 +275,44 @@ def test_half_precision_sh_storage(lib, ctx, storage):
         lib.render_backward(st, gs, torch.zeros(sum(c.width * c.height for c in cams) * 3, device="cuda"))
 
 
+def _codec_scene(seed, sigma_high):
+    scene = scenes.cluster_scene(30_000, 8, 1.2, seed=seed, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    if sigma_high is not None:
+        g = np.random.default_rng(seed)
+        scene.sh[:, 1:] = g.normal(0, sigma_high, scene.sh[:, 1:].shape).astype(np.float32)
+    return scene
+
+
+@pytest.mark.parametrize("sigma_high", [None, 0.02])
+def test_packed_sh_codec(lib, ctx, sigma_high):
+    """32-byte packed SH (Sec. 4.2): the device encoder gives the oracle
+    encoder's codes for the device's scales (bit for bit), the scales are the
+    99.5th percentile within one histogram bin, and the image equals the
+    oracle's on the decoded coefficients.  The image's PSNR against the
+    float32 coefficients is measured (it depends on the SH distribution: the
+    benchmark's N(0, 0.2) higher-order coefficients, or N(0, 0.02))."""
+    from oracle import sh_codec as SC
+    scene = _codec_scene(21, sigma_high)
+    gs = lib.GpuScene.from_scene(ctx, scene, sh_storage=lib.SH_CODEC32)
+    scales, codes = gs.sh_codec()
+    sh = scene.sh.reshape(-1, 16, 3)
+    assert np.array_equal(codes, SC.encode(sh, scales))
+    frac = (np.abs(SC.ycocg_r(sh)) <= scales[None]).mean(0)
+    assert np.all(frac >= 0.995) and np.all(frac <= 0.9965)
+    ref_scene = scene.copy()
+    ref_scene.sh = SC.decode(codes, scales).astype(np.float32).reshape(scene.sh.shape)
+    cams = scenes.scene_orbit(8, 320, 200)[1:3]
+    imgs, ts = render_np(lib, gs, cams)
+    mse = []
+    for v, cam in enumerate(cams):
+        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)))
+        full = C.render(P.project(scene, cam))["rgb"]
+        mse.append(np.mean((imgs[v].reshape(full.shape) - full) ** 2))
+    psnr = 10 * np.log10(1.0 / max(np.mean(mse), 1e-30))
+    print(f"packed SH, higher-order sigma {sigma_high or 0.2}: PSNR {psnr:.1f} dB against float32 coefficients")
+    assert psnr > (40.0 if sigma_high else 28.0)
+
+
 def test_image_background_and_multiview(lib, ctx):
     scene = scenes.uniform_scene(8000, seed=6)
     cams = [scenes.look_at((3, 0, 0), width=128, height=128),

@@ -11,7 +11,7 @@ F32 = np.float32
 
 
 def test_fields_fit_32_bytes():
-    assert sum(sum(b) for b in SC.BITS) == 236 <= 256
+    assert sum(sum(b) for b in SC.BITS) == 252 <= 256
     assert len(SC.BITS) == SC.N_BASES == 16
 
 
@@ -42,7 +42,9 @@ def test_quantiser_is_within_half_a_step_in_the_gamma_domain():
 
 
 def test_grid_values_round_trip():
-    """v = s (q / Q)^2 sign(q) decodes to itself for every code q."""
+    """Values on the quantisation grid decode to themselves: v = s (q / Q)^2
+    sign(q) for the square-root fields, q / 4095 s for the linear DC chroma,
+    float16 values for the DC luma."""
     s = np.full((16, 3), 0.5, F32)
     n = 31
     ycc = np.zeros((2 * n + 1, 16, 3), np.float64)
@@ -50,12 +52,31 @@ def test_grid_values_round_trip():
         for k in range(16):
             for c in range(3):
                 b = SC.BITS[k][c]
-                qm = 2 ** (b - 1) - 1
-                qq = int(np.clip(q, -qm, qm))
-                ycc[i, k, c] = np.sign(qq) * (qq / qm) ** 2 * 0.5
+                if k == 0 and c == 0:
+                    ycc[i, k, c] = float(np.float16(q / 8.0))
+                elif k == 0:
+                    ycc[i, k, c] = q * 100 / SC.DC_LINEAR_Q * 0.5
+                else:
+                    qm = 2 ** (b - 1) - 1
+                    qq = int(np.clip(q, -qm, qm))
+                    ycc[i, k, c] = np.sign(qq) * (qq / qm) ** 2 * 0.5
     rgb = SC.ycocg_r_inverse(ycc).astype(F32)
     dec = SC.decode(SC.encode(rgb, s), s)
     np.testing.assert_allclose(dec, rgb, atol=2e-6)
+
+
+def test_dc_fields():
+    """DC luma is the float16 of Y; DC chroma is within half a linear step."""
+    g = np.random.default_rng(3)
+    sh = np.zeros((3000, 16, 3), F32)
+    sh[:, 0] = g.normal(1.8, 0.7, (3000, 3))
+    s = SC.scales(sh)
+    dec_ycc = SC.ycocg_r(SC.decode(SC.encode(sh, s), s).astype(F32))
+    ycc = SC.ycocg_r(sh)
+    np.testing.assert_allclose(dec_ycc[:, 0, 0], ycc[:, 0, 0].astype(np.float16).astype(np.float32), rtol=2e-6)
+    inside = np.abs(ycc[:, 0, 1:]) <= s[0, 1:]
+    err = np.abs(dec_ycc[:, 0, 1:] - ycc[:, 0, 1:])
+    assert np.all(err[inside] <= (s[0, 1:] / SC.DC_LINEAR_Q * 0.5 + 1e-6)[None].repeat(3000, 0)[inside])
 
 
 def test_every_field_has_its_own_bits():
