@@ -485,6 +485,18 @@ def gpu_arm(args):
                                  "project_ms": round(statistics.mean(s_["ms_project"] for s_ in hstats), 4),
                                  "psnr_db_vs_f32_sh": round(10 * math.log10(1.0 / max(mse, 1e-30)), 1)}
             gsv.close()
+        # half-precision rasterisation on the float32-SH scene
+        fopts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
+                             batch_cap=opts.batch_cap, bin_test=opts.bin_test,
+                             flags=higs.FLAG_TIMING | higs.FLAG_FP16)
+        hsteps = max(3, min(args.steps, 10))
+        hms, hstats, _ = time_graph(higs, gs, cams, fopts, hsteps, min(args.warmup, 3), rank, world, stream)
+        hvalue, hms = job_throughput(hms, hsteps * VIEWS, world)
+        img, _ = higs.render(gs, pose_batch(cams, 0, rank), fopts, with_T=False, stream=stream)
+        mse = float(((img - ref_img) ** 2).mean().item())
+        sh_variants["fp16_raster"] = {"value": round(hvalue, 2), "unit": UNIT, "ms_per_step": round(hms / hsteps, 3),
+                                      "raster_ms": round(statistics.mean(s_["ms_raster"] for s_ in hstats), 4),
+                                      "psnr_db_vs_f32": round(10 * math.log10(1.0 / max(mse, 1e-30)), 1)}
     del scene16
 
     plain = None
@@ -544,7 +556,7 @@ def gpu_arm(args):
         "gpu_launches": int(kernels * args.steps),
         "clocks": clocks,
         "plain_path": plain,
-        "sh_storage_variants": sh_variants or None,
+        "precision_variants": sh_variants or None,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "frame_stats": {
             "pairs_per_step": int(statistics.mean(s["n_pairs"] for s in s0)),

@@ -141,7 +141,13 @@ enum {
                               composite the partials by Eq. 1 with exact-termination
                               replay (the paper's schedule) instead of chaining the
                               batches of a macro-tile in depth order */
-  HG_FLAG_PROFILE = 16     /* count rasteriser phase cycles (hg_frame_stats) */
+  HG_FLAG_PROFILE = 16,    /* count rasteriser phase cycles (hg_frame_stats) */
+  HG_FLAG_FP16 = 32        /* half-precision rasterisation (Sec. 3.5, 4.5): alpha of
+                              the two pixels a thread owns in half2 arithmetic from
+                              prescaled Cholesky factors and macro-tile-relative
+                              coordinates; transmittance and colour stay float32 with
+                              exact per-pixel termination.  Its own tolerance (PSNR,
+                              not the float32 bounds); not with save_for_backward */
 };
 
 typedef struct {

@@ -282,6 +282,8 @@ static bool valid_opts(const hg_render_opts* o, std::string& why) {
   if (!shape_ok) return why = "macro shape must be 8x4, 4x4 or 8x8", false;
   if (o->batch_cap < 32 || o->batch_cap > 2048 || (o->batch_cap & 31)) return why = "batch_cap", false;
   if (o->bin_test != HG_BIN_RECT && o->bin_test != HG_BIN_ELLIPSE) return why = "bin_test", false;
+  if ((o->flags & HG_FLAG_FP16) && o->save_for_backward)
+    return why = "HG_FLAG_FP16 does not save for the backward (float32 only)", false;
   return true;
 }
 
@@ -558,6 +560,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
     ra.persistent_ctas = 0;
     ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;
+    ra.fp16 = (o->flags & HG_FLAG_FP16) ? 1 : 0;
     ra.profile = (o->flags & HG_FLAG_PROFILE) ? 1 : 0;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");

@@ -8,6 +8,8 @@
 // decisions are written as saturated multiply-adds, which keeps the inner
 // loop off the integer/compare pipe.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace hg {
@@ -91,6 +93,43 @@ __device__ __forceinline__ void blend(PixelAcc& p, float ubase, float dy, const 
                                       const float4& g2) {
   float raw;
   apply_alpha(p, alpha_of(ubase, dy, g0, g1, g2, raw), g2);
+}
+
+// ---- half-precision rasterisation (HG_FLAG_FP16, Sec. 3.5 / 4.5)
+// The staged record's first two float4 are rewritten as half2 pairs
+// {my, my} {l1', l1'} {l2', l2'} {o, o} | {mx, mx} {l0', l0'} {E, E} {0, 0},
+// positions relative to the macro-tile origin (so every operand of the
+// Mahalanobis sum stays far inside the fp16 range); the colour float4 stays.
+__device__ __forceinline__ uint32_t h2_bits(float x) {
+  const __half2 h = __float2half2_rn(x);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void half_record(float4* r, float ox, float oy) {
+  const float4 g0 = r[0], g1 = r[1], g2 = r[2];
+  uint4* q = reinterpret_cast<uint4*>(r);
+  q[0] = make_uint4(h2_bits(g0.y - oy), h2_bits(g0.w), h2_bits(g1.x), h2_bits(g1.y));
+  q[1] = make_uint4(h2_bits(g0.x - ox), h2_bits(g0.z), h2_bits(g2.w), 0u);
+}
+
+// alpha of one gaussian at the two pixels a thread owns, in half2: hpx the
+// pixel column, hpy the two pixel rows (macro-tile-relative).  The blend test
+// e <= E is the saturated multiply-add of the float32 path at half scale
+// (fp16 spacing at e = 6.5 is 2^-8, so (E - e) 2^10 + 1 is <= -3 when e > E).
+__device__ __forceinline__ float2 half_alpha2(const float4* r, __half2 hpx, __half2 hpy) {
+  const uint4 q0 = reinterpret_cast<const uint4*>(r)[0], q1 = reinterpret_cast<const uint4*>(r)[1];
+  const __half2 my = *reinterpret_cast<const __half2*>(&q0.x), l1 = *reinterpret_cast<const __half2*>(&q0.y);
+  const __half2 l2 = *reinterpret_cast<const __half2*>(&q0.z), o = *reinterpret_cast<const __half2*>(&q0.w);
+  const __half2 mx = *reinterpret_cast<const __half2*>(&q1.x), l0 = *reinterpret_cast<const __half2*>(&q1.y);
+  const __half2 E = *reinterpret_cast<const __half2*>(&q1.z);
+  const __half2 ub = __hmul2(l0, __hsub2(hpx, mx));
+  const __half2 dy = __hsub2(hpy, my);
+  const __half2 u = __hfma2(l1, dy, ub);
+  const __half2 w = __hmul2(l2, dy);
+  const __half2 e = __hfma2(u, u, __hmul2(w, w));
+  const __half2 a = __hmin2(__hmul2(o, h2exp2(__hneg2(e))), __float2half2_rn(ALPHA_MAX));
+  const __half2 f = __hfma2_sat(__hsub2(E, e), __float2half2_rn(1024.f), __float2half2_rn(1.f));
+  return __half22float2(__hmul2(a, f));
 }
 
 // Per-gaussian level E of the blend test (stored in the record's g2.w).

@@ -110,6 +110,7 @@ struct RasterArgs {
   float4* prefix;             // optional [cap_batches][M][64]: (C, +-T) entering the batch (backward)
   int persistent_ctas;
   int independent;            // never wait: every batch after the first renders from T = 1
+  int fp16;                   // half2 alpha (HG_FLAG_FP16)
   int profile;                // accumulate phase cycles into FrameCounters::raster_cycles
   FrameCounters* fc;
 };

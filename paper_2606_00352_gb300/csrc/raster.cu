@@ -37,7 +37,7 @@ constexpr int RW = 8;  // warps per CTA
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
-template <int MW, int MH, bool SAVE>
+template <int MW, int MH, bool SAVE, bool HALF>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -98,6 +98,15 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     // phase 1: per-gaussian tile masks, transposed to per-tile masks
     const int K = (int)((count + 31) / 32);
     build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, RW);
+    if (HALF) {
+      // each thread rewrites the records of the gaussians it built masks for
+      // (no other thread reads them before the barrier below) as half2 pairs
+      // relative to the macro-tile origin; the colour stays float32
+      __syncwarp();
+      const float ox = (float)(mtx0 * TILE), oy = (float)(mty0 * TILE);
+      for (uint32_t j = (uint32_t)warp * 32 + lane; j < count; j += RT)
+        half_record(s_rec + (size_t)j * 3, ox, oy);
+    }
     __syncthreads();
 
     // tile work queue (warp 0), longest first: a tile's work is about the
@@ -190,6 +199,9 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         pre[lane + 32] = pixel_state(p1);
       }
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
+      // macro-tile-relative pixel coordinates (half mode)
+      const __half2 hpx = __float2half2_rn((float)(px - mtx0 * TILE));
+      const __half2 hpy = __floats2half2_rn((float)(py - mty0 * TILE), (float)(py + 4 - mty0 * TILE));
       uint32_t n_blend = 0;
       // gaussians of this tile in depth order: the set bits of its per
       // mini-batch masks (warp-uniform), blended directly; the unanimous
@@ -203,14 +215,21 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           const uint32_t bit = m & (0u - m);
           m ^= bit;
           const uint32_t j = (uint32_t)k * 32 + (__ffs(bit) - 1);
-          const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
-          const float ub = g0.z * (fpx - g0.x);
-          // a half the gaussian cannot reach is skipped (its blend is a no-op)
-          if (mt & bit) {
-            blend(p0, ub, fpy - g0.y, g0, g1, g2);
-            if (mb & bit) blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+          if (HALF) {
+            const float2 al = half_alpha2(s_rec + (size_t)j * 3, hpx, hpy);
+            const float4 g2 = s_rec[j * 3 + 2];
+            if (mt & bit) apply_alpha(p0, al.x, g2);
+            if (mb & bit) apply_alpha(p1, al.y, g2);
           } else {
-            blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
+            const float ub = g0.z * (fpx - g0.x);
+            // a half the gaussian cannot reach is skipped (its blend is a no-op)
+            if (mt & bit) {
+              blend(p0, ub, fpy - g0.y, g0, g1, g2);
+              if (mb & bit) blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+            } else {
+              blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+            }
           }
         } while (m);
         if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
@@ -248,28 +267,29 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   if (lane == 0 && evals) atomicAdd(&a.fc->raster_evals, evals);
 }
 
-template <int MW, int MH, bool SAVE>
+template <int MW, int MH, bool SAVE, bool HALF>
 cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) {
   constexpr int M = MW * MH;
   const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 8;
   cudaError_t e =
-      cudaFuncSetAttribute(k_raster<MW, MH, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_raster<MW, MH, SAVE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1, dev = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raster<MW, MH, SAVE>, RT, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raster<MW, MH, SAVE, HALF>, RT, sm);
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (occ < 1) occ = 1;
   const int grid = a.persistent_ctas > 0 ? a.persistent_ctas : sms * occ;
-  k_raster<MW, MH, SAVE><<<grid, RT, sm, st>>>(a, cap);
+  k_raster<MW, MH, SAVE, HALF><<<grid, RT, sm, st>>>(a, cap);
   note_launch();
   return cudaGetLastError();
 }
 
 template <int MW, int MH>
 cudaError_t launch_raster_shape(const RasterArgs& a, int cap, cudaStream_t st) {
-  return a.prefix ? launch_raster_kernel<MW, MH, true>(a, cap, st)
-                                  : launch_raster_kernel<MW, MH, false>(a, cap, st);
+  if (a.prefix) return launch_raster_kernel<MW, MH, true, false>(a, cap, st);
+  return a.fp16 ? launch_raster_kernel<MW, MH, false, true>(a, cap, st)
+                : launch_raster_kernel<MW, MH, false, false>(a, cap, st);
 }
 
 }  // namespace

@@ -21,7 +21,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error"
           -5: "device timeout", -6: "busy", -7: "not found", -8: "cancelled", -9: "unsupported"}
 PATH_HIGS, PATH_PLAIN = 0, 1
 BIN_RECT, BIN_ELLIPSE = 0, 1
-FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT, FLAG_PROFILE = 1, 2, 4, 8, 16
+FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT, FLAG_PROFILE, FLAG_FP16 = 1, 2, 4, 8, 16, 32
 BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE = range(6)
 
 EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",

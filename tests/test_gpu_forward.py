@@ -313,6 +313,28 @@ def test_packed_sh_codec(lib, ctx, sigma_high):
     assert psnr > (40.0 if sigma_high else 28.0)
 
 
+@pytest.mark.parametrize("macro", [(4, 4), (8, 4)])
+def test_half_precision_rasterisation(lib, ctx, macro):
+    """HG_FLAG_FP16 (Sec. 3.5 / 4.5): alpha in half2 from the prescaled
+    Cholesky factors and macro-tile-relative positions.  Its tolerance is
+    image fidelity, not the float32 bounds: PSNR against the float64 oracle
+    of at least 50 dB.  It does not save for the backward."""
+    import torch
+    scene = scenes.cluster_scene(40_000, 8, 1.2, seed=14, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    cams = scenes.scene_orbit(8, 320, 200)[4:6]
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    imgs, ts = render_np(lib, gs, cams, macro_w=macro[0], macro_h=macro[1], flags=lib.FLAG_FP16)
+    mse = []
+    for v, cam in enumerate(cams):
+        ref = C.render(P.project(scene, cam))
+        mse.append(np.mean((imgs[v].reshape(ref["rgb"].shape) - ref["rgb"]) ** 2))
+    psnr = 10 * np.log10(1.0 / np.mean(mse))
+    print(f"fp16 rasterisation {macro}: PSNR {psnr:.1f} dB against the float64 oracle")
+    assert psnr >= 50.0
+    with pytest.raises(lib.HgError):
+        lib.render(gs, cams, lib.Options(flags=lib.FLAG_FP16, save_for_backward=True))
+
+
 def test_image_background_and_multiview(lib, ctx):
     scene = scenes.uniform_scene(8000, seed=6)
     cams = [scenes.look_at((3, 0, 0), width=128, height=128),
