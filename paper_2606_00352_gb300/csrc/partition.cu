@@ -23,6 +23,7 @@ namespace hg {
 namespace {
 
 constexpr int PART_THREADS = 512;
+constexpr int UNR = 4;  // entries per thread per round in count / fill
 
 __global__ void __launch_bounds__(PART_THREADS) k_count(PartitionArgs a) {
   extern __shared__ uint32_t hist[];
@@ -34,11 +35,22 @@ __global__ void __launch_bounds__(PART_THREADS) k_count(PartitionArgs a) {
   __syncthreads();
   const long long i_end = min(a.n, (long long)(b + 1) * BP);
   const uint32_t* vis = a.vis + (size_t)v * a.vis_words;
-  for (long long i = (long long)b * BP + tid; i < i_end; i += PART_THREADS) {
-    const uint32_t word = vis[i >> 5];
-    if (word == 0) continue;  // whole warp culled
-    if (!((word >> (i & 31)) & 1u)) continue;
-    for_each_cell(a.bin[(size_t)v * a.n + i], V.mgx, [&](int m) { atomicAdd(&hist[m], 1u); });
+  // UNR entries per thread per round: all their loads are issued before any
+  // is used (the loop is bound by memory latency, not bandwidth)
+  for (long long i0 = (long long)b * BP + tid; i0 < i_end; i0 += UNR * PART_THREADS) {
+    uint4 rec[UNR];
+    bool on[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const long long i = i0 + (long long)u * PART_THREADS;
+      on[u] = i < i_end && ((vis[i >> 5] >> (i & 31)) & 1u);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+      if (on[u]) rec[u] = a.bin[(size_t)v * a.n + i0 + (long long)u * PART_THREADS];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+      if (on[u]) for_each_cell(rec[u], V.mgx, [&](int m) { atomicAdd(&hist[m], 1u); });
   }
   __syncthreads();
   uint16_t* row = a.hist + (size_t)b * a.n_seg + V.seg_base;
@@ -200,17 +212,32 @@ __global__ void __launch_bounds__(PART_THREADS) k_fill(PartitionArgs a) {
   __syncthreads();
   const long long i_end = min(a.n, (long long)(b + 1) * BP);
   const uint32_t* vis = a.vis + (size_t)v * a.vis_words;
-  for (long long i = (long long)b * BP + tid; i < i_end; i += PART_THREADS) {
-    const uint32_t word = vis[i >> 5];
-    if (word == 0) continue;
-    if (!((word >> (i & 31)) & 1u)) continue;
-    const size_t o = (size_t)v * a.n + i;
-    const uint32_t key = a.dkeys[o];
-    for_each_cell(a.bin[o], V.mgx, [&](int m) {
-      const uint32_t pos = atomicAdd(&cursor[m], 1u);
-      a.keys[pos] = key;
-      a.vals[pos] = (uint32_t)i;
-    });
+  for (long long i0 = (long long)b * BP + tid; i0 < i_end; i0 += UNR * PART_THREADS) {
+    uint4 rec[UNR];
+    uint32_t key[UNR];
+    bool on[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const long long i = i0 + (long long)u * PART_THREADS;
+      on[u] = i < i_end && ((vis[i >> 5] >> (i & 31)) & 1u);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (!on[u]) continue;
+      const size_t o = (size_t)v * a.n + i0 + (long long)u * PART_THREADS;
+      rec[u] = a.bin[o];
+      key[u] = a.dkeys[o];
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (!on[u]) continue;
+      const uint32_t id = (uint32_t)(i0 + (long long)u * PART_THREADS);
+      for_each_cell(rec[u], V.mgx, [&](int m) {
+        const uint32_t pos = atomicAdd(&cursor[m], 1u);
+        a.keys[pos] = key[u];
+        a.vals[pos] = id;
+      });
+    }
   }
 }
 
