@@ -561,6 +561,11 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.persistent_ctas = 0;
     ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;
     ra.fp16 = (o->flags & HG_FLAG_FP16) ? 1 : 0;
+    ra.direct_out = o->save_for_backward ? 0 : 1;
+    ra.first_batch = pa.first_batch;
+    ra.out_rgb = out_rgb;
+    ra.out_T = out_T;
+    for (int c = 0; c < 3; ++c) ra.bg[c] = o->bg[c];
     ra.profile = (o->flags & HG_FLAG_PROFILE) ? 1 : 0;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");
@@ -573,6 +578,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ma.tile_state = ra.tile_state;
     ma.tile_rank = ra.tile_rank;
     ma.first_batch = pa.first_batch;
+    ma.chain = ra.chain;
     ma.batches = pa.batches;
     ma.vals = pa.vals;
     ma.rec = ra.rec;

@@ -111,6 +111,13 @@ struct RasterArgs {
   int persistent_ctas;
   int independent;            // never wait: every batch after the first renders from T = 1
   int fp16;                   // half2 alpha (HG_FLAG_FP16)
+  // direct output: the last chained batch of a macro-tile writes the image
+  // (C + T bg, T) itself and marks the segment CHAIN_DONE for the merge
+  int direct_out;
+  const uint32_t* first_batch;  // [S + 1]
+  float* out_rgb;
+  float* out_T;
+  float bg[3];
   int profile;                // accumulate phase cycles into FrameCounters::raster_cycles
   FrameCounters* fc;
 };
@@ -118,8 +125,10 @@ struct RasterArgs {
 constexpr uint32_t BATCH_CHAINED = 1;  // rendered from the exact transmittance entering it
 constexpr uint32_t BATCH_LOCAL = 2;    // rendered from T = 1; composited by the merge
 constexpr uint32_t CHAIN_BROKEN = 0x80000000u;
+constexpr uint32_t CHAIN_DONE = 0x40000000u;  // the raster wrote the segment's output
 
 struct MergeArgs {
+  const uint32_t* chain;      // [S]: CHAIN_DONE segments were written by the rasteriser
   const float4* partial;
   const unsigned long long* active;
   const uint32_t* mode;

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
     const int lt = tile - V.tile_base;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
     const int seg = V.seg_base + (ty / MH) * V.mgx + (tx / MW);
+    if (a.chain[seg] & CHAIN_DONE) continue;  // written by the rasteriser
     const int tl = (ty % MH) * MW + (tx % MW);
     const int px = tx * TILE + (lane & 7), py = ty * TILE + (lane >> 3);
     const bool in0 = px < V.W && py < V.H, in1 = px < V.W && py + 4 < V.H;

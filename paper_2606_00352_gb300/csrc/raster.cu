@@ -22,9 +22,11 @@
 //           bits of the tile's mini-batch masks (warp-uniform words, so the
 //           gaussians are taken straight from the masks), with a unanimous
 //           vote per mini-batch as the early out when every pixel has stopped
-//   store   chained: the new per-tile state; unchained: the partial
-//           (r, g, b, +-T) with streaming stores (T negated when the pixel
-//           stopped inside the batch)
+//   store   chained: the new per-tile state, or, for the last batch of the
+//           macro-tile, the final pixels straight into the image (the
+//           macro-tile's other tiles from their state or the background; the
+//           merge then skips it); unchained: the partial (r, g, b, +-T) with
+//           streaming stores (T negated when the pixel stopped inside it)
 #include "blend.cuh"
 #include "kernels.cuh"
 #include "raster_common.cuh"
@@ -37,6 +39,27 @@ constexpr int RW = 8;  // warps per CTA
 constexpr int RT = RW * 32;
 constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
+// Final pixels of a tile (C + T bg, T) into the outputs.
+__device__ __forceinline__ void write_pixels(const RasterArgs& a, const ViewDesc& V, int px, int py, bool in0,
+                                             bool in1, const PixelAcc& p0, const PixelAcc& p1) {
+  if (in0) {
+    const long long o = V.pix_base + (long long)py * V.W + px;
+    const float tf = pixel_final_T(p0);
+    a.out_rgb[o * 3 + 0] = fmaf(tf, a.bg[0], p0.r);
+    a.out_rgb[o * 3 + 1] = fmaf(tf, a.bg[1], p0.g);
+    a.out_rgb[o * 3 + 2] = fmaf(tf, a.bg[2], p0.b);
+    if (a.out_T) a.out_T[o] = tf;
+  }
+  if (in1) {
+    const long long o = V.pix_base + (long long)(py + 4) * V.W + px;
+    const float tf = pixel_final_T(p1);
+    a.out_rgb[o * 3 + 0] = fmaf(tf, a.bg[0], p1.r);
+    a.out_rgb[o * 3 + 1] = fmaf(tf, a.bg[1], p1.g);
+    a.out_rgb[o * 3 + 2] = fmaf(tf, a.bg[2], p1.b);
+    if (a.out_T) a.out_T[o] = tf;
+  }
+}
+
 template <int MW, int MH, bool SAVE, bool HALF>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
@@ -47,7 +70,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   __shared__ uint64_t bar;
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
-  __shared__ unsigned long long s_active, s_blended;
+  __shared__ unsigned long long s_active, s_blended, s_written;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -65,6 +88,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       s_unit = atomicAdd(&a.fc->raster_claim, 1u);
       s_qhead = 0;
       s_blended = 0;
+      s_written = 0;
     }
     __syncthreads();
     const uint32_t u = s_unit;
@@ -170,6 +194,9 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     const long long t_p2 = a.profile ? clock64() : 0;
     const uint32_t qn = s_qn;
     const bool chained = s_mode == BATCH_CHAINED;
+    // the last batch of a chained macro-tile writes the image itself
+    const bool write_out =
+        !SAVE && a.direct_out && chained && rank + 1 == a.first_batch[seg + 1] - a.first_batch[seg];
 
     // phase 2: warps claim tiles
     while (true) {
@@ -191,7 +218,13 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         pixel_load(p1, in1, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane + 32]));
       }
       // every pixel already stopped in an earlier batch: nothing to blend
-      if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) continue;
+      if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
+        if (write_out) {
+          write_pixels(a, V, px, py, in0, in1, p0, p1);
+          if (lane == 0) atomicOr(&s_written, 1ull << t);
+        }
+        continue;
+      }
       if (lane == 0) atomicOr(&s_blended, 1ull << t);
       if (SAVE) {
         float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
@@ -235,7 +268,10 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 32ull;
-      if (chained) {
+      if (write_out) {
+        write_pixels(a, V, px, py, in0, in1, p0, p1);
+        if (lane == 0) atomicOr(&s_written, 1ull << t);
+      } else if (chained) {
         float4* st = a.tile_state + (size_t)gt * TILE_PX;
         st[lane] = pixel_state(p0);
         st[lane + 32] = pixel_state(p1);
@@ -244,6 +280,28 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         float4* out = a.partial + ((size_t)r * M + t) * TILE_PX;
         st_cs(out + lane, pixel_state(p0));
         st_cs(out + lane + 32, pixel_state(p1));
+      }
+    }
+    if (write_out) {
+      // the macro-tile's other tiles: their state after the last batch that
+      // blended them, or the background
+      __syncthreads();
+      const unsigned long long done = s_written;
+      for (int t = warp; t < M; t += RW) {
+        if ((done >> t) & 1ull) continue;
+        const int gtx = mtx0 + t % MW, gty = mty0 + t / MW;
+        if (gtx >= V.tiles_x || gty >= V.tiles_y) continue;
+        const int gt = V.tile_base + gty * V.tiles_x + gtx;
+        const int px = gtx * TILE + (lane & 7), py = gty * TILE + (lane >> 3);
+        const bool in0 = px < V.W && py < V.H, in1 = px < V.W && py + 4 < V.H;
+        PixelAcc p0, p1;
+        pixel_init(p0, in0);
+        pixel_init(p1, in1);
+        if (__ldcg(&a.tile_rank[gt]) != 0) {
+          pixel_load(p0, in0, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane]));
+          pixel_load(p1, in1, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane + 32]));
+        }
+        write_pixels(a, V, px, py, in0, in1, p0, p1);
       }
     }
     // publish: the tile states are visible before the chain advances
@@ -258,7 +316,9 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     if (tid == 0) {
       a.active[r] = chained ? s_blended : s_active;
       a.mode[r] = chained ? BATCH_CHAINED : BATCH_LOCAL;
-      if (chained)
+      if (write_out)
+        atomicOr(&a.chain[seg], CHAIN_DONE);
+      else if (chained)
         atomicCAS(&a.chain[seg], rank, rank + 1);
       else
         atomicOr(&a.chain[seg], CHAIN_BROKEN);
