@@ -274,9 +274,9 @@ def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
 # each stage's kernels on this workload, from one ncu capture of
 # `bench.py --case 5m8 --macro 4x4 --steps 1 --warmup 1` (summary under
 # profiles/), valid while the CUDA sources hash to `digest`.
-MEASURED_TRAFFIC = {"digest": "7ae894072a5bbd98",
-                    "bytes": {"project": 3161.4e6, "partition": 1401.7e6, "sort": 230.6e6, "raster": 3329.0e6,
-                              "merge": 220.5e6}}
+MEASURED_TRAFFIC = {"digest": "fb65a2ba4b616ef6",
+                    "bytes": {"project": 3161.4e6, "partition": 1273.2e6, "sort": 230.3e6, "raster": 3333.9e6,
+                              "merge": 0.0}}
 
 
 def sources_digest() -> str:
@@ -562,7 +562,7 @@ def gpu_arm(args):
             "pairs_per_step": int(statistics.mean(s["n_pairs"] for s in s0)),
             "batches_per_step": int(statistics.mean(s["n_batches"] for s in s0)),
             "max_segment": int(max(s["max_segment"] for s in s0)),
-            "segments_by_tier": s0[-1]["seg_by_tier"],
+            "segments_by_tier_last_pose": s0[-1]["seg_by_tier"],
             "replays_per_step": int(statistics.mean(s["n_replays"] for s in s0)),
             "raster_evals_per_step": int(statistics.mean(s["raster_evals"] for s in s0)),
             "visible_per_step": int(statistics.mean(s["n_visible"] for s in s0)),
