@@ -22,25 +22,25 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // Pixel state.  T is the live transmittance: it is 0 once the pixel has
 // stopped (and for pixels outside the image), so later gaussians add nothing;
-// Ts is the transmittance at the stop (0 while the pixel is live).  The final
-// transmittance is T + Ts (one of the two is 0).
+// U is the final transmittance: equal to T (bit for bit) while the pixel is
+// live, frozen at the transmittance of the stop afterwards.
 struct PixelAcc {
-  float r, g, b, T, Ts;
+  float r, g, b, T, U;
 };
 
 __device__ __forceinline__ void pixel_init(PixelAcc& p, bool inside, float t_in = 1.f) {
   p.r = p.g = p.b = 0.f;
   p.T = inside ? t_in : 0.f;
-  p.Ts = 0.f;
+  p.U = p.T;
 }
 
 __device__ __forceinline__ bool pixel_live(const PixelAcc& p) { return p.T > 0.f; }
-__device__ __forceinline__ float pixel_final_T(const PixelAcc& p) { return p.T + p.Ts; }
+__device__ __forceinline__ float pixel_final_T(const PixelAcc& p) { return p.U; }
 
 // Stored per-pixel state (per-tile chain state, partials, saved prefixes):
-// {r, g, b, w} with w = T while live and -Ts once stopped.
+// {r, g, b, w} with w = T while live and -U once stopped.
 __device__ __forceinline__ float4 pixel_state(const PixelAcc& p) {
-  return make_float4(p.r, p.g, p.b, p.T > 0.f ? p.T : -p.Ts);
+  return make_float4(p.r, p.g, p.b, p.T > 0.f ? p.T : -p.U);
 }
 __device__ __forceinline__ void pixel_load(PixelAcc& p, bool inside, const float4& s) {
   p.r = s.x;
@@ -48,43 +48,57 @@ __device__ __forceinline__ void pixel_load(PixelAcc& p, bool inside, const float
   p.b = s.z;
   const bool st = signbit(s.w);
   p.T = inside && !st ? s.w : 0.f;
-  p.Ts = st ? -s.w : 0.f;
+  p.U = st ? -s.w : p.T;
 }
 
 // Blend test and alpha of gaussian (g0 = {mx, my, l0', l1'}, g1 = {l2', o, ., .},
-// g2 = {r, g, b, E}) at pixel offset dy from its centre, ubase = l0' dx:
+// g2 = {r, g, b, E''}) at pixel offset dy from its centre, ubase = l0' dx:
 // e = (l0' dx + l1' dy)^2 + (l2' dy)^2 = q log2(e) / 2 and alpha =
 // min(0.99, o 2^-e).  The support q <= 9 and alpha >= 1/255 together are
-// e <= E with E = min(9 log2(e) / 2, log2(255 o)) (stored per gaussian).
+// e <= E with E = min(9 log2(e) / 2, log2(255 o)) per gaussian.  The record
+// stores E'' = E' 2^64 with E' the next float above max(E, 2^-40)
+// (blend_level), and the test is one saturated multiply-add, (E' - e) 2^64:
+// E' - E >= 2^-63, so it is >= 2 (1 after saturation) when e <= E and <= 0
+// when e >= E', and no float lies between E and E'.  (Only for E < 2^-40,
+// alpha within a factor 2^(2^-40) of 1/255, does it accept e up to 2^-40.)
 // Returns alpha, or 0 when the gaussian fails the test; raw = o 2^-e.
-// The test is the sign of E - e scaled by 2^64 and saturated (a multiply-add,
-// not a compare-select): exact whenever E and e differ by at least 2^-64.
 __device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g0, const float4& g1,
                                           const float4& g2, float& raw) {
   const float u = fmaf(g0.w, dy, ubase);
   const float w = g1.x * dy;
   const float e = fmaf(u, u, w * w);
   raw = g1.y * ex2_approx(-e);
-  const float f = __saturatef(fmaf(g2.w - e, 18446744073709551616.f, 1.f));
+  const float f = __saturatef(fmaf(e, -18446744073709551616.f, g2.w));
   return fminf(ALPHA_MAX, raw) * f;
 }
 
+// Per-gaussian level of the blend test as the record stores it (g2.w):
+// E'' = E' 2^64 with E = min(SUPPORT_E, log2(255 o)) and E' the next float
+// above max(E, 2^-40); a negative E (a gaussian that never passes) is stored
+// as E 2^64.  record_level recovers E' (exact: a power-of-two scale).
+__device__ __forceinline__ float blend_level(float o) {
+  const float E = fminf(SUPPORT_E, log2f(255.f * o));
+  const float Ep = E >= 0.f ? nextafterf(fmaxf(E, 9.094947017729282e-13f), INFINITY) : E;
+  return Ep * 18446744073709551616.f;
+}
+__device__ __forceinline__ float record_level(const float4& g2) { return g2.w * 5.421010862427522e-20f; }
+
 // Ordered update with the alpha from alpha_of: T' = T - alpha T; the pixel
-// stops before T' < 1e-4 (that gaussian excluded).  The stop test is the
-// sign of T' - 1e-4 scaled by 2^40 and saturated: exact, since two distinct
-// floats near 1e-4 differ by at least 2^-37.  Returns the gaussian's weight
-// alpha T (0 when it did not contribute).
+// stops before T' < 1e-4 (that gaussian excluded).  The stop test is one
+// saturated multiply-add, (T' - e') 2^40 with e' the float below 1e-4: two
+// distinct floats near 1e-4 differ by at least 2^-37, so it is >= 8 (1 after
+// saturation) exactly when T' >= 1e-4 and <= 0 otherwise.  U drops by the
+// weight, so it follows T' while the pixel goes on and keeps the stop's T.
+// Returns the gaussian's weight alpha T (0 when it did not contribute).
 __device__ __forceinline__ float apply_alpha(PixelAcc& p, float al, const float4& g2) {
   const float aT = al * p.T;
   const float tn = p.T - aT;
-  const float dt = tn - T_EPS;
-  const float s = __saturatef(fmaf(dt, 1099511627776.f, 1.f));  // 1: keeps going
-  const float ns = __saturatef(dt * -1099511627776.f);           // 1: stops (or stopped)
+  const float s = __saturatef(fmaf(tn, 1099511627776.f, -109951152.0f));  // 1: keeps going
   const float wt = aT * s;
   p.r = fmaf(g2.x, wt, p.r);
   p.g = fmaf(g2.y, wt, p.g);
   p.b = fmaf(g2.z, wt, p.b);
-  p.Ts = fmaf(ns, p.T, p.Ts);
+  p.U -= wt;
   p.T = tn * s;
   return wt;
 }
@@ -109,7 +123,7 @@ __device__ __forceinline__ void half_record(float4* r, float ox, float oy) {
   const float4 g0 = r[0], g1 = r[1], g2 = r[2];
   uint4* q = reinterpret_cast<uint4*>(r);
   q[0] = make_uint4(h2_bits(g0.y - oy), h2_bits(g0.w), h2_bits(g1.x), h2_bits(g1.y));
-  q[1] = make_uint4(h2_bits(g0.x - ox), h2_bits(g0.z), h2_bits(g2.w), 0u);
+  q[1] = make_uint4(h2_bits(g0.x - ox), h2_bits(g0.z), h2_bits(record_level(g2)), 0u);
 }
 
 // alpha of one gaussian at the two pixels a thread owns, in half2: hpx the
@@ -132,12 +146,10 @@ __device__ __forceinline__ float2 half_alpha2(const float4* r, __half2 hpx, __ha
   return __half22float2(__hmul2(a, f));
 }
 
-// Per-gaussian level E of the blend test (stored in the record's g2.w).
-__device__ __forceinline__ float blend_level(float o) { return fminf(SUPPORT_E, log2f(255.f * o)); }
 
 // Tile-mask geometry of one gaussian (Alg. 1 phase 1, the opacity-threshold
 // ellipse of Sec. 4.5).  The blend test passes only where
-// e = (l0' dx + l1' dy)^2 + (l2' dy)^2 <= E, E = g2.w the record's level.
+// e = (l0' dx + l1' dy)^2 + (l2' dy)^2 <= E, E the record's level.
 // Masks only need to be conservative, so this uses fast approximate
 // arithmetic (rsqrt, fast reciprocal) with margins far above its error: the
 // level is enlarged by 2^-10 relative + 2^-12, the y extent and the row spans
@@ -154,7 +166,7 @@ __device__ __forceinline__ float fast_sqrt0(float v) { return v > 0.f ? v * rsqr
 __device__ __forceinline__ MaskGauss mask_gauss(const float4& g0, const float4& g1, const float4& g2) {
   MaskGauss m;
   m.live = g2.w >= 0.f;
-  m.E = fmaf(g2.w, 1.f + 1.f / 1024.f, 1.f / 4096.f);
+  m.E = fmaf(record_level(g2), 1.f + 1.f / 1024.f, 1.f / 4096.f);
   m.l1 = g0.w;
   m.l2 = g1.x;
   m.ok = g0.z > 0.f && g1.x > 0.f;

@@ -33,7 +33,7 @@ __device__ __forceinline__ void apply_partial(PixelAcc& p, const float4& q, bool
       p.r += q.x;
       p.g += q.y;
       p.b += q.z;
-      p.Ts = tk;
+      p.U = tk;
       p.T = 0.f;
     } else {
       need = true;
@@ -44,6 +44,7 @@ __device__ __forceinline__ void apply_partial(PixelAcc& p, const float4& q, bool
   p.g = fmaf(p.T, q.y, p.g);
   p.b = fmaf(p.T, q.z, p.b);
   p.T *= tk;
+  p.U = p.T;
 }
 
 __device__ __forceinline__ float4 shfl4(const float4& v, int src) {
@@ -135,14 +136,14 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
         p0.g += q0r.g;
         p0.b += q0r.b;
         p0.T = q0r.T;
-        p0.Ts = q0r.Ts;
+        p0.U = q0r.U;
       }
       if (need1) {
         p1.r += q1r.r;
         p1.g += q1r.g;
         p1.b += q1r.b;
         p1.T = q1r.T;
-        p1.Ts = q1r.Ts;
+        p1.U = q1r.U;
       }
     }
     if (in0) {
