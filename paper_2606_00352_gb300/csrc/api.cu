@@ -252,6 +252,19 @@ hg_status state_create(hg_ctx* ctx, hg_state** out) {
   }
   memset(s->fc_host, 0, sizeof(FrameCounters));
   for (int i = 0; i < N_EVENTS; ++i) cudaEventCreate(&s->ev[i]);
+  {
+    SortStreams& ss = s->sort_streams;
+    bool ok = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 3; ++i) {
+      ok = ok && cudaStreamCreateWithFlags(&ss.aux[i], cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      hg_state_free(s);
+      return hg_cuda_status(cudaGetLastError(), "sort streams");
+    }
+    s->has_sort_streams = true;
+  }
   *out = s;
   return HG_OK;
 }
@@ -262,6 +275,14 @@ extern "C" void hg_state_free(hg_state* s) {
   cudaDeviceSynchronize();
   for (int i = 0; i < BUF_COUNT; ++i) ctx_free(s->ctx, s->bufs[i].p, s->bufs[i].bytes, nullptr);
   for (int i = 0; i < N_EVENTS; ++i) cudaEventDestroy(s->ev[i]);
+  {
+    SortStreams& ss = s->sort_streams;
+    if (ss.fork) cudaEventDestroy(ss.fork);
+    for (int i = 0; i < 3; ++i) {
+      if (ss.aux[i]) cudaStreamDestroy(ss.aux[i]);
+      if (ss.join[i]) cudaEventDestroy(ss.join[i]);
+    }
+  }
   cudaFreeHost(s->fc_host);
   cudaFreeHost(s->views_host);
   delete s;
@@ -532,7 +553,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     sa.cap_tiles = pa.cap_tiles;
     sa.cap_big_segs = pa.cap_big_segs;
     sa.fc = fc;
-    if (n > 0) HG_TRY(launch_sort(sa, st), "sort");
+    if (n > 0) HG_TRY(launch_sort(sa, st, s->has_sort_streams ? &s->sort_streams : nullptr), "sort");
     if (timing) HG_TRY(record_stage(s->ev[3], st), "stage event 3");
 
     HG_TRY(cudaMemsetAsync(s->bufs[B_CHAIN].p, 0, sizeof(uint32_t) * g.S, st), "memset chain");

@@ -53,6 +53,7 @@ struct FrameCounters {
   uint32_t raster_claim;
   uint32_t merge_claim;
   uint32_t os_claim[8];
+  uint32_t tier_claim[6];  // next list entry of each SMEM sort tier (dynamic claiming)
   uint32_t timeout_where;
   uint32_t pad0;
   unsigned long long replays;

@@ -67,6 +67,8 @@ struct hg_state {
   hg::FrameCounters* fc_host = nullptr;  // pinned
   hg::ViewDesc* views_host = nullptr;    // pinned, MAX_VIEWS entries
   cudaEvent_t ev[hg::N_EVENTS] = {};
+  hg::SortStreams sort_streams{};  // side streams of the sort tiers
+  bool has_sort_streams = false;
   cudaStream_t last_stream = nullptr;
   bool has_frame = false;
   hg::FrameGeom geom;

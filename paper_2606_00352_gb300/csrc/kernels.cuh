@@ -241,7 +241,16 @@ cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words,
                                      const ProjectArgs& out, cudaStream_t st);
 cudaError_t launch_partition(const PartitionArgs& a, cudaStream_t st);
-cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
+// Side streams of a frame's sort: the SMEM tiers sort disjoint segments, so
+// three of them run on their own streams (forked from and joined back into
+// the frame's stream with events, which stream capture turns into graph
+// branches) while the smallest tier and the onesweep run on the frame's.
+struct SortStreams {
+  cudaStream_t aux[3];
+  cudaEvent_t fork;
+  cudaEvent_t join[3];
+};
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t st, const SortStreams* ss);
 cudaError_t launch_raster(const RasterArgs& a, cudaStream_t st);
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
 cudaError_t launch_raster_backward(const BackwardArgs& a, cudaStream_t st);

@@ -114,17 +114,29 @@ __device__ __forceinline__ int radix_passes(uint32_t kmin, uint32_t kmax) {
   return span ? (32 - __clz(span) + 7) / 8 : 0;
 }
 
-// One CTA per segment (grid-stride over the tier's list): the segment is
-// loaded into shared memory, sorted there (sort_region) and written back.
+// Next entry of a tier's segment list for this CTA (dynamic claiming: the
+// segments differ in size, so CTAs take the next one when they are done).
+__device__ __forceinline__ uint32_t claim_segment(FrameCounters* fc, int tier, uint32_t* s_claim) {
+  if (threadIdx.x == 0) *s_claim = atomicAdd(&fc->tier_claim[tier], 1u);
+  __syncthreads();
+  return *s_claim;
+}
+
+// One CTA per segment (claimed from the tier's list): the segment is loaded
+// into shared memory, sorted there (sort_region) and written back.
 template <int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<NT, IPT>& s = *reinterpret_cast<BlockSortSmem<NT, IPT>*>(smem_raw);
+  __shared__ uint32_t s_claim;
   if (read_status(a.fc)) return;
   const uint32_t count = a.fc->tier_count[tier];
   const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
   const int tid = threadIdx.x;
-  for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+  // every thread reads the claim before the body's first barrier, and the
+  // next claim is written only after the barrier that ends the body
+  for (uint32_t idx = claim_segment(a.fc, tier, &s_claim); idx < count;
+       idx = claim_segment(a.fc, tier, &s_claim)) {
     const uint32_t seg = list[idx];
     const uint32_t start = a.seg_off[seg];
     const int n = (int)(a.seg_off[seg + 1] - start);
@@ -174,11 +186,13 @@ __global__ void __launch_bounds__(NT) k_block_merge_sort(SortArgs a, int tier) {
   constexpr int H = NT * IPT;  // one half's region
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MergeSortSmem<NT, IPT>& s = *reinterpret_cast<MergeSortSmem<NT, IPT>*>(smem_raw);
+  __shared__ uint32_t s_claim;
   if (read_status(a.fc)) return;
   const uint32_t count = a.fc->tier_count[tier];
   const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
   const int tid = threadIdx.x;
-  for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+  for (uint32_t idx = claim_segment(a.fc, tier, &s_claim); idx < count;
+       idx = claim_segment(a.fc, tier, &s_claim)) {
     const uint32_t seg = list[idx];
     const uint32_t start = a.seg_off[seg];
     const int n = (int)(a.seg_off[seg + 1] - start);
@@ -486,12 +500,15 @@ static cudaError_t launch_merge_tier(const SortArgs& a, int tier, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
+static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaStream_t s1, cudaStream_t s2,
+                                       cudaStream_t s3) {
   cudaError_t e;
+  // the largest tiers first, each on its own stream when s1..s3 differ from
+  // st: their tails overlap
+  if ((e = launch_merge_tier<512, 16>(a, 3, s3)) != cudaSuccess) return e;
+  if ((e = launch_tier<512, 16>(a, 2, 2, s2)) != cudaSuccess) return e;
+  if ((e = launch_tier<256, 16>(a, 1, 4, s1)) != cudaSuccess) return e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
-  if ((e = launch_tier<256, 16>(a, 1, 4, st)) != cudaSuccess) return e;
-  if ((e = launch_tier<512, 16>(a, 2, 2, st)) != cudaSuccess) return e;
-  if ((e = launch_merge_tier<512, 16>(a, 3, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   bool alt = false;
   e = launch_onesweep<uint32_t, 4>(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist,
@@ -501,6 +518,24 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
   k_os_fixup<<<num_sms() * 4, 256, 0, st>>>(tv, a.keys, a.vals, a.fc);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t st, const SortStreams* ss) {
+  if (!ss) return launch_sort_kernels(a, st, st, st, st);
+  cudaError_t e = cudaEventRecord(ss->fork, st);
+  if (e != cudaSuccess) return e;
+  int forked = 0;
+  for (; forked < 3; ++forked)
+    if ((e = cudaStreamWaitEvent(ss->aux[forked], ss->fork, 0)) != cudaSuccess) break;
+  if (e == cudaSuccess) e = launch_sort_kernels(a, st, ss->aux[2], ss->aux[1], ss->aux[0]);
+  // join every forked stream back, also after an error (an open fork would
+  // leave a stream capture unjoined)
+  for (int i = 0; i < forked; ++i) {
+    cudaError_t j = cudaEventRecord(ss->join[i], ss->aux[i]);
+    if (j == cudaSuccess) j = cudaStreamWaitEvent(st, ss->join[i], 0);
+    if (e == cudaSuccess) e = j;
+  }
+  return e;
 }
 
 // ------------------------------------------------------------------------
