@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   __shared__ uint32_t s_unit, s_qn, s_qhead, s_mode;
   __shared__ uint8_t s_q[64];
   __shared__ unsigned long long s_active, s_blended, s_written;
+  __shared__ uint32_t s_cnt[64];  // (gaussian, half) entries per tile of the unit
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       s_blended = 0;
       s_written = 0;
     }
+    if (tid < M) s_cnt[tid] = 0;
     __syncthreads();
     const uint32_t u = s_unit;
     if (u >= n_units) break;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 
     // phase 1: per-gaussian tile masks, transposed to per-tile masks
     const int K = (int)((count + 31) / 32);
-    build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, RW);
+    build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, RW, s_cnt);
     if (HALF) {
       // each thread rewrites the records of the gaussians it built masks for
       // (no other thread reads them before the barrier below) as half2 pairs
@@ -143,9 +145,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int t = h * 32 + lane;
-        uint32_t n = 0;
-        if (t < M)
-          for (int k = 0; k < K; ++k) n += __popc(s_top[k * M + t]) + __popc(s_bot[k * M + t]);
+        const uint32_t n = t < M ? s_cnt[t] : 0u;
         // key: count above, tile index below (distinct keys, ties by index)
         key[h] = n ? ((n << 6) | (uint32_t)(63 - t)) : 0u;
         act |= (unsigned long long)__ballot_sync(0xffffffffu, n != 0) << (h * 32);

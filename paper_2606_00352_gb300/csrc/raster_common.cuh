@@ -28,15 +28,19 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 
 // Phase 1 of a processing unit: every warp takes mini-batches of 32 staged
 // gaussians, computes each gaussian's render-tile masks inside the macro-tile
-// for the top (rows 0-3) and bottom (rows 4-7) half of every tile (3-sigma
-// rectangle refined by the ellipse of the blend test per half-tile row band)
-// and transposes the 32 x M bit matrices, so that s_top[k * M + t] and
+// for the top (rows 0-3) and bottom (rows 4-7) half of every tile and
+// transposes the 32 x M bit matrices, so that s_top[k * M + t] and
 // s_bot[k * M + t] hold, for tile t, the bits of the mini-batch-k gaussians
-// that can pass the blend test in its top / bottom half.
+// that can pass the blend test in its top / bottom half.  Per tile row the
+// 3-sigma rectangle is refined by the x span of the blend-test ellipse over
+// the row's 8 pixel rows; a half keeps those columns when its 4 pixel rows
+// meet the ellipse's y extent.  With s_cnt, lane t also adds the number of
+// (gaussian, half) entries of tile t to s_cnt[t] (the tile's work, for the
+// queue order).
 template <int MW, int MH>
 __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* s_top, uint32_t* s_bot,
                                                  uint32_t count, const ViewDesc& V, int mtx0, int mty0,
-                                                 int n_warps) {
+                                                 int n_warps, uint32_t* s_cnt = nullptr) {
   constexpr int M = MW * MH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int K = (int)((count + 31) / 32);
@@ -61,20 +65,15 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
             continue;
           }
           const float ya = (float)((mty0 + y) * TILE);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float xl, xr;
-            const float yh = ya + (float)(h * (TILE / 2));
-            if (!mask_row_span(mg, g0.x, g0.y, yh, yh + (float)(TILE / 2 - 1), xl, xr)) continue;
-            const int c0 = max(x0, floordiv((int)ceilf(xl), TILE) - mtx0);
-            const int c1 = min(x1, floordiv((int)floorf(xr), TILE) - mtx0);
-            if (c0 > c1) continue;
-            const unsigned long long bits = (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
-            if (h == 0)
-              gt |= bits;
-            else
-              gb |= bits;
-          }
+          float xl, xr;
+          if (!mask_row_span(mg, g0.x, g0.y, ya, ya + (float)(TILE - 1), xl, xr)) continue;
+          const int c0 = max(x0, floordiv((int)ceilf(xl), TILE) - mtx0);
+          const int c1 = min(x1, floordiv((int)floorf(xr), TILE) - mtx0);
+          if (c0 > c1) continue;
+          const unsigned long long bits = (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
+          const float ry = ya - g0.y;  // offset of the tile's first pixel row
+          if (ry <= mg.hyw && ry + (float)(TILE / 2 - 1) >= -mg.hyw) gt |= bits;
+          if (ry + (float)(TILE / 2) <= mg.hyw && ry + (float)(TILE - 1) >= -mg.hyw) gb |= bits;
         }
       }
     }
@@ -83,11 +82,13 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
     if (lane < M) {
       s_top[k * M + lane] = tlo;
       s_bot[k * M + lane] = blo;
+      if (s_cnt) atomicAdd(&s_cnt[lane], (uint32_t)(__popc(tlo) + __popc(blo)));
     }
     if (M > 32) {
       const uint32_t thi = transpose32((uint32_t)(gt >> 32), lane), bhi = transpose32((uint32_t)(gb >> 32), lane);
       s_top[k * M + 32 + lane] = thi;
       s_bot[k * M + 32 + lane] = bhi;
+      if (s_cnt) atomicAdd(&s_cnt[32 + lane], (uint32_t)(__popc(thi) + __popc(bhi)));
     }
   }
 }
