@@ -7,8 +7,8 @@
 //   bin  uint4  plain path: {mx bits, my bits, radius, depth key}; HiGS: the
 //               binning record of the macro cells (binning.cuh), with the
 //               depth key in dkeys
-//   rec  float4 x4 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, E} {0}
-//        (E: the per-gaussian level of the blend test)
+//   rec  float4 x4 {mx, my, l0', l1'} {l2', o, radius bits, key bits} {r, g, b, E''} {0}
+//        (E'': the per-gaussian level of the blend test, blend_level)
 //   vis  one bit per gaussian, written per warp (Sec. 4.2 visibility bitfield)
 // bin and rec are written for visible entries only.
 // l' are the Cholesky factors of the conic prescaled by sqrt(log2(e)/2), so the
