@@ -218,10 +218,10 @@ __device__ __forceinline__ bool mask_row_span(const MaskGauss& m, float mx, floa
 __device__ __forceinline__ void tile_rect(const float4& g0, const float4& g1, int& x0, int& x1, int& y0, int& y1) {
   const int rad = __float_as_int(g1.z);
   const int px = (int)floorf(g0.x), py = (int)floorf(g0.y);
-  x0 = floordiv(px - rad, TILE);
-  x1 = floordiv(px + rad, TILE);
-  y0 = floordiv(py - rad, TILE);
-  y1 = floordiv(py + rad, TILE);
+  x0 = (px - rad) >> TILE_SHIFT;
+  x1 = (px + rad) >> TILE_SHIFT;
+  y0 = (py - rad) >> TILE_SHIFT;
+  y1 = (py + rad) >> TILE_SHIFT;
 }
 
 }  // namespace hg

@@ -9,6 +9,7 @@
 namespace hg {
 
 constexpr int TILE = 8;            // render tile edge in pixels (Sec. 3.1)
+constexpr int TILE_SHIFT = 3;      // floor(a / TILE) = a >> TILE_SHIFT (arithmetic shift)
 constexpr int TILE_PX = TILE * TILE;
 constexpr int BP = 8192;           // partitioning batch B_p (Sec. 3.2)
 constexpr float T_EPS = 1e-4f;     // termination threshold

@@ -17,10 +17,10 @@ __device__ __forceinline__ int tile_span(const uint4& r, const ViewDesc& V, int&
   const int rad = (int)r.z;
   if (rad <= 0) return 0;
   const int px = (int)floorf(__uint_as_float(r.x)), py = (int)floorf(__uint_as_float(r.y));
-  x0 = max(floordiv(px - rad, TILE), 0);
-  x1 = min(floordiv(px + rad, TILE), V.tiles_x - 1);
-  y0 = max(floordiv(py - rad, TILE), 0);
-  y1 = min(floordiv(py + rad, TILE), V.tiles_y - 1);
+  x0 = max((px - rad) >> TILE_SHIFT, 0);
+  x1 = min((px + rad) >> TILE_SHIFT, V.tiles_x - 1);
+  y0 = max((py - rad) >> TILE_SHIFT, 0);
+  y1 = min((py + rad) >> TILE_SHIFT, V.tiles_y - 1);
   if (x0 > x1 || y0 > y1) return 0;
   return (x1 - x0 + 1) * (y1 - y0 + 1);
 }

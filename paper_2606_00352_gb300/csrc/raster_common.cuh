@@ -67,8 +67,8 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
           const float ya = (float)((mty0 + y) * TILE);
           float xl, xr;
           if (!mask_row_span(mg, g0.x, g0.y, ya, ya + (float)(TILE - 1), xl, xr)) continue;
-          const int c0 = max(x0, floordiv((int)ceilf(xl), TILE) - mtx0);
-          const int c1 = min(x1, floordiv((int)floorf(xr), TILE) - mtx0);
+          const int c0 = max(x0, ((int)ceilf(xl) >> TILE_SHIFT) - mtx0);
+          const int c1 = min(x1, ((int)floorf(xr) >> TILE_SHIFT) - mtx0);
           if (c0 > c1) continue;
           const unsigned long long bits = (((1ull << (c1 - c0 + 1)) - 1ull) << c0) << (y * MW);
           const float ry = ya - g0.y;  // offset of the tile's first pixel row
