@@ -271,11 +271,11 @@ def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# each stage's kernels on this workload, from one ncu capture of
-# `bench.py --case 5m8 --macro 4x4 --steps 1 --warmup 1` (summary under
-# profiles/), valid while the CUDA sources hash to `digest`.
-MEASURED_TRAFFIC = {"digest": "fb65a2ba4b616ef6",
-                    "bytes": {"project": 3161.4e6, "partition": 1273.2e6, "sort": 230.3e6, "raster": 3333.9e6,
+# each stage's kernels on this workload (spatially ordered scene), from one
+# ncu capture of `bench.py --case 5m8 --macro 4x4 --steps 1 --warmup 1`
+# (summary under profiles/), valid while the CUDA sources hash to `digest`.
+MEASURED_TRAFFIC = {"digest": "fe28363921fa61bf",
+                    "bytes": {"project": 2928.1e6, "partition": 911.5e6, "sort": 236.0e6, "raster": 2202.8e6,
                               "merge": 0.0}}
 
 
@@ -350,10 +350,19 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     sids = [srv.add_scene(g) for g in gscenes]
     pool = [torch.empty(3840 * 2160 * 3, device="cuda") for _ in range(48)]
     poses = {r: scenes.scene_orbit(N_POSES, r[0], r[1]) for r in SERVE_RES}
-    # warm the slots' workspaces at every resolution
+    # warm the slots' workspaces at every resolution, then with bursts of the
+    # largest batch (max_views_per_launch views at the largest resolution of
+    # one scene, submitted together so that they share launches), so that no
+    # slot grows its workspace inside the timed rates
     warm = [srv.submit(sids[k % len(sids)], poses[SERVE_RES[k % 3]][k], pool[k]) for k in range(12)]
     for rid in warm:
         srv.wait(rid)
+    big = max(SERVE_RES, key=lambda r: r[0] * r[1])
+    for _ in range(2):
+        for sid in sids:
+            burst = [srv.submit(sid, poses[big][k], pool[k]) for k in range(32)]
+            for rid in burst:
+                srv.wait(rid)
     rows = []
     for rate in SERVE_RATES:
         srv.reset_stats()
@@ -386,11 +395,13 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     return rows
 
 
-def train_step_ms(higs, ctx, steps=10):
+def train_step_ms(higs, ctx, steps=10, spatial=True):
     """Densification-free optimisation steps on the 1M-gaussian scene, 4
     views at 1080p, against the render of a perturbed copy (means + N(0,
     1e-3), opacity logits + N(0, 0.1)): forward (saving what the backward
-    needs), L2 loss, backward, Adam, each timed with CUDA events."""
+    needs), L2 loss, backward, Adam, each timed with CUDA events.  With
+    `spatial` the parameter tensors are permuted once into hg_spatial_order
+    before training (the optimiser state follows the same order)."""
     import torch
     from paper_2606_00352_gb300 import scenes
     scene = scenes.scene_1m()
@@ -401,6 +412,9 @@ def train_step_ms(higs, ctx, steps=10):
     dev = torch.device("cuda", ctx.device)
     params = [torch.as_tensor(x, device=dev).contiguous()
               for x in (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh)]
+    if spatial:
+        perm = higs.spatial_order(ctx, params[0]).long()
+        params = [p[perm].contiguous() for p in params]
     tr = higs.Trainer(ctx, params, scene.sh_degree, cams, target)
     stream = torch.cuda.current_stream()
     times, losses = [], []
@@ -426,7 +440,7 @@ def train_step_ms(higs, ctx, steps=10):
             "step_ms": round(sum(med), 3), "loss_first": round(losses[0], 3), "loss_last": round(losses[-1], 3),
             "workload": "1M-gaussian SH-3 scene (64 clusters, Zipf 1.2), 4 views at 1920x1080, target = render "
                         "of a perturbed copy; forward with saved prefixes + hg_l2_loss + hg_render_backward + "
-                        "hg_adam_step (3DGS learning rates)"}
+                        "hg_adam_step (3DGS learning rates)" + ("; parameters in hg_spatial_order" if spatial else "")}
 
 
 def gpu_arm(args):
@@ -438,7 +452,8 @@ def gpu_arm(args):
     scene = scenes.scene_5m8()
     cams = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)
     ctx = higs.Context(torch.cuda.current_device())
-    gs = higs.GpuScene.from_scene(ctx, scene)
+    order = higs.ORDER_SPATIAL if args.order == "spatial" else higs.ORDER_INPUT
+    gs = higs.GpuScene.from_scene(ctx, scene, order=order)
     scene16 = scene if not args.skip_plain else None
     del scene
     stream = torch.cuda.Stream()
@@ -475,7 +490,7 @@ def gpu_arm(args):
         ref_img, _ = higs.render(gs, pose_batch(cams, 0, rank), opts, with_T=False, stream=stream)
         ref_img = ref_img.clone()
         for name, code in (("sh_f16", higs.SH_F16), ("sh_codec32", higs.SH_CODEC32)):
-            gsv = higs.GpuScene.from_scene(ctx, scene16, sh_storage=code)
+            gsv = higs.GpuScene.from_scene(ctx, scene16, sh_storage=code, order=order)
             hsteps = max(3, min(args.steps, 10))
             hms, hstats, _ = time_graph(higs, gsv, cams, opts, hsteps, min(args.warmup, 3), rank, world, stream)
             hvalue, hms = job_throughput(hms, hsteps * VIEWS, world)
@@ -514,7 +529,7 @@ def gpu_arm(args):
         from paper_2606_00352_gb300 import scenes as sc_mod
         small = [higs.GpuScene.from_scene(ctx, sc_mod.cluster_scene(n, 256, 1.4, seed=11 + k,
                                                                     sigma_range=sc_mod.CLUSTER_SIGMA,
-                                                                    extent=sc_mod.EXTENT))
+                                                                    extent=sc_mod.EXTENT), order=order)
                  for k, n in enumerate((500_000, 2_000_000))]
         sopts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
                              batch_cap=opts.batch_cap, bin_test=opts.bin_test)
@@ -525,7 +540,7 @@ def gpu_arm(args):
         del small
     training = None
     if not args.skip_train and world == 1:
-        training = train_step_ms(higs, ctx)
+        training = train_step_ms(higs, ctx, spatial=args.order == "spatial")
 
     e2e_opts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
                             batch_cap=opts.batch_cap, bin_test=opts.bin_test)
@@ -547,7 +562,7 @@ def gpu_arm(args):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config() | {"macro_tile": f"{opts.macro_w}x{opts.macro_h}", "batch_cap": opts.batch_cap,
-                                       "bin_test": args.bin},
+                                       "bin_test": args.bin, "scene_order": args.order},
         "roofline": {k: v for k, v in rl[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
         | {"kernel": top, "traffic": rl[top]["traffic"], "peak_source": pk["source"]},
         "stages": rl | {"merge": {"ms": round(stage_ms["merge"], 4)}},
@@ -586,7 +601,7 @@ def profile_case(args):
     scene = scenes.scene_5m8() if args.case == "5m8" else scenes.scene_1m()
     cams = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)
     ctx = higs.Context(0)
-    gs = higs.GpuScene.from_scene(ctx, scene)
+    gs = higs.GpuScene.from_scene(ctx, scene, order=higs.ORDER_SPATIAL if args.order == "spatial" else higs.ORDER_INPUT)
     st = higs.State(ctx)
     path = higs.PATH_PLAIN if args.case == "1m-plain" else higs.PATH_HIGS
     mw, mh = (int(x) for x in args.macro.split("x"))
@@ -634,6 +649,8 @@ def main():
     ap.add_argument("--macro", default="8x4", choices=["4x4", "8x4", "8x8"], help="macro shape without autotuning")
     ap.add_argument("--cap", type=int, default=1024, help="batch cap B_r without autotuning")
     ap.add_argument("--bin", default="ellipse", choices=["rect", "ellipse"], help="macro-tile binning test")
+    ap.add_argument("--order", default="spatial", choices=["input", "spatial"],
+                    help="scene storage order (hg_create_scene HG_ORDER_*)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.oracle_steps and not args.case:
         args.warmup = 3

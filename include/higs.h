@@ -72,7 +72,12 @@ typedef struct {
  *   opacity_logits [n], sh [n][(sh_degree+1)^2][3] (coefficient k = l*l+l+m).
  * borrow = 0: the library copies the arrays into memory it owns.
  * borrow = 1: the library keeps the pointers; the caller keeps them alive
- * and unchanged while the scene exists. */
+ * and unchanged while the scene exists.
+ * order: HG_ORDER_INPUT keeps the caller's gaussian order; HG_ORDER_SPATIAL
+ * (borrow = 0 only) stores the gaussians in hg_spatial_order, so gaussians
+ * that are near in space are near in memory and the projection's writes and
+ * the partition's pair writes of one screen region are close together; the
+ * image is that of the reordered set (hg_scene_order gives the order). */
 typedef struct {
   int64_t n;
   int32_t sh_degree; /* 0..3 */
@@ -82,16 +87,18 @@ typedef struct {
   const float* quats;
   const float* opacity_logits;
   const void* sh;     /* [n][(deg+1)^2][3] of the element type sh_storage */
-  int32_t sh_storage; /* HG_SH_F32, HG_SH_F16 or HG_SH_BF16 */
-  int32_t pad;
+  int32_t sh_storage; /* HG_SH_F32, HG_SH_F16, HG_SH_BF16 or HG_SH_CODEC32 */
+  int32_t order;      /* HG_ORDER_INPUT or HG_ORDER_SPATIAL */
 } hg_scene_desc;
+
+enum { HG_ORDER_INPUT = 0, HG_ORDER_SPATIAL = 1 };
 
 /* Storage type of the SH coefficients (the projection computes in float32
  * either way; half storage halves the bytes the projection reads per
  * gaussian at degree 3, 236 -> 140).  HG_SH_CODEC32 is the 32-byte packed
- * representation of Sec. 4.2 (degree 3 only; YCoCg-R, square-root gamma,
- * 10/8/8 bits for the DC basis and 6/4/4 for the others, per-channel
- * 99.5th-percentile scales): `sh` then points to float32 coefficients in
+ * representation of Sec. 4.2 (degree 3 only; YCoCg-R; the DC basis as a
+ * float16 luma and 13-bit linear chroma, the others square-root gamma with
+ * 6/4/4 bits; per-channel 99.5th-percentile scales): `sh` then points to float32 coefficients in
  * device memory, which hg_create_scene encodes (the scene always owns the
  * codes; 236 -> 76 bytes per gaussian).  Scenes with half or packed SH
  * render and serve; hg_render_backward and hg_adam_step need float32 SH. */
@@ -102,6 +109,29 @@ enum { HG_SH_F32 = 0, HG_SH_F16 = 1, HG_SH_BF16 = 2, HG_SH_CODEC32 = 3 };
  * n * 8 uint32 code words.  Synchronous.
  * Errors: HG_ERR_INVALID_ARG (not a packed-SH scene), HG_ERR_CUDA. */
 hg_status hg_scene_sh_codec(const hg_scene* scene, float* scales_host, uint32_t* codes_host);
+
+/* Spatial storage order of n gaussians (not part of the paper's method: a
+ * memory layout for the front end's bandwidth, Sec. 4.2-4.3).  perm[i] is
+ * the index of the i-th gaussian in ascending 30-bit Morton code of its
+ * mean, ties by index.  The code quantises each axis a over the bounding
+ * box [lo_a, hi_a] of the finite coordinates: q_a = min(1023,
+ * floor((x_a - lo_a) * s_a)) with s_a = 1024 / (hi_a - lo_a) (1 when
+ * hi_a = lo_a), every operation float32 round-to-nearest, a non-finite
+ * coordinate counting as lo_a; bit 3 b + a of the code is bit b of q_a
+ * (a = 0, 1, 2 for x, y, z).
+ *   means  device float32 [n][3]
+ *   perm   device int32 [n], written
+ * Stream-ordered on `stream`; scratch (24 n bytes and the sort's tile
+ * buffers) comes from the context's allocator and is released before the
+ * call returns, which synchronises the stream.
+ * Errors: HG_ERR_INVALID_ARG (n < 0, n > 2^30, null pointers), HG_ERR_OOM,
+ * HG_ERR_CUDA. */
+hg_status hg_spatial_order(hg_ctx* ctx, const float* means, int64_t n, int32_t* perm, void* stream);
+
+/* Storage order of a scene: perm_host[i] = the caller's index of the
+ * scene's i-th gaussian (the identity for HG_ORDER_INPUT).  Synchronous.
+ * Errors: HG_ERR_INVALID_ARG, HG_ERR_CUDA. */
+hg_status hg_scene_order(const hg_scene* scene, int32_t* perm_host);
 
 /* Pinhole camera: world->camera 4x4 row-major (x right, y down, z forward),
  * focal lengths and principal point in pixels; pixel (i, j) has its centre

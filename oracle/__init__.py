@@ -24,6 +24,8 @@ float32 scene parameters:
   * ``grad``      - analytic FP64 gradient of 0.5*||C - C_target||^2.
   * ``train``     - the L2 loss and the Adam step of the differentiable path.
   * ``sh_codec``  - the 32-byte packed SH representation (Sec. 4.2).
+  * ``order``     - the spatial (Morton) storage order of a scene (a memory
+                    layout outside the paper's method).
 
 Every function names the passage it follows; readings of silent or
 ambiguous passages are listed in the repository's design notes.

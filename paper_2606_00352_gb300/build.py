@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhigs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "project.cu", "partition.cu", "sort.cu", "raster.cu", "merge.cu", "plain.cu",
-           "backward.cu", "graph.cu", "tune.cu", "serve.cu", "train.cu", "sh_codec.cu"]
+           "backward.cu", "graph.cu", "tune.cu", "serve.cu", "train.cu", "sh_codec.cu", "order.cu"]
 
 
 def nvcc() -> str:

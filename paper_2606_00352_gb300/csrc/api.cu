@@ -151,7 +151,8 @@ extern "C" void hg_ctx_destroy(hg_ctx* ctx) {
 // ---------------------------------------------------------------- scenes
 extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_scene** out) {
   if (!ctx || !d || !out || d->n < 0 || d->sh_degree < 0 || d->sh_degree > 3 || d->sh_storage < HG_SH_F32 ||
-      d->sh_storage > HG_SH_CODEC32 || (d->sh_storage == HG_SH_CODEC32 && d->sh_degree != 3)) {
+      d->sh_storage > HG_SH_CODEC32 || (d->sh_storage == HG_SH_CODEC32 && d->sh_degree != 3) ||
+      (d->order != HG_ORDER_INPUT && d->order != HG_ORDER_SPATIAL) || (d->order == HG_ORDER_SPATIAL && d->borrow)) {
     hg_set_error("hg_create_scene: bad arguments");
     return HG_ERR_INVALID_ARG;
   }
@@ -214,6 +215,38 @@ extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_sce
       s->arr[i] = (float*)const_cast<void*>(src[i]);
     }
   }
+  if (d->order == HG_ORDER_SPATIAL && d->n > 0) {
+    // store the gaussians in spatial order: permutation, then each array
+    // gathered into a new buffer that replaces the copy
+    s->perm = (int32_t*)ctx_alloc(ctx, sizeof(int32_t) * (size_t)d->n, nullptr);
+    if (!s->perm) {
+      hg_destroy_scene(s);
+      hg_set_error("hg_create_scene: allocation failed");
+      return HG_ERR_OOM;
+    }
+    hg_status r = spatial_order(ctx, s->arr[0], d->n, s->perm, nullptr);
+    for (int i = 0; i < 5 && r == HG_OK; ++i) {
+      void* dst = ctx_alloc(ctx, s->bytes[i], nullptr);
+      if (!dst) {
+        r = HG_ERR_OOM;
+        hg_set_error("hg_create_scene: allocation failed");
+        break;
+      }
+      cudaError_t e = gather_rows(s->arr[i], dst, s->perm, d->n, s->bytes[i] / (size_t)d->n, nullptr);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) {
+        ctx_free(ctx, dst, s->bytes[i], nullptr);
+        r = hg_cuda_status(e, "hg_create_scene reorder");
+        break;
+      }
+      ctx_free(ctx, s->arr[i], s->bytes[i], nullptr);
+      s->arr[i] = (float*)dst;
+    }
+    if (r != HG_OK) {
+      hg_destroy_scene(s);
+      return r;
+    }
+  }
   *out = s;
   return HG_OK;
 }
@@ -223,7 +256,22 @@ extern "C" void hg_destroy_scene(hg_scene* s) {
   if (s->owned)
     for (int i = 0; i < 5; ++i) ctx_free(s->ctx, s->arr[i], s->bytes[i], nullptr);
   if (s->sh_scale) ctx_free(s->ctx, s->sh_scale, sizeof(float) * 2 * SH_CODEC_CH, nullptr);
+  if (s->perm) ctx_free(s->ctx, s->perm, sizeof(int32_t) * (size_t)s->n, nullptr);
   delete s;
+}
+
+extern "C" hg_status hg_scene_order(const hg_scene* s, int32_t* perm_host) {
+  if (!s || (s->n > 0 && !perm_host)) {
+    hg_set_error("hg_scene_order: bad arguments");
+    return HG_ERR_INVALID_ARG;
+  }
+  if (!s->perm) {
+    for (int64_t i = 0; i < s->n; ++i) perm_host[i] = (int32_t)i;
+    return HG_OK;
+  }
+  cudaSetDevice(s->ctx->device);
+  const cudaError_t e = cudaMemcpy(perm_host, s->perm, sizeof(int32_t) * (size_t)s->n, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? HG_OK : hg_cuda_status(e, "hg_scene_order");
 }
 
 extern "C" hg_status hg_scene_sh_codec(const hg_scene* s, float* scales_host, uint32_t* codes_host) {

@@ -24,6 +24,7 @@ struct hg_scene {
   float* sh_scale = nullptr;   // packed SH: device [2][48] (s, s / Q^2)
   float* arr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // means, log_scales, quats, logits, sh
   size_t bytes[5] = {0, 0, 0, 0, 0};
+  int32_t* perm = nullptr;  // HG_ORDER_SPATIAL: device [n], caller's index of each stored gaussian
 };
 
 namespace hg {
@@ -88,6 +89,12 @@ void ctx_free(hg_ctx* ctx, void* p, size_t bytes, cudaStream_t st);
 constexpr int LOSS_BLOCKS = 304;
 constexpr size_t LOSS_SCRATCH_BYTES = sizeof(double) * LOSS_BLOCKS + 256;
 hg_status ws_ensure(hg_state* s, int id, size_t bytes, cudaStream_t st);
+namespace hg {
+// hg_spatial_order on a stream (synchronises it); gather of scene rows by a permutation
+hg_status spatial_order(hg_ctx* ctx, const float* means, long long n, int32_t* perm, cudaStream_t st);
+cudaError_t gather_rows(const void* src, void* dst, const int32_t* perm, long long n, size_t row_bytes,
+                        cudaStream_t st);
+}  // namespace hg
 hg_status state_create(hg_ctx* ctx, hg_state** out);
 hg_status build_views(hg_state* s, const hg_camera* cams, int V, const hg_render_opts* o, hg::FrameGeom& g);
 hg_status enqueue_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg::FrameGeom& g,

@@ -488,6 +488,9 @@ template cudaError_t launch_onesweep<unsigned long long, 8>(const OsTileView&, u
                                                             unsigned long long*, uint32_t*, uint32_t*, size_t,
                                                             uint32_t*, size_t, uint32_t*, int, int,
                                                             FrameCounters*, cudaStream_t, bool*);
+template cudaError_t launch_onesweep<uint32_t, 4>(const OsTileView&, uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                                                  uint32_t*, size_t, uint32_t*, size_t, uint32_t*, int, int,
+                                                  FrameCounters*, cudaStream_t, bool*);
 
 template <int NT, int IPT>
 static cudaError_t launch_merge_tier(const SortArgs& a, int tier, cudaStream_t st) {

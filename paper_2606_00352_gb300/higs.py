@@ -31,7 +31,7 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward", "hg_autotune",
            "hg_serve_create", "hg_serve_add_scene", "hg_serve_submit", "hg_serve_poll", "hg_serve_wait",
            "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats", "hg_serve_destroy", "hg_l2_loss",
-           "hg_adam_step", "hg_scene_sh_codec"]
+           "hg_adam_step", "hg_scene_sh_codec", "hg_spatial_order", "hg_scene_order"]
 
 
 class AdamOpts(C.Structure):
@@ -49,10 +49,11 @@ class SceneDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("borrow", C.c_int32),
                 ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("sh_storage", C.c_int32),
-                ("pad", C.c_int32)]
+                ("order", C.c_int32)]
 
 
 SH_F32, SH_F16, SH_BF16, SH_CODEC32 = 0, 1, 2, 3
+ORDER_INPUT, ORDER_SPATIAL = 0, 1
 
 
 class CameraC(C.Structure):
@@ -156,6 +157,10 @@ def load(path: str = LIB_PATH):
     lib.hg_render_backward.argtypes = [C.c_void_p] + [C.c_void_p] * 7
     lib.hg_scene_sh_codec.restype = C.c_int
     lib.hg_scene_sh_codec.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hg_spatial_order.restype = C.c_int
+    lib.hg_spatial_order.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    lib.hg_scene_order.restype = C.c_int
+    lib.hg_scene_order.argtypes = [C.c_void_p, C.c_void_p]
     lib.hg_l2_loss.restype = C.c_int
     lib.hg_l2_loss.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hg_adam_step.restype = C.c_int
@@ -258,10 +263,12 @@ class GpuScene:
     """Device-resident scene (hg_create_scene).  Arrays are torch CUDA tensors
     (float32, contiguous; SH in the storage type sh_storage, converted with
     round-to-nearest-even when given in another type); borrow=True keeps
-    references instead of copying."""
+    references instead of copying.  order=ORDER_SPATIAL stores the gaussians
+    in hg_spatial_order (owned copies only); order() returns the stored
+    order as the caller's indices."""
 
     def __init__(self, ctx: Context, means, log_scales, quats, opacity_logits, sh, sh_degree: int,
-                 borrow: bool = False, sh_storage: int = SH_F32):
+                 borrow: bool = False, sh_storage: int = SH_F32, order: int = ORDER_INPUT):
         import torch
         dev = torch.device("cuda", ctx.device)
 
@@ -274,7 +281,7 @@ class GpuScene:
                 SH_CODEC32: torch.float32}[sh_storage]
         self.tensors = [t(means), t(log_scales), t(quats), t(opacity_logits), t(sh, sh_t)]
         n = self.tensors[0].shape[0]
-        d = SceneDesc(n, sh_degree, int(borrow), *[x.data_ptr() for x in self.tensors], sh_storage, 0)
+        d = SceneDesc(n, sh_degree, int(borrow), *[x.data_ptr() for x in self.tensors], sh_storage, order)
         h = C.c_void_p()
         torch.cuda.synchronize(dev)
         check(ctx.lib.hg_create_scene(ctx.h, C.byref(d), C.byref(h)))
@@ -291,10 +298,18 @@ class GpuScene:
                                              codes.ctypes.data_as(C.c_void_p)))
         return scales, codes
 
+    def order(self):
+        """Stored order (hg_scene_order): int32 [n], the caller's index of
+        each stored gaussian."""
+        perm = np.zeros(self.n, np.int32)
+        check(self.ctx.lib.hg_scene_order(self.h, perm.ctypes.data_as(C.c_void_p)))
+        return perm
+
     @classmethod
-    def from_scene(cls, ctx: Context, scene, borrow: bool = False, sh_storage: int = SH_F32):
+    def from_scene(cls, ctx: Context, scene, borrow: bool = False, sh_storage: int = SH_F32,
+                   order: int = ORDER_INPUT):
         return cls(ctx, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
-                   scene.sh_degree, borrow, sh_storage)
+                   scene.sh_degree, borrow, sh_storage, order)
 
     def close(self):
         if self.h:
@@ -417,6 +432,18 @@ def render_backward(state: State, scene: GpuScene, dl_drgb, stream=None, out=Non
     check(scene.ctx.lib.hg_render_backward(state.h, C.c_void_p(g.data_ptr()),
                                            *[C.c_void_p(o.data_ptr()) for o in outs], _stream_ptr(stream)))
     return tuple(outs)
+
+
+def spatial_order(ctx: Context, means, stream=None):
+    """hg_spatial_order: int32 CUDA tensor [n], the indices of the gaussians
+    (means: float32 CUDA [n][3]) in ascending Morton code, ties by index."""
+    import torch
+    means = torch.as_tensor(means, device=torch.device("cuda", ctx.device)).to(torch.float32).contiguous()
+    n = means.shape[0]
+    perm = torch.empty(n, dtype=torch.int32, device=means.device)
+    check(ctx.lib.hg_spatial_order(ctx.h, C.c_void_p(means.data_ptr()), n, C.c_void_p(perm.data_ptr()),
+                                   _stream_ptr(stream)))
+    return perm
 
 
 def l2_loss(ctx: Context, rgb, target, dl_drgb=None, loss=None, stream=None):
