@@ -396,3 +396,25 @@ def test_image_1m_scene_sampled_tiles(lib, ctx):
             tiles = sample_tiles(1920, 1080, 48, seed=v)
             ref = C.render(P.project(scene, cam), tiles=tiles)
             compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles))
+
+
+def test_image_5m8_scene_bench_configuration(lib, ctx):
+    """The benchmark's workload and launch configuration: the 5.8M-gaussian
+    SH3 scene stored in spatial order, 4 views at 1080p in one launch, macro
+    4x4, B_r = 1024, ellipse binning; sampled tiles of two views against the
+    oracle's render of the same (permuted) scene, computed tile by tile."""
+    scene = scenes.scene_5m8()
+    gs = lib.GpuScene.from_scene(ctx, scene, order=lib.ORDER_SPATIAL)
+    perm = gs.order()
+    ref_scene = scene.copy()
+    ref_scene.means, ref_scene.log_scales = scene.means[perm], scene.log_scales[perm]
+    ref_scene.quats, ref_scene.opacity_logits, ref_scene.sh = (scene.quats[perm], scene.opacity_logits[perm],
+                                                                scene.sh[perm])
+    del scene
+    cams = scenes.scene_orbit(64, 1920, 1080)[4:8]
+    imgs, ts = render_np(lib, gs, cams, macro_w=4, macro_h=4, batch_cap=1024, bin_test=lib.BIN_ELLIPSE)
+    gs.close()
+    for v in (0, 3):
+        tiles = sample_tiles(1920, 1080, 24, seed=100 + v)
+        ref = C.render(P.project(ref_scene, cams[v]), tiles=tiles)
+        compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles))
