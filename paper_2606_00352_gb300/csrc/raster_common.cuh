@@ -78,6 +78,16 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
       }
     }
     // TransposeMasks: lane t receives the 32-gaussian masks of tile t
+    if constexpr (M <= 16) {
+      // both halves in one word (top masks in bits 0-15, bottom in 16-31):
+      // lane t < 16 receives tile t's top masks, lane 16 + t its bottom ones
+      const uint32_t tb = transpose32((uint32_t)gt | ((uint32_t)gb << 16), lane);
+      if ((lane & 15) < M) {
+        (lane < 16 ? s_top : s_bot)[k * M + (lane & 15)] = tb;
+        if (s_cnt) atomicAdd(&s_cnt[lane & 15], (uint32_t)__popc(tb));
+      }
+      continue;
+    }
     const uint32_t tlo = transpose32((uint32_t)gt, lane), blo = transpose32((uint32_t)gb, lane);
     if (lane < M) {
       s_top[k * M + lane] = tlo;
