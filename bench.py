@@ -522,7 +522,8 @@ def gpu_arm(args):
         pvalue, pms = job_throughput(pms, psteps * VIEWS, world)
         plain = {"value": round(pvalue, 2), "unit": UNIT,
                  "ms_per_step": round(pms / psteps, 3),
-                 "tile_pairs_per_step": int(statistics.mean(s["n_pairs"] for s in pstats))}
+                 "tile_pairs_per_step": int(statistics.mean(s["n_pairs"] for s in pstats)),
+                 "peak_tile_gaussians": int(max(s["max_segment"] for s in pstats))}
 
     serving = None
     if not args.skip_serve and world == 1:
@@ -577,6 +578,7 @@ def gpu_arm(args):
             "pairs_per_step": int(statistics.mean(s["n_pairs"] for s in s0)),
             "batches_per_step": int(statistics.mean(s["n_batches"] for s in s0)),
             "max_segment": int(max(s["max_segment"] for s in s0)),
+            "peak_unit_gaussians": int(min(opts.batch_cap, max(s["max_segment"] for s in s0))),
             "segments_by_tier_last_pose": s0[-1]["seg_by_tier"],
             "replays_per_step": int(statistics.mean(s["n_replays"] for s in s0)),
             "raster_evals_per_step": int(statistics.mean(s["raster_evals"] for s in s0)),

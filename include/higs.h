@@ -197,7 +197,7 @@ typedef struct {
   int64_t n_pairs;        /* macro-tile pairs (HiGS) or tile pairs (plain) */
   int64_t n_segments;     /* macro-tiles over all views */
   int64_t n_batches;      /* N_R */
-  int64_t max_segment;    /* largest segment */
+  int64_t max_segment;    /* largest segment (HiGS: macro-tile; plain path: 8x8 tile) */
   int64_t seg_by_tier[6]; /* segments sorted by tier: <=1K, <=4K, <=8K, <=16K, onesweep, empty/1 */
   int64_t n_sort_tiles;   /* onesweep tiles */
   int64_t n_replays;      /* merge replays (exact termination across batches) */

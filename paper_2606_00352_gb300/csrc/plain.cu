@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(TILE_PX) k_plain_raster(PlainArgs a, const uin
   PixelAcc p;
   pixel_init(p, inside);
   const uint2 rg = a.ranges[tile];
+  if (tid == 0 && rg.y > rg.x) atomicMax(&a.fc->max_seg, rg.y - rg.x);  // densest tile (frame stats)
   const float fpx = (float)px, fpy = (float)py;
   for (uint32_t base = rg.x; base < rg.y; base += TILE_PX) {
     if (__syncthreads_count(pixel_live(p)) == 0) break;
