@@ -247,23 +247,41 @@ def time_graph(lib, gs, cams, opts, steps, warmup, rank, world, stream, collect_
 
 def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
     """Public-API frames: hg_render with host cameras (uploaded by the call)
-    and the rendered images read back into pinned host memory every step."""
+    and the rendered images read back into pinned host memory every step.
+    Two image buffers alternate: the read-back of step k runs on a copy
+    stream while hg_render draws step k + 1; every step's copies are inside
+    the timed region, which ends when the last read-back has landed."""
     import torch
     pix = sum(c.width * c.height for c in cams[:VIEWS])
-    rgb = torch.empty(pix * 3, device="cuda", dtype=torch.float32)
-    host = torch.empty(pix * 3, dtype=torch.float32, pin_memory=True)
+    rgb = [torch.empty(pix * 3, device="cuda", dtype=torch.float32) for _ in range(2)]
+    host = [torch.empty(pix * 3, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
     state = lib.State(gs.ctx)
+
+    def step(k):
+        b = k % 2
+        stream.wait_event(copied[b])  # the buffer's previous read-back is done
+        lib.render(gs, pose_batch(cams, k, rank), opts, state=state, stream=stream, out_rgb=rgb[b], with_T=False)
+        rendered[b].record(stream)
+        copy_stream.wait_event(rendered[b])
+        with torch.cuda.stream(copy_stream):
+            host[b].copy_(rgb[b], non_blocking=True)
+        copied[b].record(copy_stream)
+
     with torch.cuda.stream(stream):
+        for b in range(2):
+            copied[b].record(copy_stream)
         for w in range(warmup):
-            lib.render(gs, pose_batch(cams, w, rank), opts, state=state, stream=stream, out_rgb=rgb, with_T=False)
-            host.copy_(rgb, non_blocking=True)
-            stream.synchronize()
+            step(w)
+        copy_stream.synchronize()
+        stream.synchronize()
         t0 = time.perf_counter()
         for k in range(steps):
-            lib.render(gs, pose_batch(cams, warmup + k, rank), opts, state=state, stream=stream, out_rgb=rgb,
-                       with_T=False)
-            host.copy_(rgb, non_blocking=True)
-            stream.synchronize()
+            step(warmup + k)
+        copy_stream.synchronize()
+        stream.synchronize()
         dt = time.perf_counter() - t0
     state.close()
     view_desc_bytes = 144  # camera table entry uploaded per view by hg_render

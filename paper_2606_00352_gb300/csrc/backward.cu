@@ -195,11 +195,13 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       // the tile's gaussians in depth order: set bits of its mini-batch masks
       if (__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
         for (int k = 0; k < K; ++k) {
-          uint32_t m = s_top[k * M + t] | s_bot[k * M + t];
+          const uint32_t mt = s_top[k * M + t], mb = s_bot[k * M + t];
+          uint32_t m = mt | mb;
           if (!m) continue;
           do {
-            const uint32_t j = (uint32_t)k * 32 + (__ffs(m) - 1);
-            m &= m - 1;
+            const uint32_t bit = m & (0u - m);
+            m ^= bit;
+            const uint32_t j = (uint32_t)k * 32 + (__ffs(bit) - 1);
             const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
             const float cA = g0.z * g0.z * k2, cB = g0.z * g0.w * k2, cC = (g0.w * g0.w + g1.x * g1.x) * k2;
             const float dx = fpx - g0.x;
@@ -207,9 +209,10 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
             float gs[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) gs[q] = 0.f;
-            bool c0, c1;
-            bwd_pixel(p0, ub, dx, fpy - g0.y, g0, g1, g2, cA, cB, cC, ct0, v0, gs, c0);
-            bwd_pixel(p1, ub, dx, fpy1 - g0.y, g0, g1, g2, cA, cB, cC, ct1, v1, gs, c1);
+            // a half the gaussian cannot reach is skipped, as in the forward
+            bool c0 = false, c1 = false;
+            if (mt & bit) bwd_pixel(p0, ub, dx, fpy - g0.y, g0, g1, g2, cA, cB, cC, ct0, v0, gs, c0);
+            if (mb & bit) bwd_pixel(p1, ub, dx, fpy1 - g0.y, g0, g1, g2, cA, cB, cC, ct1, v1, gs, c1);
             if (__any_sync(0xffffffffu, c0 || c1)) {
               const float tot = reduce_scatter16(gs, lane);
               const int idx = (lane >> 1) & 15;
