@@ -413,7 +413,7 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     return rows
 
 
-def train_step_ms(higs, ctx, steps=10, spatial=True):
+def train_step_ms(higs, ctx, steps=10, spatial=True, opts=None):
     """Densification-free optimisation steps on the 1M-gaussian scene, 4
     views at 1080p, against the render of a perturbed copy (means + N(0,
     1e-3), opacity logits + N(0, 0.1)): forward (saving what the backward
@@ -433,7 +433,7 @@ def train_step_ms(higs, ctx, steps=10, spatial=True):
     if spatial:
         perm = higs.spatial_order(ctx, params[0]).long()
         params = [p[perm].contiguous() for p in params]
-    tr = higs.Trainer(ctx, params, scene.sh_degree, cams, target)
+    tr = higs.Trainer(ctx, params, scene.sh_degree, cams, target, opts=opts)
     stream = torch.cuda.current_stream()
     times, losses = [], []
     for k in range(steps + 2):
@@ -458,7 +458,9 @@ def train_step_ms(higs, ctx, steps=10, spatial=True):
             "step_ms": round(sum(med), 3), "loss_first": round(losses[0], 3), "loss_last": round(losses[-1], 3),
             "workload": "1M-gaussian SH-3 scene (64 clusters, Zipf 1.2), 4 views at 1920x1080, target = render "
                         "of a perturbed copy; forward with saved prefixes + hg_l2_loss + hg_render_backward + "
-                        "hg_adam_step (3DGS learning rates)" + ("; parameters in hg_spatial_order" if spatial else "")}
+                        "hg_adam_step (3DGS learning rates)" + ("; parameters in hg_spatial_order" if spatial else "")
+                        + (f"; macro {opts.macro_w}x{opts.macro_h}, B_r {opts.batch_cap}, "
+                           f"{'ellipse' if opts.bin_test else 'rect'} binning" if opts else "")}
 
 
 def gpu_arm(args):
@@ -559,7 +561,9 @@ def gpu_arm(args):
         del small
     training = None
     if not args.skip_train and world == 1:
-        training = train_step_ms(higs, ctx, spatial=args.order == "spatial")
+        # the training default of higs.Trainer (macro 4x4, B_r 512, ellipse)
+        training = train_step_ms(higs, ctx, spatial=args.order == "spatial",
+                                 opts=higs.Options(macro_w=4, macro_h=4, batch_cap=512, bin_test=higs.BIN_ELLIPSE))
 
     e2e_opts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
                             batch_cap=opts.batch_cap, bin_test=opts.bin_test)
