@@ -60,8 +60,8 @@ struct PartitionArgs {
 
 // Sort tiers: segment-size limits handled by one CTA in shared memory.
 constexpr int TIER0_MAX = 1024;    // 128 threads x 8
-constexpr int TIER1_MAX = 4096;    // 256 threads x 16
-constexpr int TIER2_MAX = 8192;    // 512 threads x 16
+constexpr int TIER1_MAX = 4096;    // 512 threads x 8
+constexpr int TIER2_MAX = 8192;    // 1024 threads x 8
 constexpr int TIER3_MAX = 16384;   // 512 threads x 16, two halves then a merge
 // tiers: <= 1K, <= 4K, <= 8K, <= 16K (shared memory), onesweep, empty / one pair
 constexpr int N_TIERS = 6;

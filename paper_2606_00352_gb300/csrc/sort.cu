@@ -509,8 +509,8 @@ static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaS
   // the largest tiers first, each on its own stream when s1..s3 differ from
   // st: their tails overlap
   if ((e = launch_merge_tier<512, 16>(a, 3, s3)) != cudaSuccess) return e;
-  if ((e = launch_tier<512, 16>(a, 2, 2, s2)) != cudaSuccess) return e;
-  if ((e = launch_tier<256, 16>(a, 1, 4, s1)) != cudaSuccess) return e;
+  if ((e = launch_tier<1024, 8>(a, 2, 1, s2)) != cudaSuccess) return e;
+  if ((e = launch_tier<512, 8>(a, 1, 2, s1)) != cudaSuccess) return e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   bool alt = false;
