@@ -23,7 +23,7 @@ namespace hg {
 namespace {
 
 constexpr int PART_THREADS = 512;
-constexpr int UNR = 4;  // entries per thread per round in count / fill
+constexpr int UNR = 2;  // entries per thread per round in count / fill
 
 __global__ void __launch_bounds__(PART_THREADS) k_count(PartitionArgs a) {
   extern __shared__ uint32_t hist[];
