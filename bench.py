@@ -59,7 +59,8 @@ def workload_config():
     return {"workload": "5.8M-gaussian SH-3 cluster scene (256 clusters, Zipf 1.4), 1920x1080, "
                         "4 views per captured CUDA graph, 64-pose orbit",
             "n_gaussians": 5_800_000, "resolution": f"{WIDTH}x{HEIGHT}", "views_per_step": VIEWS,
-            "sh_degree": 3, "macro_tile": "8x4", "batch_cap": 1024, "scene_extent": scenes.EXTENT,
+            "sh_degree": 3, "macro_tile": "4x4", "batch_cap": 1024, "bin_test": "ellipse", "scene_order": "spatial",
+            "scene_extent": scenes.EXTENT,
             "orbit_radius": scenes.ORBIT_RADIUS,
             "l2": "inputs larger than L2 (scene arrays 1.37 GB, records 1.5 GB per step)"}
 
