@@ -254,7 +254,8 @@ hg_status hg_render_splats(hg_ctx* ctx, const hg_splat* d_splats, int64_t n,
 /* Backward of 0.5 ||C - C*||^2-style losses: given dL/dC (device, same layout
  * as out_rgb) of the frame saved in `state` (rendered with
  * save_for_backward), write dL/d(parameter) into the device arrays (same
- * shapes as the scene arrays; they are overwritten, not accumulated).  The
+ * shapes as the scene arrays, in the scene's stored order (hg_scene_order);
+ * they are overwritten, not accumulated).  The
  * forward saved the (C, T) entering every (batch, tile) (the prefix of the
  * Eq. 1 scan, Sec. 6) and the final colours; every batch is replayed from
  * its prefix with the forward's arithmetic, so the suffix colour behind a
