@@ -546,6 +546,25 @@ def gpu_arm(args):
                  "tile_pairs_per_step": int(statistics.mean(s["n_pairs"] for s in pstats)),
                  "peak_tile_gaussians": int(max(s["max_segment"] for s in pstats))}
 
+    # the same scene at 3840x2160 (the paper's second resolution), HiGS with
+    # the chosen shape and the plain per-tile path, 4 views per step
+    uhd = None
+    if not args.skip_plain:
+        cams4k = scenes.scene_orbit(N_POSES, 3840, 2160)
+        usteps = max(3, min(args.steps, 10))
+        hopts = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
+                             batch_cap=opts.batch_cap, bin_test=opts.bin_test, flags=higs.FLAG_TIMING)
+        ums, _, _ = time_graph(higs, gs, cams4k, hopts, usteps, min(args.warmup, 3), rank, world, stream,
+                               collect_stats=False)
+        uvalue, ums = job_throughput(ums, usteps * VIEWS, world)
+        popts4 = higs.Options(path=higs.PATH_PLAIN, flags=higs.FLAG_TIMING)
+        pums, _, _ = time_graph(higs, gs, cams4k, popts4, usteps, min(args.warmup, 3), rank, world, stream,
+                                collect_stats=False)
+        puvalue, pums = job_throughput(pums, usteps * VIEWS, world)
+        uhd = {"resolution": "3840x2160", "value": round(uvalue, 2), "unit": UNIT,
+               "ms_per_step": round(ums / usteps, 3), "plain_path_value": round(puvalue, 2),
+               "speedup_vs_plain": round(uvalue / puvalue, 3)}
+
     serving = None
     if not args.skip_serve and world == 1:
         from paper_2606_00352_gb300 import scenes as sc_mod
@@ -595,6 +614,7 @@ def gpu_arm(args):
         "gpu_launches": int(kernels * args.steps),
         "clocks": clocks,
         "plain_path": plain,
+        "uhd_4k": uhd,
         "precision_variants": sh_variants or None,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "frame_stats": {

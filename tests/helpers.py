@@ -32,6 +32,7 @@ def compare_image(img, T, ref, mask=None):
     worst_amb = float(err[amb].max()) if amb.any() else 0.0
     stats = {"max_abs": worst, "max_abs_T": worst_t, "ambiguous": int(amb.sum()), "ambiguous_frac": frac,
              "max_abs_ambiguous": worst_amb, "pixels": int(done.sum())}
+    print("image parity", stats)  # shown with pytest -s
     assert worst <= IMG_TOL, stats
     assert worst_t <= IMG_TOL, stats
     assert frac <= AMB_FRACTION, stats

@@ -52,6 +52,7 @@ def _compare(gpu, ref, rel_l2=1e-3, elem_frac=0.995):
         scale = 1e-3 * np.abs(b).max()
         ok = np.abs(a - b) <= 1e-3 * np.maximum(np.abs(b), scale) + 1e-7
         stats[k] = (rel, ok.mean())
+        print("gradient parity", k, "relative L2", rel, "elements within 1e-3", ok.mean())  # pytest -s
         assert nb > 0, k
         assert rel <= rel_l2, (k, stats)
         assert ok.mean() >= elem_frac, (k, stats)
