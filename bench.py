@@ -218,6 +218,12 @@ def time_graph(lib, gs, cams, opts, steps, warmup, rank, world, stream, collect_
     rgb = torch.empty(pix * 3, device="cuda", dtype=torch.float32)
     T = torch.empty(pix, device="cuda", dtype=torch.float32)
     state = lib.State(gs.ctx)
+    # size the workspace for every pose batch the replays will use: a
+    # captured graph cannot grow its buffers, and pair counts differ between
+    # poses (the synchronous render grows the state's buffers as needed)
+    sizing = lib.Options(**{**opts.__dict__, "flags": 0})
+    for k in range(warmup + steps + 1):
+        lib.render(gs, pose_batch(cams, k, rank), sizing, state=state, stream=stream, out_rgb=rgb, out_T=T)
     graph = lib.Graph(gs, pose_batch(cams, 0, rank), opts, rgb, T, state, stream)
     for w in range(warmup):
         graph.set_cameras(pose_batch(cams, w + 1, rank))
