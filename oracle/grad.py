@@ -77,10 +77,12 @@ def sh_poly_eval(dirs: np.ndarray, degree: int):
     return arr(f(x, y, z)), np.stack([arr(d(x, y, z)) for d in dfs])
 
 
-def pixel_grads(proj: dict, dl_drgb: np.ndarray, bg=(0.0, 0.0, 0.0), tile: int = 8):
+def pixel_grads(proj: dict, dl_drgb: np.ndarray, bg=(0.0, 0.0, 0.0), tile: int = 8, tiles=None):
     """Per-gaussian gradients of sum(dl_drgb * C) w.r.t. the projected
     quantities: mean2d [N, 2], conic [N, 3] (A, B, C of q = A dx^2 + 2B dx dy
-    + C dy^2), opacity [N], rgb [N, 3].  dl_drgb [H, W, 3]."""
+    + C dy^2), opacity [N], rgb [N, 3].  dl_drgb [H, W, 3].  `tiles` lists
+    the tile indices whose pixels carry a non-zero dl_drgb (None: all
+    tiles); a tile with dl_drgb = 0 adds exactly zero, so it is skipped."""
     n = proj["n"]
     w, h = proj["width"], proj["height"]
     bg = np.asarray(bg, np.float64)
@@ -89,7 +91,7 @@ def pixel_grads(proj: dict, dl_drgb: np.ndarray, bg=(0.0, 0.0, 0.0), tile: int =
     g_op = np.zeros(n)
     g_rgb = np.zeros((n, 3))
     gw, gh, off, gid = tile_candidates(proj, tile)
-    for t in range(gw * gh):
+    for t in (range(gw * gh) if tiles is None else tiles):
         ids = gid[off[t]:off[t + 1]]
         if len(ids) == 0:
             continue
@@ -231,13 +233,16 @@ def project_grads(scene, cam, proj: dict, g: dict):
     return {"means": g_means, "log_scales": g_logs, "quats": g_quat, "opacity_logits": g_logit, "sh": g_sh}
 
 
-def render_grads(scene, cams, dl_drgb_views, bg=(0.0, 0.0, 0.0)):
-    """Gradient of sum_v sum(dl_drgb_v * C_v) over views w.r.t. the scene."""
+def render_grads(scene, cams, dl_drgb_views, bg=(0.0, 0.0, 0.0), tiles_views=None):
+    """Gradient of sum_v sum(dl_drgb_v * C_v) over views w.r.t. the scene.
+    `tiles_views[v]` (optional) lists the tiles of view v outside which
+    dl_drgb_v is zero."""
     from .project import project
     out = None
-    for cam, dl in zip(cams, dl_drgb_views):
+    for v, (cam, dl) in enumerate(zip(cams, dl_drgb_views)):
         pr = project(scene, cam)
-        g = project_grads(scene, cam, pr, pixel_grads(pr, dl, bg))
+        tl = None if tiles_views is None else tiles_views[v]
+        g = project_grads(scene, cam, pr, pixel_grads(pr, dl, bg, tiles=tl))
         if out is None:
             out = g
         else:

@@ -9,7 +9,7 @@ from paper_2606_00352_gb300 import scenes
 from oracle import composite as C
 from oracle import grad as G
 from oracle import project as P
-from tests.helpers import ambiguous
+from tests.helpers import ambiguous, sample_tiles, tiles_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -111,17 +111,59 @@ def test_autograd_l2_loss(lib, ctx):
     _compare(gpu, ref, rel_l2=2e-3, elem_frac=0.99)
 
 
-def test_backward_1m_scene_runs(lib, ctx):
-    """Gradient of the 1M-gaussian scene over 4 views at 1080p: finite and
-    non-zero for visible gaussians (full size; parity is checked above)."""
+def test_backward_1m_training_configuration_sampled_tiles(lib, ctx):
+    """The training step's workload and launch configuration: the 1M-gaussian
+    SH3 scene stored in spatial order, 4 views at 1080p in one launch, macro
+    4x4, B_r = 512, ellipse binning.  The upstream gradient is random on
+    sampled tiles of every view and zero elsewhere, so the oracle gradient,
+    computed tile by tile, is the exact gradient of the whole scene: the
+    gaussians it reaches must match it, every other one must get zero.
+
+    The colour behind a gaussian is the pixel's final colour minus the
+    colour in front of it; in float32 that difference carries an absolute
+    error of ~1e-7 of the pixel colour, which for gaussians deep in a
+    1080p stack (T near 1e-4) is ~1e-3 of their terms.  Gradient elements
+    near the 1e-3 floor of their array therefore reach relative errors of a
+    few 1e-3 (0.6% of the mean gradients here), so 99% of the elements must
+    be within 1e-3; the relative L2 bound is the usual 1e-3."""
     import torch
     scene = scenes.scene_1m()
+    gs = lib.GpuScene.from_scene(ctx, scene, order=lib.ORDER_SPATIAL)
+    perm = gs.order()
+    ref_scene = scene.copy()
+    ref_scene.means, ref_scene.log_scales = scene.means[perm], scene.log_scales[perm]
+    ref_scene.quats, ref_scene.opacity_logits, ref_scene.sh = (scene.quats[perm], scene.opacity_logits[perm],
+                                                                scene.sh[perm])
+    del scene
+    n = ref_scene.n
     cams = scenes.scene_orbit(32, 1920, 1080)[:4]
-    gs = lib.GpuScene.from_scene(ctx, scene)
+    g = np.random.default_rng(21)
+    tiles_views, vs = [], []
+    for v, cam in enumerate(cams):
+        tl = sample_tiles(1920, 1080, 12, seed=200 + v)
+        fwd = C.render(P.project(ref_scene, cam), tiles=tl)
+        m = tiles_mask(1920, 1080, tl)
+        up = np.zeros((1080, 1920, 3))
+        up[m] = g.normal(0.0, 1.0, (int(m.sum()), 3))
+        up[ambiguous(fwd)] = 0.0
+        tiles_views.append(tl)
+        vs.append(up)
+    ref = G.render_grads(ref_scene, cams, vs, tiles_views=tiles_views)
     st = lib.State(ctx)
-    rgb, _ = lib.render(gs, cams, lib.Options(save_for_backward=True), state=st, with_T=False)
-    g = lib.render_backward(st, gs, torch.ones_like(rgb))
+    opts = lib.Options(macro_w=4, macro_h=4, batch_cap=512, bin_test=lib.BIN_ELLIPSE, save_for_backward=True)
+    lib.render(gs, cams, opts, state=st, with_T=False)
+    flat = torch.from_numpy(np.concatenate([v.reshape(-1) for v in vs]).astype(np.float32)).cuda()
+    out = lib.render_backward(st, gs, flat)
     torch.cuda.synchronize()
-    for t in g:
-        assert torch.isfinite(t).all()
-    assert (g[3] != 0).float().mean().item() > 0.3
+    gpu = {k: o.cpu().numpy().astype(np.float64) for k, o in zip(NAMES, out)}
+    st.close()
+    gs.close()
+    reached = np.zeros(n, bool)
+    for k in NAMES:
+        assert np.isfinite(gpu[k]).all(), k
+        reached |= np.abs(ref[k].reshape(n, -1)).max(axis=1) > 0
+    print("gaussians reached by the sampled tiles", int(reached.sum()))  # pytest -s
+    assert reached.sum() >= 1000
+    _compare({k: gpu[k][reached] for k in NAMES}, {k: ref[k][reached] for k in NAMES}, elem_frac=0.99)
+    for k in NAMES:
+        assert np.abs(gpu[k][~reached]).max() <= 1e-6 * np.abs(ref[k]).max(), k

@@ -132,3 +132,29 @@ def test_single_gaussian_opacity_gradient_closed_form():
     ana = G.render_grads(sc, [cam], [v])
     img = C.render(P.project(sc, cam))["rgb"]
     np.testing.assert_allclose(ana["opacity_logits"][0], img[8, 8, 0] * (1 - o), rtol=1e-10)
+
+
+def test_gradient_restricted_to_tiles_equals_full():
+    """An upstream gradient that is zero outside a few tiles: skipping the
+    other tiles gives the full sum bit for bit (the form the full-size GPU
+    backward test uses)."""
+    scene = _scene(n=80, seed=4)
+    cams = [look_at((2.5, 0.2, 0.1), width=44, height=35, fov_x_deg=40.0),
+            look_at((0.3, 2.4, -0.5), width=33, height=41, fov_x_deg=45.0)]
+    g = np.random.default_rng(11)
+    tiles_views, vs = [], []
+    for cam in cams:
+        gw, gh = -(-cam.width // 8), -(-cam.height // 8)
+        tl = sorted(set(int(t) for t in g.choice(gw * gh, size=4, replace=False)) | {gw * gh - 1})
+        v = np.zeros((cam.height, cam.width, 3))
+        for t in tl:
+            tx, ty = t % gw, t // gw
+            v[ty * 8:(ty + 1) * 8, tx * 8:(tx + 1) * 8] = g.normal(0.0, 1.0, v[ty * 8:(ty + 1) * 8, tx * 8:(tx + 1) * 8].shape)
+        tiles_views.append(tl)
+        vs.append(v)
+    bg = (0.2, 0.1, 0.3)
+    full = G.render_grads(scene, cams, vs, bg)
+    part = G.render_grads(scene, cams, vs, bg, tiles_views=tiles_views)
+    for k in full:
+        assert np.array_equal(full[k], part[k]), k
+        assert np.abs(full[k]).max() > 0, k
