@@ -299,17 +299,25 @@ def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
 # each stage's kernels on this workload (spatially ordered scene), from one
 # ncu capture of `bench.py --case 5m8 --macro 4x4 --steps 1 --warmup 1`
 # (summary under profiles/), valid while the CUDA sources hash to `digest`.
-MEASURED_TRAFFIC = {"digest": "5df64fa4fe653fe6",
+MEASURED_TRAFFIC = {"digest": "4e373627ab730a6b",
                     "bytes": {"project": 2928.0e6, "partition": 913.5e6, "sort": 235.9e6, "raster": 2214.3e6,
                               "merge": 0.0}}
 
 
+# CUDA sources that do not build or launch a kernel of the forward HiGS frame
+# (backward, training, serving, CUDA graphs, autotuner, plain path, SH
+# encoder): a change there leaves the forward kernels' DRAM bytes as captured
+FORWARD_INDEPENDENT = ("backward.cu", "train.cu", "serve.cu", "graph.cu", "tune.cu", "plain.cu", "sh_codec.cu")
+
+
 def sources_digest() -> str:
+    """Digest of the CUDA sources the forward frame's kernels are built from
+    (every header, every translation unit but FORWARD_INDEPENDENT)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2606_00352_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) and f not in FORWARD_INDEPENDENT:
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -420,13 +428,13 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     return rows
 
 
-def train_step_ms(higs, ctx, steps=10, spatial=True, opts=None):
-    """Densification-free optimisation steps on the 1M-gaussian scene, 4
-    views at 1080p, against the render of a perturbed copy (means + N(0,
-    1e-3), opacity logits + N(0, 0.1)): forward (saving what the backward
-    needs), L2 loss, backward, Adam, each timed with CUDA events.  With
-    `spatial` the parameter tensors are permuted once into hg_spatial_order
-    before training (the optimiser state follows the same order)."""
+def train_setup(higs, ctx, spatial=True, opts=None):
+    """The training workload: the 1M-gaussian scene, 4 views at 1080p, a
+    Trainer (default launch configuration unless `opts`) whose target is the
+    render of a perturbed copy (means + N(0, 1e-3), opacity logits + N(0,
+    0.1)).  With `spatial` the parameter tensors are permuted once into
+    hg_spatial_order before training (the optimiser state follows the same
+    order)."""
     import torch
     from paper_2606_00352_gb300 import scenes
     scene = scenes.scene_1m()
@@ -440,7 +448,15 @@ def train_step_ms(higs, ctx, steps=10, spatial=True, opts=None):
     if spatial:
         perm = higs.spatial_order(ctx, params[0]).long()
         params = [p[perm].contiguous() for p in params]
-    tr = higs.Trainer(ctx, params, scene.sh_degree, cams, target, opts=opts)
+    return higs.Trainer(ctx, params, scene.sh_degree, cams, target, opts=opts), cams
+
+
+def train_step_ms(higs, ctx, steps=10, spatial=True, opts=None):
+    """Densification-free optimisation steps of the training workload
+    (train_setup): forward (saving what the backward needs), L2 loss,
+    backward, Adam, each timed with CUDA events."""
+    import torch
+    tr, cams = train_setup(higs, ctx, spatial, opts)
     stream = torch.cuda.current_stream()
     times, losses = [], []
     for k in range(steps + 2):
@@ -666,6 +682,25 @@ def profile_case(args):
     print(json.dumps({"case": args.case, "stats": s}), flush=True)
 
 
+def profile_train_case(args):
+    """Small case for kernel captures of the training step: the training
+    workload (train_setup) in the Trainer's default launch configuration
+    (macro 4x4, B_r = 512, ellipse), `--warmup + --steps` optimisation
+    steps through Trainer.step."""
+    import torch
+    from paper_2606_00352_gb300 import higs
+    higs.load()
+    torch.cuda.set_device(0)
+    ctx = higs.Context(0)
+    tr, _ = train_setup(higs, ctx, spatial=args.order == "spatial")
+    loss = None
+    for _ in range(args.warmup + args.steps):
+        loss = tr.step()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "loss": float(loss.item())}), flush=True)
+    tr.close()
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -694,7 +729,7 @@ def main():
     ap.add_argument("--skip-train", action="store_true")
     ap.add_argument("--skip-tune", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--case", default="", choices=["", "1m", "1m-plain", "5m8"],
+    ap.add_argument("--case", default="", choices=["", "1m", "1m-plain", "5m8", "train1m"],
                     help="small profiling case instead of the benchmark")
     ap.add_argument("--profile", action="store_true", help="count rasteriser phase cycles (profiling case)")
     ap.add_argument("--macro", default="8x4", choices=["4x4", "8x4", "8x8"], help="macro shape without autotuning")
@@ -711,7 +746,9 @@ def main():
         print(json.dumps({"value": 1.0 / (statistics.mean(times) * ORACLE_FRACTION), "ms_per_step": ms,
                           "times": times}))
         return
-    if args.case:
+    if args.case == "train1m":
+        profile_train_case(args)
+    elif args.case:
         profile_case(args)
     elif args.impl == "reference":
         reference_arm(args)

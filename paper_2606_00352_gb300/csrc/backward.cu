@@ -20,7 +20,8 @@
 //                 projection in float32 as the forward did and applies the
 //                 chain rule through conic, EWA covariance, Jacobian, mean,
 //                 quaternion, scales, sigmoid opacity and the SH colour
-//                 (coefficients and view direction).
+//                 (coefficients and view direction); the SH rows and their
+//                 gradients move through shared memory in coalesced sweeps.
 #include "internal.h"
 #include "raster_common.cuh"
 
@@ -270,11 +271,13 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
   }
 }
 
+// Chain rule of one gaussian i through all views: writes the gradients of
+// its mean, log-scales, quaternion and opacity logit, and adds the SH
+// gradient to dsh.  shr is the gaussian's SH row (K x 3 floats).
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project_bwd(ProjectBackwardArgs a) {
+__device__ __forceinline__ void project_bwd_gaussian(const ProjectBackwardArgs& a, long long i, const float* shr,
+                                                     float (&dsh)[(DEG + 1) * (DEG + 1) * 3]) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
   const float px = a.means[i * 3 + 0], py = a.means[i * 3 + 1], pz = a.means[i * 3 + 2];
   const float sx = expf(a.log_scales[i * 3 + 0]), sy = expf(a.log_scales[i * 3 + 1]), sz = expf(a.log_scales[i * 3 + 2]);
   const float4 q = reinterpret_cast<const float4*>(a.quats)[i];
@@ -297,9 +300,6 @@ __global__ void __launch_bounds__(128) k_project_bwd(ProjectBackwardArgs a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) sig3[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
   float dmu[3] = {0.f, 0.f, 0.f}, dM[3][3] = {}, dlogit = 0.f;
-  float dsh[K * 3];
-#pragma unroll
-  for (int k = 0; k < K * 3; ++k) dsh[k] = 0.f;
   for (int v = 0; v < a.n_views; ++v) {
     const float* g = a.g2d + ((size_t)v * a.n + i) * NG;
     float gv[NG];
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(ProjectBackwardArgs a) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) raw[c] = fmaf(Y[k], a.sh[(i * K + k) * 3 + c], raw[c]);
+      for (int c = 0; c < 3; ++c) raw[c] = fmaf(Y[k], shr[k * 3 + c], raw[c]);
     float gc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.f ? gv[6 + c] : 0.f;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(ProjectBackwardArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         dsh[k * 3 + c] += Y[k] * gc[c];
-        s = fmaf(a.sh[(i * K + k) * 3 + c], gc[c], s);
+        s = fmaf(shr[k * 3 + c], gc[c], s);
       }
       gdx = fmaf(Yx[k], s, gdx);
       gdy = fmaf(Yy[k], s, gdy);
@@ -450,8 +450,37 @@ __global__ void __launch_bounds__(128) k_project_bwd(ProjectBackwardArgs a) {
     a.d_log_scales[i * 3 + k] = ds[k] * S[k];
   }
   a.d_opacity_logits[i] = dlogit;
+}
+
+// One thread per gaussian.  The CTA's SH rows are read from and the SH
+// gradient rows written to global memory by coalesced row-major sweeps
+// through shared memory (rows padded to an odd stride, so the per-thread
+// row accesses of a warp fall in distinct banks).
+constexpr int PB_THREADS = 128;
+
+template <int DEG>
+__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(ProjectBackwardArgs a) {
+  constexpr int KS = (DEG + 1) * (DEG + 1) * 3;
+  constexpr int ST = KS | 1;
+  __shared__ float s_sh[PB_THREADS * ST];
+  const int t = threadIdx.x;
+  const long long base = (long long)blockIdx.x * PB_THREADS;
+  const int rows = (int)min((long long)PB_THREADS, a.n - base);
+  const float* src = a.sh + base * KS;
+  for (int e = t; e < rows * KS; e += PB_THREADS) s_sh[(e / KS) * ST + e % KS] = src[e];
+  __syncthreads();
+  float dsh[KS];
 #pragma unroll
-  for (int k = 0; k < K * 3; ++k) a.d_sh[i * K * 3 + k] = dsh[k];
+  for (int k = 0; k < KS; ++k) dsh[k] = 0.f;
+  if (t < rows) project_bwd_gaussian<DEG>(a, base + t, s_sh + t * ST, dsh);
+  __syncthreads();
+  if (t < rows) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) s_sh[t * ST + k] = dsh[k];
+  }
+  __syncthreads();
+  float* dst = a.d_sh + base * KS;
+  for (int e = t; e < rows * KS; e += PB_THREADS) dst[e] = s_sh[(e / KS) * ST + e % KS];
 }
 
 template <int MW, int MH>
@@ -473,7 +502,7 @@ cudaError_t launch_bwd_shape(const BackwardArgs& a, cudaStream_t st) {
 template <int DEG>
 cudaError_t launch_pbwd_deg(const ProjectBackwardArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_project_bwd<DEG><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a);
+  k_project_bwd<DEG><<<(unsigned)((a.n + PB_THREADS - 1) / PB_THREADS), PB_THREADS, 0, st>>>(a);
   note_launch();
   return cudaGetLastError();
 }
