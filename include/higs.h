@@ -273,8 +273,9 @@ hg_status hg_render_backward(hg_state* state, const float* dL_drgb,
 /* L2 photometric loss L = 1/2 sum_i (rgb_i - target_i)^2 over n floats and
  * its gradient dL/d rgb_i = rgb_i - target_i (float32).  rgb, target and
  * dL_drgb are device arrays of n floats (dL_drgb may alias neither input);
- * *loss (device double) receives L.  The sum is accumulated in double in a
- * fixed order, so the result is deterministic.  Scratch for the reduction
+ * *loss (device double) receives L.  The squares are summed in float32
+ * four consecutive elements at a time and those sums in double, in a fixed
+ * order, so the result is deterministic.  Scratch for the reduction
  * is allocated through the context's allocator on the first call: make that
  * call outside CUDA graph capture.  Calls on one context must be
  * stream-serialised (they share the scratch).

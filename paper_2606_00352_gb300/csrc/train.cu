@@ -14,11 +14,17 @@ namespace hg {
 
 namespace {
 
-constexpr int LOSS_THREADS = 256;
+constexpr int LOSS_THREADS = 1024;  // 2 blocks per SM (the block count is fixed): enough loads in flight
 
-// dL/dC = C - C* per element; L = 1/2 sum (C - C*)^2 accumulated in double
-// with a fixed grid and a fixed summation order (deterministic): per-block
-// partials, the last block to finish adds them in block order.
+// dL/dC = C - C* per element; L = 1/2 sum (C - C*)^2.  Elements are taken
+// four at a time (16-byte vectors when the three arrays allow it): the four
+// squares are summed in float32, (d0^2 + d1^2) + (d2^2 + d3^2), and the
+// group sums in double (FP64 arithmetic is slow on this part, so one double
+// add per four elements).  The grid is fixed and so is the summation order
+// (deterministic): per-block partials, which the last block to finish adds
+// with a fixed reduction tree.
+__device__ __forceinline__ float sq4(float a, float b, float c, float d) { return (a * a + b * b) + (c * c + d * d); }
+
 __global__ void __launch_bounds__(LOSS_THREADS) k_l2_loss(const float* __restrict__ rgb,
                                                           const float* __restrict__ target, long long n,
                                                           float* __restrict__ dl, double* partial,
@@ -26,11 +32,33 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_l2_loss(const float* __restric
   __shared__ double red[LOSS_THREADS / 32];
   __shared__ bool last;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * LOSS_THREADS + threadIdx.x; i < n;
-       i += (long long)gridDim.x * LOSS_THREADS) {
+  const long long stride = (long long)gridDim.x * LOSS_THREADS;
+  const bool vec = ((reinterpret_cast<uintptr_t>(rgb) | reinterpret_cast<uintptr_t>(target) |
+                     reinterpret_cast<uintptr_t>(dl)) & 15u) == 0;
+  const long long groups = n / 4;
+  for (long long q = (long long)blockIdx.x * LOSS_THREADS + threadIdx.x; q < groups; q += stride) {
+    float4 d;
+    if (vec) {
+      const float4 a = reinterpret_cast<const float4*>(rgb)[q], b = reinterpret_cast<const float4*>(target)[q];
+      d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+      reinterpret_cast<float4*>(dl)[q] = d;
+    } else {
+      const long long i = q * 4;
+      d = make_float4(rgb[i] - target[i], rgb[i + 1] - target[i + 1], rgb[i + 2] - target[i + 2],
+                      rgb[i + 3] - target[i + 3]);
+      dl[i] = d.x;
+      dl[i + 1] = d.y;
+      dl[i + 2] = d.z;
+      dl[i + 3] = d.w;
+    }
+    acc += (double)sq4(d.x, d.y, d.z, d.w);
+  }
+  // the last n mod 4 elements: block 0, one thread each
+  if (blockIdx.x == 0 && threadIdx.x < (int)(n - groups * 4)) {
+    const long long i = groups * 4 + threadIdx.x;
     const float d = rgb[i] - target[i];
     dl[i] = d;
-    acc += (double)d * (double)d;
+    acc += (double)(d * d);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -45,10 +73,20 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_l2_loss(const float* __restric
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
+  if (!last) return;  // block-uniform
+  // the last block adds the partials with a fixed tree (one per thread, then
+  // the warp and block reductions above), so the order is fixed and the
+  // partials are read in parallel
+  __threadfence();
+  double v = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += LOSS_THREADS) v += __ldcg(&partial[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double s = 0.0;
-    for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double*)partial)[b];
+    for (int w = 0; w < LOSS_THREADS / 32; ++w) s += red[w];
     *loss = 0.5 * s;
     *counter = 0;
   }
@@ -60,30 +98,54 @@ struct AdamGroup {
   float* m;
   float* v;
   long long n;
+  long long nv;  // 4-element vector units (0 when an array is not 16-byte aligned)
   float lr;
 };
 
 struct AdamArgs {
   AdamGroup grp[5];
-  long long end[5];  // exclusive prefix ends of the groups in the flat index
+  long long end[5];  // exclusive prefix ends of the groups, in units
   float b1, b2, c1, c2, eps;
 };
 
-// One thread per parameter element of all five groups.
+__device__ __forceinline__ float adam_one(const AdamArgs& a, const AdamGroup& G, float g, float& m, float& v,
+                                          float p) {
+  m = fmaf(a.b1, m, (1.f - a.b1) * g);
+  v = fmaf(a.b2, v, (1.f - a.b2) * g * g);
+  return p - G.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+}
+
+// One thread per unit of all five groups; a unit is four consecutive
+// elements of a group (16-byte vectors) for the first nv units of the
+// group, then single elements for the rest (the last count mod 4, or all of
+// them when one of the group's arrays is not 16-byte aligned).
 __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
   const long long total = a.end[4];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int k = 0;
     while (i >= a.end[k]) ++k;
-    const long long j = i - (k ? a.end[k - 1] : 0);
+    const long long u = i - (k ? a.end[k - 1] : 0);
     const AdamGroup& G = a.grp[k];
-    const float g = G.g[j];
-    const float m = fmaf(a.b1, G.m[j], (1.f - a.b1) * g);
-    const float v = fmaf(a.b2, G.v[j], (1.f - a.b2) * g * g);
-    G.m[j] = m;
-    G.v[j] = v;
-    G.p[j] -= G.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+    const long long nv = G.nv;
+    if (u < nv) {
+      const float4 g = reinterpret_cast<const float4*>(G.g)[u];
+      float4 m = reinterpret_cast<const float4*>(G.m)[u], v = reinterpret_cast<const float4*>(G.v)[u];
+      float4 p = reinterpret_cast<const float4*>(G.p)[u];
+      p.x = adam_one(a, G, g.x, m.x, v.x, p.x);
+      p.y = adam_one(a, G, g.y, m.y, v.y, p.y);
+      p.z = adam_one(a, G, g.z, m.z, v.z, p.z);
+      p.w = adam_one(a, G, g.w, m.w, v.w, p.w);
+      reinterpret_cast<float4*>(G.m)[u] = m;
+      reinterpret_cast<float4*>(G.v)[u] = v;
+      reinterpret_cast<float4*>(G.p)[u] = p;
+    } else {
+      const long long j = nv * 4 + (u - nv);
+      float m = G.m[j], v = G.v[j];
+      G.p[j] = adam_one(a, G, G.g[j], m, v, G.p[j]);
+      G.m[j] = m;
+      G.v[j] = v;
+    }
   }
 }
 
@@ -143,8 +205,11 @@ extern "C" hg_status hg_adam_step(hg_scene* scene, const float* const grads[5], 
       hg_set_error("hg_adam_step: missing buffer");
       return HG_ERR_INVALID_ARG;
     }
-    a.grp[k] = AdamGroup{scene->arr[k], grads[k], m[k], v[k], counts[k], o->lr[k]};
-    end += counts[k];
+    const bool aligned = ((reinterpret_cast<uintptr_t>(scene->arr[k]) | reinterpret_cast<uintptr_t>(grads[k]) |
+                           reinterpret_cast<uintptr_t>(m[k]) | reinterpret_cast<uintptr_t>(v[k])) & 15u) == 0;
+    const long long nv = aligned ? counts[k] / 4 : 0;
+    a.grp[k] = AdamGroup{scene->arr[k], grads[k], m[k], v[k], counts[k], nv, o->lr[k]};
+    end += nv + (counts[k] - 4 * nv);
     a.end[k] = end;
   }
   a.b1 = o->beta1;
