@@ -385,17 +385,19 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     poses = {r: scenes.scene_orbit(N_POSES, r[0], r[1]) for r in SERVE_RES}
     # warm the slots' workspaces at every resolution, then with bursts of the
     # largest batch (max_views_per_launch views at the largest resolution of
-    # one scene, submitted together so that they share launches), so that no
-    # slot grows its workspace inside the timed rates
+    # one scene, submitted together so that they share launches) over every
+    # pose, so that no slot grows its workspace inside the timed rates (a
+    # growth reallocates and re-renders, a stall of tens of milliseconds)
     warm = [srv.submit(sids[k % len(sids)], poses[SERVE_RES[k % 3]][k], pool[k]) for k in range(12)]
     for rid in warm:
         srv.wait(rid)
     big = max(SERVE_RES, key=lambda r: r[0] * r[1])
     for _ in range(2):
         for sid in sids:
-            burst = [srv.submit(sid, poses[big][k], pool[k]) for k in range(32)]
-            for rid in burst:
-                srv.wait(rid)
+            for k0 in range(0, N_POSES, 32):
+                burst = [srv.submit(sid, poses[big][k0 + k], pool[k]) for k in range(32)]
+                for rid in burst:
+                    srv.wait(rid)
     rows = []
     for rate in SERVE_RATES:
         srv.reset_stats()
