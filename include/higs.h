@@ -352,7 +352,12 @@ void hg_graph_destroy(hg_graph* graph);
  * scene of the oldest pending request (any mix of resolutions) into one
  * multi-view launch, if the memory the slots then hold stays within
  * mem_budget_bytes (0 = no limit).  Requests arriving meanwhile are admitted
- * as slots and memory free up, so their work overlaps on the device. */
+ * as slots and memory free up, so their work overlaps on the device.  A
+ * slot's workspace grows on demand: a launch that binned more pairs than it
+ * holds is re-run after the slot reallocates (25% headroom), which delays
+ * that launch and the device by the allocation; latency-sensitive callers
+ * warm every slot with the largest launches they expect (max_views_per_launch
+ * views at the largest resolution) before serving. */
 typedef struct {
   int32_t max_inflight;          /* 1..64 launches on the device at once */
   int32_t max_views_per_launch;  /* 1..64 */
