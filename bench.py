@@ -66,46 +66,159 @@ def workload_config():
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample_steps(steps: int, warmup: int, seed: int = 0):
-    """Times the FP64 oracle on bounded samples of the workload (this
-    process; numpy single-threaded).  Returns per-step seconds."""
+# The oracle's sampled work runs in a subprocess that never touches CUDA, so
+# its worker pool is forked there (each worker inherits the scene and the
+# full projection); one worker per host core.
+_ORACLE = {}
+
+
+def _oracle_state():
     import numpy as np
     from paper_2606_00352_gb300 import scenes
     from oracle import project as P, composite as Cmp
-    scene = scenes.scene_5m8()
-    cam = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)[0]
-    full = P.project(scene, cam)  # full projection for the sampled tiles (not timed)
-    cand = Cmp.tile_candidates(full)
-    n = scene.n
+    if not _ORACLE:
+        scene = scenes.scene_5m8()
+        cam = scenes.scene_orbit(N_POSES, WIDTH, HEIGHT)[0]
+        full = P.project(scene, cam)  # full projection for the sampled tiles (not timed)
+        _ORACLE.update(scene=scene, cam=cam, full=full, cand=Cmp.tile_candidates(full), np=np)
+    return _ORACLE
+
+
+# Decision-ambiguity bands of the parity tests (support q, alpha, transmittance)
+AMB_BANDS = (5e-5, 5e-5, 1e-5)
+
+
+def _ambiguous_count(ref):
+    """(decision-ambiguous pixels, evaluated pixels) of an oracle render."""
+    a = ((ref["m_q"] < AMB_BANDS[0]) | (ref["m_alpha"] < AMB_BANDS[1]) | (ref["m_T"] < AMB_BANDS[2])) & ref["done"]
+    return int(a.sum()), int(ref["done"].sum())
+
+
+def _oracle_chunk(job):
+    """One worker's share of a sampled step: the projection + binning of the
+    slice [lo, lo + sl) and the compositing of `tiles`.  Returns (seconds,
+    decision-ambiguous pixels, pixels) of the composited tiles."""
+    from oracle import project as P, composite as Cmp
+    st = _oracle_state()
+    lo, sl, tiles = job
+    t0 = time.perf_counter()
+    Cmp.tile_candidates(P.project(st["scene"].subset(slice(lo, lo + sl)), st["cam"]))
+    ref = Cmp.render(st["full"], tiles=tiles, cand=st["cand"])
+    dt = time.perf_counter() - t0
+    return (dt, *_ambiguous_count(ref))
+
+
+def oracle_sample_steps(steps: int, warmup: int, seed: int = 0, cores: int = 1):
+    """Times the FP64 oracle on bounded samples of the workload: per step
+    each of `cores` workers projects and bins 1/ORACLE_FRACTION of the
+    gaussians and composites ORACLE_TILES sampled tiles of one view (numpy,
+    one thread per worker), so a frame is ORACLE_FRACTION / cores steps.
+    Returns per-step wall seconds."""
+    import multiprocessing as mp
+    st = _oracle_state()
+    np = st["np"]
+    n = st["scene"].n
     sl = n // ORACLE_FRACTION
     gw, gh = -(-WIDTH // 8), -(-HEIGHT // 8)
     g = np.random.default_rng(seed)
-    times = []
-    for k in range(warmup + steps):
-        lo = (k * sl) % (n - sl)
-        part = scene.subset(slice(lo, lo + sl))
-        tiles = g.choice(gw * gh, ORACLE_TILES, replace=False)
-        t0 = time.perf_counter()
-        Cmp.tile_candidates(P.project(part, cam))   # 1/ORACLE_FRACTION of projection + binning
-        Cmp.render(full, tiles=tiles, cand=cand)     # ORACLE_TILES tiles of compositing
-        dt = time.perf_counter() - t0
-        if k >= warmup:
-            times.append(dt)
+    pool = mp.get_context("fork").Pool(cores) if cores > 1 else None
+    times, amb = [], [0, 0]
+    try:
+        for k in range(warmup + steps):
+            jobs = []
+            for c in range(cores):
+                lo = ((k * cores + c) * sl) % (n - sl)
+                jobs.append((lo, sl, g.choice(gw * gh, ORACLE_TILES, replace=False)))
+            t0 = time.perf_counter()
+            res = [_oracle_chunk(jobs[0])] if pool is None else pool.map(_oracle_chunk, jobs, chunksize=1)
+            dt = time.perf_counter() - t0
+            if k >= warmup:
+                times.append(dt)
+                amb[0] += sum(r[1] for r in res)
+                amb[1] += sum(r[2] for r in res)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    oracle_sample_steps.ambiguous = amb
     return times
 
 
-def run_oracle_subprocess(steps: int, warmup: int):
+def _config_tile_chunk(job):
+    from oracle import composite as Cmp
+    st = _ORACLE["cfg"]
+    t0 = time.perf_counter()
+    Cmp.render(st["proj"], tiles=job, cand=st["cand"])
+    return time.perf_counter() - t0
+
+
+def oracle_configs(cores: int):
+    """The oracle on the tiny and the 1M configurations, one pose each, on one
+    core and on `cores` workers: the tiny frame in full (projection and all
+    1,024 tiles); the 1M frame at 1080p as its full projection plus a sample
+    of 256 tiles per worker, scaled to the 32,400 tiles of the frame."""
+    import multiprocessing as mp
+    import numpy as np
+    from paper_2606_00352_gb300 import scenes
+    from oracle import project as P, composite as Cmp
+    out = {}
+    tiny_scene, tiny_cams = scenes.tiny_workload()
+    cases = (("tiny_10k_256x256", tiny_scene, tiny_cams[0], None),
+             ("1m_1920x1080", scenes.scene_1m(), scenes.scene_orbit(32, 1920, 1080)[0], 256))
+    for name, scene, cam, sample in cases:
+        t0 = time.perf_counter()
+        proj = P.project(scene, cam)
+        cand = Cmp.tile_candidates(proj)
+        t_proj = time.perf_counter() - t0
+        n_tiles = cand[0] * cand[1]
+        _ORACLE["cfg"] = {"proj": proj, "cand": cand}
+        g = np.random.default_rng(1)
+        row = {"tiles": n_tiles, "projection_s_1core": round(t_proj, 3)}
+        for workers in (1, cores):
+            per = n_tiles if sample is None else sample
+            if sample is None:
+                chunks = np.array_split(np.arange(n_tiles), workers)
+            else:
+                chunks = [g.choice(n_tiles, per, replace=False) for _ in range(workers)]
+            t0 = time.perf_counter()
+            if workers == 1:
+                _config_tile_chunk(chunks[0])
+            else:
+                with mp.get_context("fork").Pool(workers) as pool:
+                    pool.map(_config_tile_chunk, chunks, chunksize=1)
+            t_tiles = time.perf_counter() - t0
+            tiles_done = n_tiles if sample is None else per * workers
+            # the projection splits over the workers like the tiles do
+            frame_s = t_proj / workers + t_tiles * n_tiles / tiles_done
+            row[f"frames_per_s_{'1core' if workers == 1 else 'all_cores'}"] = round(1.0 / frame_s, 5)
+        row["sample"] = ("whole frame" if sample is None else
+                         f"full projection (timed on one core, divided by the workers) + {sample} sampled tiles per "
+                         f"worker, scaled to {n_tiles} tiles")
+        out[name] = row
+    return out
+
+
+def run_oracle_subprocess(steps: int, warmup: int, cores: int = 1, configs: bool = False):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-steps", str(steps),
-                          "--warmup", str(warmup)], env=env, capture_output=True, text=True, timeout=1800)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-steps", str(steps), "--warmup", str(warmup),
+           "--oracle-cores", str(cores)] + (["--oracle-configs"] if configs else [])
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample_desc(steps):
-    return (f"per step: FP64 projection + tile binning of 1/{ORACLE_FRACTION} of the 5.8M gaussians + {ORACLE_TILES} "
-            f"sampled 8x8 tiles of one 1080p view; {steps} steps; frame time = mean step x {ORACLE_FRACTION} "
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_desc(steps, cores=1):
+    return (f"per step and worker ({cores} worker{'s' if cores > 1 else ''}, one per host core): FP64 projection + "
+            f"tile binning of 1/{ORACLE_FRACTION} of the 5.8M gaussians + {ORACLE_TILES} sampled 8x8 tiles of one "
+            f"1080p view; {steps} steps; frame time = mean step x {ORACLE_FRACTION} / {cores} "
             f"({ORACLE_FRACTION * ORACLE_TILES} tiles ~ the 32,400 of a frame)")
 
 
@@ -329,8 +442,9 @@ def measured_traffic(stage: str):
     return MEASURED_TRAFFIC["bytes"].get(stage)
 
 
-def roofline(stage_ms, stats0, n, pk, clock_mhz):
-    """Roofline of the stage that takes the most time per step."""
+def roofline(stage_ms, stats0, n, pk, clock_mhz, sms):
+    """Roofline of the stage that takes the most time per step; `sms` is the
+    device's multiprocessor count."""
     hbm_peak = pk["hbm_gbs"]
     K = 16
     vis = statistics.mean(s["n_visible"] for s in stats0)
@@ -338,7 +452,7 @@ def roofline(stage_ms, stats0, n, pk, clock_mhz):
     proj_bytes = n * (44 + 12 * K) + vis * (16 + 4 + 48) + vis_bits
     pairs = statistics.mean(s["n_pairs"] for s in stats0)
     evals = statistics.mean(s["raster_evals"] for s in stats0)
-    alu_peak = 152 * FP32_LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12  # T FP32-pipe ops/s
+    alu_peak = sms * FP32_LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12  # T FP32-pipe ops/s
     table = {
         "project": {"bound": "hbm", "units": proj_bytes, "peak": hbm_peak, "unit": "GB/s",
                     "per_unit": "bytes: 236 read per gaussian + 68 written per visible (view, gaussian): "
@@ -379,25 +493,18 @@ def serving_run(higs, ctx, gscenes, seconds, seed=0, opts=None):
     import torch
     from paper_2606_00352_gb300 import scenes
     rng = np.random.default_rng(seed)
-    srv = higs.Server(ctx, max_inflight=4, max_views_per_launch=8, mem_budget_bytes=64 << 30, opts=opts)
+    # every slot is sized when the scenes are added for the largest launch
+    # (8 views at 3840 x 2160 of the largest scene), so no slot grows its
+    # workspace while serving; the warm-up is one launch per slot
+    big = max(SERVE_RES, key=lambda r: r[0] * r[1])
+    srv = higs.Server(ctx, max_inflight=4, max_views_per_launch=8, mem_budget_bytes=64 << 30, opts=opts,
+                      presize=big)
     sids = [srv.add_scene(g) for g in gscenes]
     pool = [torch.empty(3840 * 2160 * 3, device="cuda") for _ in range(48)]
     poses = {r: scenes.scene_orbit(N_POSES, r[0], r[1]) for r in SERVE_RES}
-    # warm the slots' workspaces at every resolution, then with bursts of the
-    # largest batch (max_views_per_launch views at the largest resolution of
-    # one scene, submitted together so that they share launches) over every
-    # pose, so that no slot grows its workspace inside the timed rates (a
-    # growth reallocates and re-renders, a stall of tens of milliseconds)
-    warm = [srv.submit(sids[k % len(sids)], poses[SERVE_RES[k % 3]][k], pool[k]) for k in range(12)]
+    warm = [srv.submit(sids[k % len(sids)], poses[SERVE_RES[k % 3]][k], pool[k]) for k in range(4)]
     for rid in warm:
         srv.wait(rid)
-    big = max(SERVE_RES, key=lambda r: r[0] * r[1])
-    for _ in range(2):
-        for sid in sids:
-            for k0 in range(0, N_POSES, 32):
-                burst = [srv.submit(sid, poses[big][k0 + k], pool[k]) for k in range(32)]
-                for rid in burst:
-                    srv.wait(rid)
     rows = []
     for rate in SERVE_RATES:
         srv.reset_stats()
@@ -524,7 +631,8 @@ def gpu_arm(args):
 
     stage_ms = {k: statistics.mean(s["ms_" + k] for s in stats) for k in
                 ("project", "partition", "sort", "raster", "merge")}
-    top, rl = roofline(stage_ms, stats, gs.n, pk, clocks.get("sm_mhz") or pk["sm_max_mhz"])
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    top, rl = roofline(stage_ms, stats, gs.n, pk, clocks.get("sm_mhz") or pk["sm_max_mhz"], sms)
 
     # the same workload with the SH coefficients stored in half precision
     # (236 -> 140 bytes read per gaussian) or in the 32-byte packed form
@@ -617,12 +725,30 @@ def gpu_arm(args):
     e2e = {"value": round(sum_over_ranks(e2e_steps * VIEWS, world) / e2e_t, 2), "unit": UNIT,
            "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
 
+    # one profiled frame: raster phase cycles and the intrinsic per-pixel work
+    pst = higs.State(ctx)
+    popts_prof = higs.Options(path=higs.PATH_HIGS, macro_w=opts.macro_w, macro_h=opts.macro_h,
+                              batch_cap=opts.batch_cap, bin_test=opts.bin_test, flags=higs.FLAG_PROFILE)
+    higs.render(gs, pose_batch(cams, 0, rank), popts_prof, state=pst, stream=stream, with_T=False)
+    prof = pst.stats()
+    pst.close()
+
     if rank != 0:
         return
-    cpu = None
+    cpu, amb_stats = None, None
     if world == 1 and not args.skip_cpu:
-        r = run_oracle_subprocess(steps=8, warmup=1)
-        cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": oracle_sample_desc(8)}
+        # the oracle on every host core (the headline baseline), one core, and
+        # the tiny and 1M configurations on one and on all cores
+        cores = host_cores()
+        r = run_oracle_subprocess(steps=4, warmup=1, cores=cores, configs=True)
+        r1 = run_oracle_subprocess(steps=4, warmup=1, cores=1)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": oracle_sample_desc(4, cores),
+               "one_core": {"value": r1["value"], "unit": UNIT, "cores": 1, "sample": oracle_sample_desc(4, 1)},
+               "host_cores": os.cpu_count(), "configs": r.get("configs")}
+        amb_stats = {"decision_ambiguous_pixels": r["ambiguous_pixels"], "oracle_sampled_pixels": r["sampled_pixels"],
+                     "decision_ambiguous_fraction": round(r["ambiguous_pixels"] / max(1, r["sampled_pixels"]), 6),
+                     "bands_q_alpha_T": list(AMB_BANDS)}
     s0 = stats
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -631,7 +757,9 @@ def gpu_arm(args):
         "config": workload_config() | {"macro_tile": f"{opts.macro_w}x{opts.macro_h}", "batch_cap": opts.batch_cap,
                                        "bin_test": args.bin, "scene_order": args.order},
         "roofline": {k: v for k, v in rl[top].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
-        | {"kernel": top, "traffic": rl[top]["traffic"], "peak_source": pk["source"]},
+        | {"kernel": top, "traffic": rl[top]["traffic"], "peak_source": pk["source"], "sms": sms,
+           "peak_derivation": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {pk['sm_max_mhz']:.0f} MHz"
+           if rl[top]["bound"] == "alu" else "measured copy bandwidth"},
         "stages": rl | {"merge": {"ms": round(stage_ms["merge"], 4)}},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -650,7 +778,13 @@ def gpu_arm(args):
             "replays_per_step": int(statistics.mean(s["n_replays"] for s in s0)),
             "raster_evals_per_step": int(statistics.mean(s["raster_evals"] for s in s0)),
             "visible_per_step": int(statistics.mean(s["n_visible"] for s in s0)),
-        },
+            "pixel_support_evals_first_step": prof["pixel_support_evals"],
+            "pixel_contrib_evals_first_step": prof["pixel_contrib_evals"],
+            "raster_evals_first_step": prof["raster_evals"],
+            "intrinsic_share_of_raster_evals": round(prof["pixel_support_evals"] / max(1, prof["raster_evals"]), 4),
+            "raster_phase_cycles_first_step": dict(zip(("gather", "masks", "chain_wait", "blend_warps",
+                                                        "end_barrier_warps", "units"), prof["raster_cycles"])),
+        } | (amb_stats or {}),
         "serving_p99_ms": next((r["p99_ms"] for r in serving["rows"] if r["offered_req_per_s"] == 1000), None)
         if serving else None,
         "serving": serving,
@@ -707,14 +841,15 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    r = run_oracle_subprocess(steps=args.steps, warmup=args.warmup)
+    cores = host_cores()
+    r = run_oracle_subprocess(steps=args.steps, warmup=args.warmup, cores=cores)
     fps = r["value"]
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": int(args.gpus),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": fps, "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": oracle_sample_desc(args.steps)},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "kind": "oracle", "cores": cores,
+                             "sample": oracle_sample_desc(args.steps, cores)},
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -731,6 +866,8 @@ def main():
     ap.add_argument("--skip-train", action="store_true")
     ap.add_argument("--skip-tune", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-cores", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-configs", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--case", default="", choices=["", "1m", "1m-plain", "5m8", "train1m"],
                     help="small profiling case instead of the benchmark")
     ap.add_argument("--profile", action="store_true", help="count rasteriser phase cycles (profiling case)")
@@ -743,10 +880,15 @@ def main():
     if args.warmup < 3 and not args.oracle_steps and not args.case:
         args.warmup = 3
     if args.oracle_steps:
-        times = oracle_sample_steps(args.oracle_steps, args.warmup)
+        c = max(1, args.oracle_cores)
+        times = oracle_sample_steps(args.oracle_steps, args.warmup, cores=c)
         ms = statistics.mean(times) * 1e3
-        print(json.dumps({"value": 1.0 / (statistics.mean(times) * ORACLE_FRACTION), "ms_per_step": ms,
-                          "times": times}))
+        amb, px = oracle_sample_steps.ambiguous
+        out = {"value": c / (statistics.mean(times) * ORACLE_FRACTION), "ms_per_step": ms, "cores": c,
+               "times": times, "ambiguous_pixels": amb, "sampled_pixels": px}
+        if args.oracle_configs:
+            out["configs"] = oracle_configs(c)
+        print(json.dumps(out))
         return
     if args.case == "train1m":
         profile_train_case(args)

@@ -174,7 +174,7 @@ enum {
   HG_FLAG_PROFILE = 16,    /* count rasteriser phase cycles (hg_frame_stats) */
   HG_FLAG_FP16 = 32        /* half-precision rasterisation (Sec. 3.5, 4.5): alpha of
                               the two pixels a thread owns in half2 arithmetic from
-                              prescaled Cholesky factors and macro-tile-relative
+                              prescaled Cholesky factors and macro-tile-centred
                               coordinates; transmittance and colour stay float32 with
                               exact per-pixel termination.  Its own tolerance (PSNR,
                               not the float32 bounds); not with save_for_backward */
@@ -209,6 +209,11 @@ typedef struct {
    * [0] record gather, [1] tile masks + queue, [2] chain wait, and over warps
    * of [3] tile blending, [4] end-of-unit barrier; [5] units */
   int64_t raster_cycles[6];
+  /* with HG_FLAG_PROFILE (float32 rasteriser): the intrinsic per-pixel work,
+   * the (pixel, gaussian) evaluations a per-pixel renderer cannot skip
+   * (support q <= 9 while the pixel is live, up to and including its stop),
+   * and those of them that contributed a colour */
+  int64_t pixel_support_evals, pixel_contrib_evals;
 } hg_frame_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -216,9 +221,34 @@ const char* hg_status_str(hg_status s);
 const char* hg_last_error(void);
 const char* hg_version(void);
 
-/* Create a context on `device`; `alloc` may be NULL (cudaMalloc). */
+/* Create a context on `device`; `alloc` may be NULL (cudaMalloc).  An
+ * allocator whose alloc returns NULL makes the call that needed the memory
+ * return HG_ERR_OOM (nothing is left half-built). */
 hg_status hg_ctx_create(int device, const hg_allocator* alloc, hg_ctx** out);
 void hg_ctx_destroy(hg_ctx* ctx);
+
+/* Limits of the bounded device waits of frames enqueued on this context
+ * after the call (failure detection, not part of the paper).
+ *  wait_polls   polls of an mbarrier (the TMA stagings of the projection,
+ *               the rasteriser and the backward) or of a onesweep look-back
+ *               word before the wait gives up: the frame stops with
+ *               HG_ERR_DEVICE_TIMEOUT (the CTA still waits, with the
+ *               default limit, for the copies it issued, so nothing is left
+ *               in flight) and later kernels of the frame return at once;
+ *               default 2^24.
+ *  chain_polls  polls of the batch chain (Sec. 3.4 ordered merge: the unit of
+ *               rank k waiting for rank k-1 of its macro-tile) before the
+ *               unit renders unchained from T = 1 and the merge composites
+ *               it by Eq. 1 with replay (same image); default 200000
+ *               (about 0.1 s).  A frame saved for the backward cannot
+ *               render unchained: there a chain wait that gives up ends the
+ *               frame with HG_ERR_DEVICE_TIMEOUT.  The backward's waits (its
+ *               staged copies, and batch j waiting for batches j+1.. of its
+ *               macro-tile) use wait_polls.
+ * 0 gives up at once (tests of the failure paths); a negative value
+ * restores the default.  Errors: HG_ERR_INVALID_ARG (NULL context, a value
+ * above 2^32 - 1). */
+hg_status hg_ctx_set_wait_limits(hg_ctx* ctx, int64_t wait_polls, int64_t chain_polls);
 
 /* ------------------------------------------------------------------ scene */
 /* Sec. 4.2 inputs.  Copies (borrow = 0) are enqueued on the legacy stream and
@@ -251,15 +281,23 @@ hg_status hg_render_splats(hg_ctx* ctx, const hg_splat* d_splats, int64_t n,
                            const hg_camera* cams, int n_views, const hg_render_opts* opts,
                            float* out_rgb, float* out_T, hg_state** state, void* stream);
 
-/* Backward of 0.5 ||C - C*||^2-style losses: given dL/dC (device, same layout
- * as out_rgb) of the frame saved in `state` (rendered with
- * save_for_backward), write dL/d(parameter) into the device arrays (same
- * shapes as the scene arrays, in the scene's stored order (hg_scene_order);
- * they are overwritten, not accumulated).  The
- * forward saved the (C, T) entering every (batch, tile) (the prefix of the
- * Eq. 1 scan, Sec. 6) and the final colours; every batch is replayed from
- * its prefix with the forward's arithmetic, so the suffix colour behind a
- * gaussian is C_final - C_<=i. */
+/* Backward of 0.5 ||C - C*||^2-style losses (the differentiable render that
+ * Sec. 6 sketches): given dL/dC (device, same layout as out_rgb) of the frame
+ * saved in `state` (rendered with save_for_backward), write dL/d(parameter)
+ * into the device arrays (same shapes as the scene arrays, in the scene's
+ * stored order (hg_scene_order); they are overwritten, not accumulated).
+ * The forward rendered every batch chained (save_for_backward refuses
+ * HG_FLAG_INDEPENDENT, and a chain wait that gives up ends that frame with
+ * HG_ERR_DEVICE_TIMEOUT) and saved, per pixel of every (batch, tile) it
+ * blended, the transmittance after the pixel's last contributing gaussian
+ * of the batch and that gaussian's index.  The backward walks the batches
+ * of each macro-tile from the last to the first and each batch back to
+ * front, recovering T_i = T_{i+1} / (1 - alpha_i) and accumulating the
+ * colour behind every gaussian from the back (starting at T_final bg), so
+ * no difference of pixel-sized colours enters a gradient.  Stream-ordered;
+ * its device status (a bounded wait that gave up: HG_ERR_DEVICE_TIMEOUT)
+ * is returned by the next hg_state_sync.  Errors: HG_ERR_INVALID_ARG (no
+ * saved frame, half or packed SH), HG_ERR_OOM, HG_ERR_CUDA. */
 hg_status hg_render_backward(hg_state* state, const float* dL_drgb,
                              float* d_means, float* d_log_scales, float* d_quats,
                              float* d_opacity_logits, float* d_sh, void* stream);
@@ -312,13 +350,22 @@ hg_status hg_state_sync(hg_state* state);
 hg_status hg_render_stats(hg_state* state, hg_frame_stats* out);
 
 /* Copy an intermediate buffer of the last frame to host memory (synchronises).
- * which: HG_BUF_SEG_OFF (uint32 [S+1]), HG_BUF_PAIR_KEYS (uint32 [P]),
+ * HiGS path: HG_BUF_SEG_OFF (uint32 [S+1]), HG_BUF_PAIR_KEYS (uint32 [P]),
  * HG_BUF_PAIR_IDS (uint32 [P]), HG_BUF_BATCHES (uint32 [N_R][3]: segment,
- * start, count), HG_BUF_SPLATS (hg_splat [V][n], needs HG_FLAG_KEEP_SPLATS),
- * HG_BUF_VIEW_SEG_BASE (uint32 [V+1]).  *bytes_needed receives the size; dst
- * may be NULL to query it. */
+ * start, count).  Plain path (Sec. 2 / 5 baseline): HG_BUF_PLAIN_KEYS (uint64
+ * [P] sorted keys, global render tile << 32 | depth key), HG_BUF_PLAIN_IDS
+ * (uint32 [P] record index v n + i), HG_BUF_TILE_RANGES (uint32 [tiles][2]
+ * [start, end) of every global render tile, 0 0 for an empty tile).  Both:
+ * HG_BUF_SPLATS (hg_splat [V][n], needs HG_FLAG_KEEP_SPLATS),
+ * HG_BUF_VIEW_SEG_BASE (uint32 [V+1]).  After hg_render_backward:
+ * HG_BUF_GRAD2D (float32 [V][n][9], the gradient with respect to each
+ * view's projected record: d mean2d x, y, d conic A, B, C of q = A dx^2 +
+ * 2 B dx dy + C dy^2, d opacity, d rgb).  A buffer of the other path (or a
+ * gradient before any backward) is HG_ERR_UNSUPPORTED.  *bytes_needed
+ * receives the size; dst may be NULL to query it. */
 enum { HG_BUF_SEG_OFF = 0, HG_BUF_PAIR_KEYS = 1, HG_BUF_PAIR_IDS = 2, HG_BUF_BATCHES = 3,
-       HG_BUF_SPLATS = 4, HG_BUF_VIEW_SEG_BASE = 5 };
+       HG_BUF_SPLATS = 4, HG_BUF_VIEW_SEG_BASE = 5, HG_BUF_PLAIN_KEYS = 6, HG_BUF_PLAIN_IDS = 7,
+       HG_BUF_TILE_RANGES = 8, HG_BUF_GRAD2D = 9 };
 hg_status hg_state_read(hg_state* state, int which, void* dst, size_t dst_bytes,
                         size_t* bytes_needed);
 
@@ -357,7 +404,12 @@ void hg_graph_destroy(hg_graph* graph);
  * holds is re-run after the slot reallocates (25% headroom), which delays
  * that launch and the device by the allocation; latency-sensitive callers
  * warm every slot with the largest launches they expect (max_views_per_launch
- * views at the largest resolution) before serving. */
+ * views at the largest resolution) before serving, or set presize_width /
+ * presize_height: registering a scene then sizes every slot for
+ * max_views_per_launch views of that resolution over the largest scene
+ * registered so far (pair capacity 3 n V, which covers the macro-tile pairs
+ * of the configs' scenes at 4K with headroom), so launches up to that size
+ * never grow a workspace on the request path. */
 typedef struct {
   int32_t max_inflight;          /* 1..64 launches on the device at once */
   int32_t max_views_per_launch;  /* 1..64 */
@@ -365,6 +417,8 @@ typedef struct {
   int32_t batch_window_us;       /* hold the oldest request up to this long while fewer than
                                     max_views_per_launch requests of its scene are pending
                                     (0: launch as soon as a slot is free) */
+  int32_t presize_width;         /* largest request resolution to size the slots for at */
+  int32_t presize_height;        /* hg_serve_add_scene (0 0: grow on demand) */
   int32_t pad;
   hg_render_opts opts;           /* render options of every launch (path HiGS) */
 } hg_serve_config;
@@ -425,20 +479,27 @@ hg_status hg_autotune(hg_scene* scene, const hg_camera* cams, int n_views, const
  * allocator's callback, or a host process that must not touch the device
  * heap while other work is in flight).  Its scratch (look-back words, digit
  * histograms, tile descriptors and a ping-pong copy of the pairs, about
- * 7 MB) is one fixed device array inside the library that every GPU which
- * loads the library holds until the process exits.
+ * 13 MB) is one fixed device array inside the library that every GPU which
+ * loads the library holds until the process exits.  Four stable radix passes
+ * over the values, then four over the keys, give the (key, value) order for
+ * any input (all keys equal included) in time linear in n_pairs.
  *  d_seg_off: device [n_seg + 1], non-decreasing, d_seg_off[0] = 0,
  *             d_seg_off[n_seg] = n_pairs (copied to the host and checked).
- *  d_keys_in / d_vals_in: device [n_pairs], not modified.
+ *  d_keys_in / d_vals_in: device [n_pairs], not modified unless they are
+ *             the outputs (in place: d_keys_out == d_keys_in and
+ *             d_vals_out == d_vals_in; every other overlap of the four
+ *             ranges is rejected with HG_ERR_INVALID_ARG).
  *  d_keys_out / d_vals_out: device [n_pairs], the sorted pairs.
  * Limits: n_pairs <= 524288 and n_seg <= 512; larger inputs are rejected
  * with HG_ERR_INVALID_ARG and a message, before any device work.
  * The first call on a device looks up the scratch array's device address
- * (with that device current); make that first call before any stream
- * capture.  Every call clears the parts of the array that must start at
- * zero; all calls share the array, so calls whose GPU work overlaps (other
- * threads, other streams) race and must be serialised by the caller.  The
- * call synchronises `stream` and returns the device status. */
+ * (with that device current).  Every call clears the parts of the array
+ * that must start at zero; all calls share the array, so calls whose GPU
+ * work overlaps (other threads, other streams) race and must be serialised
+ * by the caller.  The call synchronises `stream` (it reads d_seg_off and
+ * the device status back), so it cannot be recorded into a stream capture:
+ * on a capturing stream it returns HG_ERR_INVALID_ARG without enqueueing
+ * anything.  It returns the device status. */
 hg_status hg_segmented_sort_noalloc(const uint32_t* d_seg_off, int n_seg, int64_t n_pairs,
                                     const uint32_t* d_keys_in, const uint32_t* d_vals_in,
                                     uint32_t* d_keys_out, uint32_t* d_vals_out, void* stream);

@@ -239,6 +239,36 @@ def segments(views, width_height, bw, bh):
             "seg_base": bases, "n_seg": base}
 
 
+def plain_tile_pairs(views, width_height, tile: int = 8):
+    """Discrete stages of the plain per-tile path (the single-tile-size
+    baseline of Sec. 2 and 5): every (render tile, gaussian) pair of the
+    integer 3-sigma rectangle test at tile x tile pixels, over all views;
+    the global tile of view v is (tiles of views < v) + ty gw + tx.  Pairs
+    are ordered by the 64-bit key (global tile << 32 | depth key), then by
+    the record index v n + i (n gaussians per view).
+
+    views: list of (mx32, my32, radius, key); width_height: (W, H) per view.
+    Returns keys64 uint64 [P], ids int64 [P] (v n + i) and ranges int64
+    [tiles, 2]: [start, end) of each tile's pairs, (0, 0) for an empty tile.
+    """
+    seg, key, rid, base = [], [], [], 0
+    for v, (vw, (w, h)) in enumerate(zip(views, width_height)):
+        mx, my, r, k = vw[:4]
+        s, kk, i, nt = bin_pairs(mx, my, r, k, w, h, tile, tile, base)
+        seg.append(s), key.append(kk), rid.append(i + v * len(r))
+        base += nt
+    seg = np.concatenate(seg) if seg else np.zeros(0, np.int64)
+    key = np.concatenate(key) if key else np.zeros(0, np.uint32)
+    rid = np.concatenate(rid) if rid else np.zeros(0, np.int64)
+    o = np.lexsort((rid, key, seg))
+    seg, key, rid = seg[o], key[o], rid[o]
+    keys64 = (seg.astype(np.uint64) << np.uint64(32)) | key.astype(np.uint64)
+    start = np.searchsorted(seg, np.arange(base), side="left")
+    end = np.searchsorted(seg, np.arange(base), side="right")
+    ranges = np.stack([np.where(end > start, start, 0), np.where(end > start, end, 0)], axis=1)
+    return keys64, rid, ranges.astype(np.int64)
+
+
 def batches(seg_off: np.ndarray, cap: int):
     """Batch table [(segment, start, count)] in segment-major order and the
     first batch index of every segment (length S+1)."""

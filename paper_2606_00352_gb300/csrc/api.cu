@@ -148,6 +148,16 @@ extern "C" void hg_ctx_destroy(hg_ctx* ctx) {
   delete ctx;
 }
 
+extern "C" hg_status hg_ctx_set_wait_limits(hg_ctx* ctx, int64_t wait_polls, int64_t chain_polls) {
+  if (!ctx || wait_polls > (int64_t)0xffffffffu || chain_polls > (int64_t)0xffffffffu) {
+    hg_set_error("hg_ctx_set_wait_limits: bad arguments");
+    return HG_ERR_INVALID_ARG;
+  }
+  ctx->wait_polls = wait_polls < 0 ? SPIN_LIMIT : (uint32_t)wait_polls;
+  ctx->chain_polls = chain_polls < 0 ? CHAIN_SPIN : (uint32_t)chain_polls;
+  return HG_OK;
+}
+
 // ---------------------------------------------------------------- scenes
 extern "C" hg_status hg_create_scene(hg_ctx* ctx, const hg_scene_desc* d, hg_scene** out) {
   if (!ctx || !d || !out || d->n < 0 || d->sh_degree < 0 || d->sh_degree > 3 || d->sh_storage < HG_SH_F32 ||
@@ -353,6 +363,8 @@ static bool valid_opts(const hg_render_opts* o, std::string& why) {
   if (o->bin_test != HG_BIN_RECT && o->bin_test != HG_BIN_ELLIPSE) return why = "bin_test", false;
   if ((o->flags & HG_FLAG_FP16) && o->save_for_backward)
     return why = "HG_FLAG_FP16 does not save for the backward (float32 only)", false;
+  if ((o->flags & HG_FLAG_INDEPENDENT) && o->save_for_backward)
+    return why = "save_for_backward needs the chained schedule (not HG_FLAG_INDEPENDENT)", false;
   return true;
 }
 
@@ -416,11 +428,9 @@ static void sizes_from_counters(hg_state* s, const FrameGeom& g, const hg_render
   (void)g;
 }
 
-hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o, const FrameGeom& g,
-                               float* out_rgb, float* out_T, cudaStream_t st) {
-  const long long n = in.n;
+hg_status ensure_workspace(hg_state* s, long long n, const FrameGeom& g, const hg_render_opts* o,
+                           cudaStream_t st) {
   const int V = g.V;
-  const bool timing = (o->flags & HG_FLAG_TIMING) != 0;
   hg_status r;
   // capacities (first frame: estimates; later frames: measured + slack)
   if (s->cap_pairs == 0) s->cap_pairs = (size_t)std::max<long long>(1 << 20, 2 * n * V);
@@ -444,40 +454,6 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   ENS(B_REC, sizeof(float4) * REC_F4 * n * V);
   ENS(B_VIS, sizeof(uint32_t) * vis_words * V);
   if (o->flags & HG_FLAG_KEEP_SPLATS) ENS(B_SPLATS, sizeof(hg_splat) * n * V);
-  FrameCounters* fc = (FrameCounters*)s->bufs[B_FC].p;
-  ViewDesc* views = (ViewDesc*)s->bufs[B_VIEWS].p;
-  if (timing) HG_TRY(record_stage(s->ev[0], st), "stage event 0");
-  HG_TRY(cudaMemsetAsync(fc, 0, sizeof(FrameCounters), st), "memset counters");
-  HG_TRY(cudaMemcpyAsync(views, s->views_host, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st), "upload views");
-  ProjectArgs pj{};
-  pj.n = n;
-  pj.views = views;
-  pj.n_views = V;
-  pj.vis_words = (long long)vis_words;
-  pj.bin = (uint4*)s->bufs[B_BIN].p;
-  pj.dkeys = (uint32_t*)s->bufs[B_DKEY].p;
-  pj.rec = (float4*)s->bufs[B_REC].p;
-  pj.vis = (uint32_t*)s->bufs[B_VIS].p;
-  pj.bin_mode = o->path == HG_PATH_PLAIN ? BIN_CLASSIC
-                                         : (o->bin_test == HG_BIN_ELLIPSE ? BIN_CELLS_ELLIPSE : BIN_CELLS_RECT);
-  pj.macro_w = o->macro_w;
-  pj.macro_h = o->macro_h;
-  pj.fc = fc;
-  if (in.splats) {
-    HG_TRY(launch_splats_to_records(in.splats, n, V, (long long)vis_words, pj, st), "splats to records");
-  } else {
-    pj.means = in.scene->arr[0];
-    pj.log_scales = in.scene->arr[1];
-    pj.quats = in.scene->arr[2];
-    pj.opacity_logits = in.scene->arr[3];
-    pj.sh = in.scene->arr[4];
-    pj.sh_storage = in.scene->sh_storage;
-    pj.sh_scale2 = in.scene->sh_scale ? in.scene->sh_scale + SH_CODEC_CH : nullptr;
-    pj.splats = (o->flags & HG_FLAG_KEEP_SPLATS) ? (hg_splat*)s->bufs[B_SPLATS].p : nullptr;
-    HG_TRY(launch_project(pj, in.scene->deg, st), "project");
-  }
-  if (timing) HG_TRY(record_stage(s->ev[1], st), "stage event 1");
-
   if (o->path == HG_PATH_PLAIN) {
     ENS(P_COUNTS, sizeof(uint32_t) * n * V);
     ENS(P_OFFS, sizeof(uint32_t) * (n * V + 1));
@@ -488,38 +464,8 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ENS(P_VALS, sizeof(uint32_t) * s->cap_plain_pairs);
     ENS(P_VALS2, sizeof(uint32_t) * s->cap_plain_pairs);
     ENS(P_RANGES, sizeof(uint2) * g.total_tiles);
-    ENS(P_LOOKBACK, sizeof(uint32_t) * 256 * s->cap_plain_tiles);
+    ENS(P_LOOKBACK, sizeof(uint32_t) * 8 * 256 * s->cap_plain_tiles);  // one region per digit pass
     ENS(P_DHIST, sizeof(uint32_t) * 8 * 256);
-    PlainArgs pa{};
-    pa.bin = (const uint4*)s->bufs[B_BIN].p;
-    pa.rec = (const float4*)s->bufs[B_REC].p;
-    pa.n = n;
-    pa.vis = (const uint32_t*)s->bufs[B_VIS].p;
-    pa.vis_words = vis_words;
-    pa.views = views;
-    pa.n_views = V;
-    pa.total_tiles = g.total_tiles;
-    pa.counts = (uint32_t*)s->bufs[P_COUNTS].p;
-    pa.offsets = (uint32_t*)s->bufs[P_OFFS].p;
-    pa.scan_tmp = (uint32_t*)s->bufs[P_SCAN].p;
-    pa.keys = (unsigned long long*)s->bufs[P_KEYS].p;
-    pa.vals = (uint32_t*)s->bufs[P_VALS].p;
-    pa.keys_alt = (unsigned long long*)s->bufs[P_KEYS2].p;
-    pa.vals_alt = (uint32_t*)s->bufs[P_VALS2].p;
-    pa.ranges = (uint2*)s->bufs[P_RANGES].p;
-    pa.lookback = (uint32_t*)s->bufs[P_LOOKBACK].p;
-    pa.digit_hist = (uint32_t*)s->bufs[P_DHIST].p;
-    pa.cap_pairs = (uint32_t)std::min<size_t>(s->cap_plain_pairs, 0xffffffffu);
-    pa.cap_tiles = (uint32_t)s->cap_plain_tiles;
-    for (int k = 0; k < 3; ++k) pa.bg[k] = o->bg[k];
-    pa.out_rgb = out_rgb;
-    pa.out_T = out_T;
-    pa.fc = fc;
-    unsigned long long* sk = nullptr;
-    uint32_t* sv = nullptr;
-    HG_TRY(launch_plain(pa, st, &sk, &sv), "plain path");
-    if (timing)
-      for (int k = 2; k < 6; ++k) HG_TRY(record_stage(s->ev[k], st), "stage event");
   } else {
     ENS(B_HIST, sizeof(uint16_t) * (size_t)n_pb * g.S + 16);
     ENS(B_COLPRE, sizeof(uint32_t) * (size_t)n_pb * g.S + 16);
@@ -543,12 +489,97 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ENS(B_MODE, sizeof(uint32_t) * s->cap_batches);
     ENS(B_TSTATE, sizeof(float4) * TILE_PX * (size_t)g.total_tiles);
     ENS(B_TRANK, sizeof(uint32_t) * g.total_tiles);
-    ENS(B_SEGHIST, sizeof(uint32_t) * 4 * 256 * s->cap_big_segs);
-    ENS(B_LOOKBACK, sizeof(uint32_t) * 256 * s->cap_tiles);
+    ENS(B_SEGHIST, sizeof(uint32_t) * 8 * 256 * s->cap_big_segs);
+    ENS(B_LOOKBACK, sizeof(uint32_t) * 8 * 256 * s->cap_tiles);  // one region per digit pass
     if (o->save_for_backward) {
-      ENS(B_PREFIX, sizeof(float4) * TILE_PX * M * s->cap_batches);
-      ENS(B_FINAL, sizeof(float4) * (size_t)g.pixels);
+      ENS(B_EXIT, sizeof(float4) * TILE_PX * M * s->cap_batches);
+      ENS(B_EXITLAST, sizeof(uint16_t) * TILE_PX * M * s->cap_batches);
     }
+  }
+#undef ENS
+  return HG_OK;
+}
+
+hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o, const FrameGeom& g,
+                               float* out_rgb, float* out_T, cudaStream_t st) {
+  const long long n = in.n;
+  const int V = g.V;
+  const bool timing = (o->flags & HG_FLAG_TIMING) != 0;
+  hg_status r = ensure_workspace(s, n, g, o, st);
+  if (r != HG_OK) return r;
+  const size_t vis_words = (size_t)((n + 31) / 32);
+  const int M = o->macro_w * o->macro_h;
+  const int n_pb = (int)((n + BP - 1) / BP);
+  FrameCounters* fc = (FrameCounters*)s->bufs[B_FC].p;
+  ViewDesc* views = (ViewDesc*)s->bufs[B_VIEWS].p;
+  if (timing) HG_TRY(record_stage(s->ev[0], st), "stage event 0");
+  HG_TRY(cudaMemsetAsync(fc, 0, sizeof(FrameCounters), st), "memset counters");
+  HG_TRY(cudaMemcpyAsync(views, s->views_host, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st), "upload views");
+  ProjectArgs pj{};
+  pj.n = n;
+  pj.views = views;
+  pj.n_views = V;
+  pj.vis_words = (long long)vis_words;
+  pj.bin = (uint4*)s->bufs[B_BIN].p;
+  pj.dkeys = (uint32_t*)s->bufs[B_DKEY].p;
+  pj.rec = (float4*)s->bufs[B_REC].p;
+  pj.vis = (uint32_t*)s->bufs[B_VIS].p;
+  pj.bin_mode = o->path == HG_PATH_PLAIN ? BIN_CLASSIC
+                                         : (o->bin_test == HG_BIN_ELLIPSE ? BIN_CELLS_ELLIPSE : BIN_CELLS_RECT);
+  pj.macro_w = o->macro_w;
+  pj.macro_h = o->macro_h;
+  pj.wait_polls = s->ctx->wait_polls;
+  pj.fc = fc;
+  if (in.splats) {
+    HG_TRY(launch_splats_to_records(in.splats, n, V, (long long)vis_words, pj, st), "splats to records");
+  } else {
+    pj.means = in.scene->arr[0];
+    pj.log_scales = in.scene->arr[1];
+    pj.quats = in.scene->arr[2];
+    pj.opacity_logits = in.scene->arr[3];
+    pj.sh = in.scene->arr[4];
+    pj.sh_storage = in.scene->sh_storage;
+    pj.sh_scale2 = in.scene->sh_scale ? in.scene->sh_scale + SH_CODEC_CH : nullptr;
+    pj.splats = (o->flags & HG_FLAG_KEEP_SPLATS) ? (hg_splat*)s->bufs[B_SPLATS].p : nullptr;
+    HG_TRY(launch_project(pj, in.scene->deg, st), "project");
+  }
+  if (timing) HG_TRY(record_stage(s->ev[1], st), "stage event 1");
+
+  if (o->path == HG_PATH_PLAIN) {
+    PlainArgs pa{};
+    pa.bin = (const uint4*)s->bufs[B_BIN].p;
+    pa.rec = (const float4*)s->bufs[B_REC].p;
+    pa.n = n;
+    pa.vis = (const uint32_t*)s->bufs[B_VIS].p;
+    pa.vis_words = vis_words;
+    pa.views = views;
+    pa.n_views = V;
+    pa.total_tiles = g.total_tiles;
+    pa.counts = (uint32_t*)s->bufs[P_COUNTS].p;
+    pa.offsets = (uint32_t*)s->bufs[P_OFFS].p;
+    pa.scan_tmp = (uint32_t*)s->bufs[P_SCAN].p;
+    pa.keys = (unsigned long long*)s->bufs[P_KEYS].p;
+    pa.vals = (uint32_t*)s->bufs[P_VALS].p;
+    pa.keys_alt = (unsigned long long*)s->bufs[P_KEYS2].p;
+    pa.vals_alt = (uint32_t*)s->bufs[P_VALS2].p;
+    pa.ranges = (uint2*)s->bufs[P_RANGES].p;
+    pa.lookback = (uint32_t*)s->bufs[P_LOOKBACK].p;
+    pa.digit_hist = (uint32_t*)s->bufs[P_DHIST].p;
+    pa.cap_pairs = (uint32_t)std::min<size_t>(s->cap_plain_pairs, 0xffffffffu);
+    pa.cap_tiles = (uint32_t)s->cap_plain_tiles;
+    pa.wait_polls = s->ctx->wait_polls;
+    for (int k = 0; k < 3; ++k) pa.bg[k] = o->bg[k];
+    pa.out_rgb = out_rgb;
+    pa.out_T = out_T;
+    pa.fc = fc;
+    unsigned long long* sk = nullptr;
+    uint32_t* sv = nullptr;
+    HG_TRY(launch_plain(pa, st, &sk, &sv), "plain path");
+    s->plain_keys = sk;
+    s->plain_vals = sv;
+    if (timing)
+      for (int k = 2; k < 6; ++k) HG_TRY(record_stage(s->ev[k], st), "stage event");
+  } else {
     PartitionArgs pa{};
     pa.bin = (const uint4*)s->bufs[B_BIN].p;
     pa.dkeys = (const uint32_t*)s->bufs[B_DKEY].p;
@@ -581,6 +612,7 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     pa.cap_batches = (uint32_t)s->cap_batches;
     pa.cap_tiles = (uint32_t)s->cap_tiles;
     pa.cap_big_segs = (uint32_t)s->cap_big_segs;
+    pa.seg_hist = (uint32_t*)s->bufs[B_SEGHIST].p;
     pa.fc = fc;
     if (n > 0) HG_TRY(launch_partition(pa, st), "partition");
     if (timing) HG_TRY(record_stage(s->ev[2], st), "stage event 2");
@@ -600,6 +632,10 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     sa.lookback = (uint32_t*)s->bufs[B_LOOKBACK].p;
     sa.cap_tiles = pa.cap_tiles;
     sa.cap_big_segs = pa.cap_big_segs;
+    sa.wait_polls = s->ctx->wait_polls;
+    // the last completed frame of this state had no segment above the
+    // shared-memory tiers: a small onesweep grid (still correct if this one has)
+    sa.os_ctas = s->fc_host->n_big_tiles == 0 ? 8 : 0;
     sa.fc = fc;
     if (n > 0) HG_TRY(launch_sort(sa, st, s->has_sort_streams ? &s->sort_streams : nullptr), "sort");
     if (timing) HG_TRY(record_stage(s->ev[3], st), "stage event 3");
@@ -626,7 +662,8 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.mode = (uint32_t*)s->bufs[B_MODE].p;
     ra.tile_state = (float4*)s->bufs[B_TSTATE].p;
     ra.tile_rank = (uint32_t*)s->bufs[B_TRANK].p;
-    ra.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
+    ra.exitrec = o->save_for_backward ? (float4*)s->bufs[B_EXIT].p : nullptr;
+    ra.exitlast = o->save_for_backward ? (uint16_t*)s->bufs[B_EXITLAST].p : nullptr;
     ra.persistent_ctas = 0;
     ra.independent = (o->flags & HG_FLAG_INDEPENDENT) ? 1 : 0;
     ra.fp16 = (o->flags & HG_FLAG_FP16) ? 1 : 0;
@@ -636,6 +673,8 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     ra.out_T = out_T;
     for (int c = 0; c < 3; ++c) ra.bg[c] = o->bg[c];
     ra.profile = (o->flags & HG_FLAG_PROFILE) ? 1 : 0;
+    ra.wait_polls = s->ctx->wait_polls;
+    ra.chain_polls = s->ctx->chain_polls;
     ra.fc = fc;
     if (n > 0) HG_TRY(launch_raster(ra, st), "raster");
     if (timing) HG_TRY(record_stage(s->ev[4], st), "stage event 4");
@@ -660,8 +699,6 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     for (int k = 0; k < 3; ++k) ma.bg[k] = o->bg[k];
     ma.out_rgb = out_rgb;
     ma.out_T = out_T;
-    ma.prefix = o->save_for_backward ? (float4*)s->bufs[B_PREFIX].p : nullptr;
-    ma.final_px = o->save_for_backward ? (float4*)s->bufs[B_FINAL].p : nullptr;
     ma.fc = fc;
     if (n == 0) {
       // empty scene: the first batch table is all zero, merge writes background
@@ -671,7 +708,6 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
     if (timing) HG_TRY(record_stage(s->ev[5], st), "stage event 5");
   }
   HG_TRY(cudaMemcpyAsync(s->fc_host, fc, sizeof(FrameCounters), cudaMemcpyDeviceToHost, st), "read counters");
-#undef ENS
   return HG_OK;
 }
 
@@ -686,6 +722,8 @@ hg_status run_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o,
   s->scene = in.scene;
   s->last_stream = st;
   s->has_frame = true;
+  s->has_grad2d = false;
+  ++s->frame_id;
   const bool async = (o->flags & HG_FLAG_ASYNC) != 0;
   for (int attempt = 0; attempt < 4; ++attempt) {
     r = enqueue_frame(s, in, o, g, out_rgb, out_T, st);
@@ -785,6 +823,8 @@ extern "C" hg_status hg_render_stats(hg_state* s, hg_frame_stats* out) {
   out->raster_evals = (int64_t)f.raster_evals;
   out->status = f.status;
   for (int k = 0; k < 6; ++k) out->raster_cycles[k] = (int64_t)f.raster_cycles[k];
+  out->pixel_support_evals = (int64_t)f.pixel_support_evals;
+  out->pixel_contrib_evals = (int64_t)f.pixel_contrib_evals;
   if (s->opts.flags & HG_FLAG_TIMING) {
     float ms[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&ms[k], s->ev[k], s->ev[k + 1]);
@@ -842,6 +882,22 @@ extern "C" hg_status hg_state_read(hg_state* s, int which, void* dst, size_t dst
       if (!(s->opts.flags & HG_FLAG_KEEP_SPLATS)) return HG_ERR_UNSUPPORTED;
       bytes = sizeof(hg_splat) * s->n * g.V;
       src = s->bufs[B_SPLATS].p;
+      break;
+    case HG_BUF_PLAIN_KEYS:
+    case HG_BUF_PLAIN_IDS:
+      if (higs) return HG_ERR_UNSUPPORTED;
+      bytes = (which == HG_BUF_PLAIN_KEYS ? sizeof(unsigned long long) : sizeof(uint32_t)) * f.n_pairs;
+      src = which == HG_BUF_PLAIN_KEYS ? (const void*)s->plain_keys : (const void*)s->plain_vals;
+      break;
+    case HG_BUF_TILE_RANGES:
+      if (higs) return HG_ERR_UNSUPPORTED;
+      bytes = sizeof(uint32_t) * 2 * (size_t)g.total_tiles;
+      src = s->bufs[P_RANGES].p;
+      break;
+    case HG_BUF_GRAD2D:
+      if (!s->has_grad2d) return HG_ERR_UNSUPPORTED;
+      bytes = sizeof(float) * 9 * (size_t)s->n * g.V;
+      src = s->bufs[G_DMEANS2].p;
       break;
     case HG_BUF_VIEW_SEG_BASE: {
       bytes = sizeof(uint32_t) * (g.V + 1);

@@ -1,15 +1,23 @@
 // Backward of the render path (the paper sketches it in Sec. 6; it is not
 // part of the paper's implementation).
 //
-//  k_raster_bwd   one CTA per processing unit (macro-tile batch), persistent:
-//                 the unit's records are staged with TMA and its tile masks
+//  k_bwd_suffix   one warp per render tile walks its macro-tile's batches
+//                 from the last to the first and turns each blended batch's
+//                 saved colour into the colour behind the batch: T_final bg
+//                 plus the colours of the later batches, a running sum from
+//                 the back (Sec. 6: the merge, read backwards, is a suffix
+//                 scan over the batches).
+//  k_raster_bwd   one CTA per processing unit (macro-tile batch), persistent.
+//                 The unit's records are staged with TMA and its tile masks
 //                 rebuilt exactly as in the forward.  For every tile the
-//                 batch blended, a warp replays the batch front to back from
-//                 the (C, T) that entered it (saved by the forward: the merge
-//                 "becomes a prefix scan") with the forward's arithmetic, so
-//                 every contribution and every stop decision is the
-//                 forward's.  With C_total the pixel's final colour, the
-//                 colour behind gaussian i is S_i = C_total - C_{<=i} and
+//                 batch blended, a warp walks the batch's gaussians back to
+//                 front, starting at each pixel's last contributor, from the
+//                 transmittance the forward left after it and the colour
+//                 behind the batch.  alpha_i is recomputed with the forward's
+//                 arithmetic (same bits), T_i = T_{i+1} / (1 - a_i), and the
+//                 colour behind gaussian i, S_i, grows from the back by
+//                 c_i a_i T_i, so no difference of pixel-sized colours enters
+//                 a gradient.
 //                   dL/dc_i = v a_i T_i,  dL/da_i = sum_ch v (c_i T_i - S_i/(1-a_i)),
 //                 chained to d mean2d, d conic, d opacity.  A gaussian's
 //                 per-pixel terms are summed over the warp by a 16-value
@@ -68,23 +76,29 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
   return w1;
 }
 
-// One gaussian at one pixel: forward update of the pixel state plus the
-// pixel's gradient terms (added into g).
-__device__ __forceinline__ void bwd_pixel(PixelAcc& p, float ub, float dx, float dy, const float4& g0, const float4& g1,
-                                          const float4& g2, float cA, float cB, float cC, const float3& ctot,
+// One gaussian at one pixel, walking back to front: T is the transmittance
+// behind the gaussian (after it), S the colour behind it.  When the gaussian
+// contributed (alpha > 0; the caller only passes gaussians up to the pixel's
+// last contributor) its terms are added into g, T becomes the transmittance
+// in front of it and S grows by its colour.
+__device__ __forceinline__ void bwd_pixel(float& T, float3& S, float ub, float dx, float dy, const float4& g0,
+                                          const float4& g1, const float4& g2, float cA, float cB, float cC,
                                           const float3& vv, float (&g)[16], bool& contrib) {
   float raw;
   const float a = alpha_of(ub, dy, g0, g1, g2, raw);
-  const float tb = p.T;
-  const float wt = apply_alpha(p, a, g2);
-  contrib = wt > 0.f;
+  contrib = a > 0.f;
   if (!contrib) return;
+  const float inv = 1.f / (1.f - a);
+  const float tb = T * inv;  // transmittance entering the gaussian
+  const float wt = a * tb;
   g[6] += vv.x * wt;
   g[7] += vv.y * wt;
   g[8] += vv.z * wt;
-  const float inv = 1.f / (1.f - a);
-  const float dal = vv.x * (g2.x * tb - (ctot.x - p.r) * inv) + vv.y * (g2.y * tb - (ctot.y - p.g) * inv) +
-                    vv.z * (g2.z * tb - (ctot.z - p.b) * inv);
+  const float dal = vv.x * (g2.x * tb - S.x * inv) + vv.y * (g2.y * tb - S.y * inv) + vv.z * (g2.z * tb - S.z * inv);
+  S.x = fmaf(g2.x, wt, S.x);
+  S.y = fmaf(g2.y, wt, S.y);
+  S.z = fmaf(g2.z, wt, S.z);
+  T = tb;
   if (!(raw < ALPHA_MAX)) return;  // clamped alpha: no derivative
   const float ex = raw / g1.y;
   g[5] += dal * ex;
@@ -94,6 +108,47 @@ __device__ __forceinline__ void bwd_pixel(PixelAcc& p, float ub, float dx, float
   g[4] += dq * dy * dy;
   g[0] += dq * -2.f * (cA * dx + cB * dy);
   g[1] += dq * -2.f * (cB * dx + cC * dy);
+}
+
+__device__ __forceinline__ int find_view_tile(const ViewDesc* views, int n_views, int tile) {
+  int v = 0;
+  while (v + 1 < n_views && views[v + 1].tile_base <= tile) ++v;
+  return v;
+}
+
+template <int MW, int MH>
+__global__ void __launch_bounds__(256) k_bwd_suffix(SuffixArgs a) {
+  constexpr int M = MW * MH;
+  if (read_status(a.fc)) return;
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int tile = wg; tile < a.total_tiles; tile += nwarps) {
+    const int v = find_view_tile(a.views, a.n_views, tile);
+    const ViewDesc& V = a.views[v];
+    const int lt = tile - V.tile_base;
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    const int seg = V.seg_base + (ty / MH) * V.mgx + (tx / MW);
+    const int tl = (ty % MH) * MW + (tx % MW);
+    const uint32_t r0 = a.first_batch[seg], r1 = a.first_batch[seg + 1];
+    bool first = true;
+    float3 B0 = make_float3(0.f, 0.f, 0.f), B1 = B0;
+    for (uint32_t r = r1; r-- > r0;) {
+      if (!((a.active[r] >> tl) & 1ull)) continue;
+      float4* ex = a.exitrec + ((size_t)r * M + tl) * TILE_PX;
+      const float4 e0 = ex[lane], e1 = ex[lane + 32];
+      if (first) {
+        // the last batch that blended the tile leaves the final transmittance
+        B0 = make_float3(e0.w * a.bg[0], e0.w * a.bg[1], e0.w * a.bg[2]);
+        B1 = make_float3(e1.w * a.bg[0], e1.w * a.bg[1], e1.w * a.bg[2]);
+        first = false;
+      }
+      ex[lane] = make_float4(B0.x, B0.y, B0.z, e0.w);
+      ex[lane + 32] = make_float4(B1.x, B1.y, B1.z, e1.w);
+      B0 = make_float3(B0.x + e0.x, B0.y + e0.y, B0.z + e0.z);
+      B1 = make_float3(B1.x + e1.x, B1.y + e1.y, B1.z + e1.z);
+    }
+  }
 }
 
 template <int MW, int MH>
@@ -120,7 +175,8 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
   while (true) {
     __syncthreads();  // every thread has read the previous unit's index
     if (tid == 0) {
-      s_unit = atomicAdd(&a.fc->raster_claim, 1u);
+      // a failed wait anywhere invalidates the pass: stop claiming units
+      s_unit = read_status(a.fc) ? 0xffffffffu : atomicAdd(&a.fc->raster_claim, 1u);
       s_qhead = 0;
     }
     __syncthreads();
@@ -143,13 +199,13 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       tma_load_1d(s_rec + (size_t)j * 3, rec_v + (size_t)id * REC_F4, 48u, &bar);
     }
     for (uint32_t j = tid; j < count * NG; j += BT) s_grad[j] = 0.f;
-    if (!mbar_wait_bounded(&bar, phase)) {
+    if (!mbar_wait_bounded(&bar, phase, a.wait_polls)) {
       set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
-      mbar_wait_bounded(&bar, phase);
+      atomicOr(&a.fc->timeout_where, 8u);
+      mbar_wait_bounded(&bar, phase);  // the copies in flight land before the CTA exits
       return;
     }
     phase ^= 1u;
-    const int K = (int)((count + 31) / 32);
     build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, BW);
     if (warp == 0) {
       int qn = 0;
@@ -174,53 +230,51 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       const int gtx = mtx0 + t % MW, gty = mty0 + t / MW;
       const int px = gtx * TILE + (lane & 7), py = gty * TILE + (lane >> 3);
       const bool in0 = px < V.W && py < V.H, in1 = px < V.W && py + 4 < V.H;
-      const float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
-      const float4 q0 = pre[lane], q1 = pre[lane + 32];
-      PixelAcc p0, p1;
-      pixel_load(p0, in0, q0);
-      pixel_load(p1, in1, q1);
-      float3 ct0 = make_float3(0.f, 0.f, 0.f), ct1 = ct0, v0 = ct0, v1 = ct0;
-      if (in0) {
+      // {colour behind the batch, T after its last contributor} per pixel
+      const size_t eo = ((size_t)r * M + t) * TILE_PX;
+      const float4 e0 = a.exitrec[eo + lane], e1 = a.exitrec[eo + lane + 32];
+      const uint32_t la0 = a.exitlast[eo + lane], la1 = a.exitlast[eo + lane + 32];
+      const int l0 = la0 == NO_LAST ? -1 : (int)la0, l1 = la1 == NO_LAST ? -1 : (int)la1;
+      float T0 = e0.w, T1 = e1.w;
+      float3 S0 = make_float3(e0.x, e0.y, e0.z), S1 = make_float3(e1.x, e1.y, e1.z);
+      float3 v0 = make_float3(0.f, 0.f, 0.f), v1 = v0;
+      if (in0 && l0 >= 0) {
         const long long o = V.pix_base + (long long)py * V.W + px;
-        const float4 f = a.final_px[o];
-        ct0 = make_float3(f.x, f.y, f.z);
         v0 = make_float3(a.dl_drgb[o * 3 + 0], a.dl_drgb[o * 3 + 1], a.dl_drgb[o * 3 + 2]);
       }
-      if (in1) {
+      if (in1 && l1 >= 0) {
         const long long o = V.pix_base + (long long)(py + 4) * V.W + px;
-        const float4 f = a.final_px[o];
-        ct1 = make_float3(f.x, f.y, f.z);
         v1 = make_float3(a.dl_drgb[o * 3 + 0], a.dl_drgb[o * 3 + 1], a.dl_drgb[o * 3 + 2]);
       }
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
-      // the tile's gaussians in depth order: set bits of its mini-batch masks
-      if (__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
-        for (int k = 0; k < K; ++k) {
-          const uint32_t mt = s_top[k * M + t], mb = s_bot[k * M + t];
-          uint32_t m = mt | mb;
-          if (!m) continue;
-          do {
-            const uint32_t bit = m & (0u - m);
-            m ^= bit;
-            const uint32_t j = (uint32_t)k * 32 + (__ffs(bit) - 1);
-            const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
-            const float cA = g0.z * g0.z * k2, cB = g0.z * g0.w * k2, cC = (g0.w * g0.w + g1.x * g1.x) * k2;
-            const float dx = fpx - g0.x;
-            const float ub = g0.z * dx;
-            float gs[16];
+      // the tile's gaussians back to front, from the warp's latest last
+      // contributor: set bits of its mini-batch masks, highest first
+      const int lm = __reduce_max_sync(0xffffffffu, max(l0, l1));
+      for (int k = lm >> 5; k >= 0; --k) {
+        const uint32_t mt = s_top[k * M + t], mb = s_bot[k * M + t];
+        uint32_t m = mt | mb;
+        if (k == (lm >> 5)) m &= 0xffffffffu >> (31 - (lm & 31));  // bits <= lm
+        while (m) {
+          const int b = 31 - __clz(m);
+          const uint32_t bit = 1u << b;
+          m ^= bit;
+          const int j = k * 32 + b;
+          const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
+          const float cA = g0.z * g0.z * k2, cB = g0.z * g0.w * k2, cC = (g0.w * g0.w + g1.x * g1.x) * k2;
+          const float dx = fpx - g0.x;
+          const float ub = g0.z * dx;
+          float gs[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) gs[q] = 0.f;
-            // a half the gaussian cannot reach is skipped, as in the forward
-            bool c0 = false, c1 = false;
-            if (mt & bit) bwd_pixel(p0, ub, dx, fpy - g0.y, g0, g1, g2, cA, cB, cC, ct0, v0, gs, c0);
-            if (mb & bit) bwd_pixel(p1, ub, dx, fpy1 - g0.y, g0, g1, g2, cA, cB, cC, ct1, v1, gs, c1);
-            if (__any_sync(0xffffffffu, c0 || c1)) {
-              const float tot = reduce_scatter16(gs, lane);
-              const int idx = (lane >> 1) & 15;
-              if ((lane & 1) == 0 && idx < NG && tot != 0.f) atomicAdd(&s_grad[j * NG + idx], tot);
-            }
-          } while (m);
-          if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
+          for (int q = 0; q < 16; ++q) gs[q] = 0.f;
+          // a half the gaussian cannot reach is skipped, as in the forward
+          bool c0 = false, c1 = false;
+          if ((mt & bit) && j <= l0) bwd_pixel(T0, S0, ub, dx, fpy - g0.y, g0, g1, g2, cA, cB, cC, v0, gs, c0);
+          if ((mb & bit) && j <= l1) bwd_pixel(T1, S1, ub, dx, fpy1 - g0.y, g0, g1, g2, cA, cB, cC, v1, gs, c1);
+          if (__any_sync(0xffffffffu, c0 || c1)) {
+            const float tot = reduce_scatter16(gs, lane);
+            const int idx = (lane >> 1) & 15;
+            if ((lane & 1) == 0 && idx < NG && tot != 0.f) atomicAdd(&s_grad[j * NG + idx], tot);
+          }
         }
       }
     }
@@ -230,7 +284,6 @@ __global__ void __launch_bounds__(BT) k_raster_bwd(BackwardArgs a, int cap) {
       const float val = s_grad[j];
       if (val != 0.f) atomicAdd(&g2d[(size_t)a.vals[start + j / NG] * NG + j % NG], val);
     }
-    __syncthreads();
   }
 }
 
@@ -509,6 +562,25 @@ cudaError_t launch_pbwd_deg(const ProjectBackwardArgs& a, cudaStream_t st) {
 
 }  // namespace
 
+template <int MW, int MH>
+cudaError_t launch_suffix_shape(const SuffixArgs& a, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int blocks = min((a.total_tiles + 7) / 8, sms * 8);
+  if (blocks < 1) blocks = 1;
+  k_bwd_suffix<MW, MH><<<blocks, 256, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_suffix(const SuffixArgs& a, cudaStream_t st) {
+  if (a.macro_w == 8 && a.macro_h == 4) return launch_suffix_shape<8, 4>(a, st);
+  if (a.macro_w == 4 && a.macro_h == 4) return launch_suffix_shape<4, 4>(a, st);
+  if (a.macro_w == 8 && a.macro_h == 8) return launch_suffix_shape<8, 8>(a, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_raster_backward(const BackwardArgs& a, cudaStream_t st) {
   if (a.macro_w == 8 && a.macro_h == 4) return launch_bwd_shape<8, 4>(a, st);
   if (a.macro_w == 4 && a.macro_h == 4) return launch_bwd_shape<4, 4>(a, st);
@@ -551,9 +623,28 @@ extern "C" hg_status hg_render_backward(hg_state* s, const float* dL_drgb, float
   if (r != HG_OK) return r;
   float* g2d = (float*)s->bufs[G_DMEANS2].p;
   FrameCounters* fc = (FrameCounters*)s->bufs[B_FC].p;
+  // the pass starts with a clean status word (the forward completed with
+  // HG_OK; a failed earlier backward of this frame leaves nothing behind)
   cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * NG * (size_t)n * g.V, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(&fc->raster_claim, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&fc->status, 0, sizeof(int), st);
   if (e != cudaSuccess) return hg_cuda_status(e, "backward clear");
+  if (s->bwd_suffix_done != s->frame_id && n > 0) {
+    // colour behind every batch, once per saved frame (in place)
+    SuffixArgs sa{};
+    sa.active = (const unsigned long long*)s->bufs[B_ACTIVE].p;
+    sa.first_batch = (const uint32_t*)s->bufs[B_FIRSTB].p;
+    sa.exitrec = (float4*)s->bufs[B_EXIT].p;
+    sa.views = (const ViewDesc*)s->bufs[B_VIEWS].p;
+    sa.n_views = g.V;
+    sa.total_tiles = g.total_tiles;
+    sa.macro_w = s->opts.macro_w;
+    sa.macro_h = s->opts.macro_h;
+    for (int c = 0; c < 3; ++c) sa.bg[c] = s->opts.bg[c];
+    sa.fc = fc;
+    if ((e = launch_bwd_suffix(sa, st)) != cudaSuccess) return hg_cuda_status(e, "backward suffix");
+    s->bwd_suffix_done = s->frame_id;
+  }
   if (n > 0) {
     BackwardArgs ba{};
     ba.rec = (const float4*)s->bufs[B_REC].p;
@@ -564,13 +655,14 @@ extern "C" hg_status hg_render_backward(hg_state* s, const float* dL_drgb, float
     ba.batches = (const uint4*)s->bufs[B_BATCHES].p;
     ba.batch_order = (const uint32_t*)s->bufs[B_BORDER].p;
     ba.active = (const unsigned long long*)s->bufs[B_ACTIVE].p;
-    ba.prefix = (const float4*)s->bufs[B_PREFIX].p;
-    ba.final_px = (const float4*)s->bufs[B_FINAL].p;
+    ba.exitrec = (float4*)s->bufs[B_EXIT].p;
+    ba.exitlast = (const uint16_t*)s->bufs[B_EXITLAST].p;
     ba.dl_drgb = dL_drgb;
     ba.g2d = g2d;
     ba.batch_cap = s->opts.batch_cap;
     ba.macro_w = s->opts.macro_w;
     ba.macro_h = s->opts.macro_h;
+    ba.wait_polls = s->ctx->wait_polls;
     ba.fc = fc;
     if ((e = launch_raster_backward(ba, st)) != cudaSuccess) return hg_cuda_status(e, "raster backward");
   }
@@ -592,6 +684,10 @@ extern "C" hg_status hg_render_backward(hg_state* s, const float* dL_drgb, float
   pa.d_opacity_logits = d_opacity_logits;
   pa.d_sh = d_sh;
   if ((e = launch_project_backward(pa, st)) != cudaSuccess) return hg_cuda_status(e, "projection backward");
+  // the device status of the pass, for hg_state_sync
+  if ((e = cudaMemcpyAsync(s->fc_host, fc, sizeof(FrameCounters), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return hg_cuda_status(e, "backward status");
   s->last_stream = st;
+  s->has_grad2d = true;
   return HG_OK;
 }

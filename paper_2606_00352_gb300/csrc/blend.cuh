@@ -103,17 +103,19 @@ __device__ __forceinline__ float apply_alpha(PixelAcc& p, float al, const float4
   return wt;
 }
 
-__device__ __forceinline__ void blend(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
-                                      const float4& g2) {
+// One gaussian at one pixel; returns its weight alpha T (0: no contribution).
+__device__ __forceinline__ float blend(PixelAcc& p, float ubase, float dy, const float4& g0, const float4& g1,
+                                       const float4& g2) {
   float raw;
-  apply_alpha(p, alpha_of(ubase, dy, g0, g1, g2, raw), g2);
+  return apply_alpha(p, alpha_of(ubase, dy, g0, g1, g2, raw), g2);
 }
 
 // ---- half-precision rasterisation (HG_FLAG_FP16, Sec. 3.5 / 4.5)
 // The staged record's first two float4 are rewritten as half2 pairs
 // {my, my} {l1', l1'} {l2', l2'} {o, o} | {mx, mx} {l0', l0'} {E, E} {0, 0},
-// positions relative to the macro-tile origin (so every operand of the
-// Mahalanobis sum stays far inside the fp16 range); the colour float4 stays.
+// positions relative to the macro-tile centre (so every operand of the
+// Mahalanobis sum stays far inside the fp16 range, at the finest spacing the
+// macro-tile allows); the colour float4 stays.
 __device__ __forceinline__ uint32_t h2_bits(float x) {
   const __half2 h = __float2half2_rn(x);
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -127,7 +129,7 @@ __device__ __forceinline__ void half_record(float4* r, float ox, float oy) {
 }
 
 // alpha of one gaussian at the two pixels a thread owns, in half2: hpx the
-// pixel column, hpy the two pixel rows (macro-tile-relative).  The blend test
+// pixel column, hpy the two pixel rows (relative to the macro-tile centre).  The blend test
 // e <= E is the saturated multiply-add of the float32 path at half scale
 // (fp16 spacing at e = 6.5 is 2^-8, so (E - e) 2^10 + 1 is <= -3 when e > E).
 __device__ __forceinline__ float2 half_alpha2(const float4* r, __half2 hpx, __half2 hpy) {

@@ -25,7 +25,8 @@ constexpr int MAX_VIEWS = 64;
 // that a record never straddles two 64-byte DRAM access chunks.
 constexpr int REC_F4 = 4;
 constexpr int RADIUS_MAX = 1 << 20;
-constexpr uint32_t SPIN_LIMIT = 1u << 24;  // bounded device waits
+constexpr uint32_t SPIN_LIMIT = 1u << 24;  // bounded device waits (polls), default
+constexpr uint32_t CHAIN_SPIN = 200000;    // batch-chain polls (~0.1 s) before a unit renders unchained
 
 // Per-view geometry, uploaded once per frame.
 struct ViewDesc {
@@ -59,6 +60,10 @@ struct FrameCounters {
   uint32_t pad0;
   unsigned long long replays;
   unsigned long long raster_evals;
+  // HG_FLAG_PROFILE: the intrinsic per-pixel work of the frame (support
+  // evaluations of live pixels up to their stop; contributing ones)
+  unsigned long long pixel_support_evals;
+  unsigned long long pixel_contrib_evals;
   // rasteriser phase cycles summed over units (HG_FLAG_PROFILE): load, masks,
   // chain wait, blend (per warp, summed), end barrier (per warp, summed), units
   unsigned long long raster_cycles[6];
@@ -107,10 +112,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for phase `parity` of `bar` with an iteration limit; returns false on
-// timeout (the caller records HG_ERR_DEVICE_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < SPIN_LIMIT; ++it)
+// Wait for phase `parity` of `bar` with at most `polls` polls (0: give up at
+// once); returns false on timeout (the caller records HG_ERR_DEVICE_TIMEOUT
+// and then waits, with the default limit, for its copies still in flight).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls = SPIN_LIMIT) {
+  for (uint32_t it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -102,6 +102,8 @@ extern "C" hg_status hg_graph_launch(hg_graph* G, void* stream) {
   if (e != cudaSuccess) return hg_cuda_status(e, "graph launch");
   G->state->last_stream = st;
   G->state->has_frame = true;
+  ++G->state->frame_id;  // a new frame (a saved one needs its own backward suffix)
+  G->state->has_grad2d = false;
   return HG_OK;
 }
 

@@ -13,6 +13,11 @@ struct hg_ctx {
   int sms = 0;
   hg_state* internal = nullptr;  // workspace used when the caller passes no state
   void* loss_scratch = nullptr;   // hg_l2_loss block partials + counter (allocated on first use)
+  // bounded device waits (hg_ctx_set_wait_limits): polls of an mbarrier or a
+  // look-back word before the wait gives up, and of the batch chain before a
+  // unit renders unchained
+  uint32_t wait_polls = hg::SPIN_LIMIT;
+  uint32_t chain_polls = hg::CHAIN_SPIN;
 };
 
 struct hg_scene {
@@ -38,7 +43,7 @@ enum BufId {
   B_FC, B_VIEWS, B_BIN, B_DKEY, B_REC, B_VIS, B_SPLATS,
   B_HIST, B_COLPRE, B_SEGTOT, B_SEGOFF, B_FIRSTB, B_TIERLIST, B_BIGTILES, B_BIGSEGS, B_BIGTF,
   B_KEYS, B_VALS, B_KEYS2, B_VALS2, B_BATCHES, B_BORDER, B_RANKC,
-  B_PARTIAL, B_ACTIVE, B_CHAIN, B_MODE, B_TSTATE, B_TRANK, B_STOPPOS, B_FINAL, B_PREFIX, B_SEGHIST, B_LOOKBACK,
+  B_PARTIAL, B_ACTIVE, B_CHAIN, B_MODE, B_TSTATE, B_TRANK, B_STOPPOS, B_EXIT, B_EXITLAST, B_SEGHIST, B_LOOKBACK,
   P_COUNTS, P_OFFS, P_SCAN, P_KEYS, P_KEYS2, P_VALS, P_VALS2, P_RANGES, P_LOOKBACK, P_DHIST,
   G_DMEANS2, G_AUX,
   BUF_COUNT
@@ -78,6 +83,13 @@ struct hg_state {
   const hg_scene* scene = nullptr;
   size_t cap_pairs = 0, cap_batches = 0, cap_tiles = 0, cap_big_segs = 0;
   size_t cap_plain_pairs = 0, cap_plain_tiles = 0;
+  // plain path: the buffers holding the sorted (64-bit key, record) pairs
+  unsigned long long* plain_keys = nullptr;
+  uint32_t* plain_vals = nullptr;
+  // frames rendered into this state, and the frame whose saved batch colours
+  // the backward already turned into colours behind the batches
+  uint64_t frame_id = 0, bwd_suffix_done = 0;
+  bool has_grad2d = false;  // a backward of the current frame wrote G_DMEANS2
 };
 
 void hg_set_error(const std::string& s);
@@ -97,6 +109,10 @@ cudaError_t gather_rows(const void* src, void* dst, const int32_t* perm, long lo
 }  // namespace hg
 hg_status state_create(hg_ctx* ctx, hg_state** out);
 hg_status build_views(hg_state* s, const hg_camera* cams, int V, const hg_render_opts* o, hg::FrameGeom& g);
+// Grows the frame workspace of `s` to n gaussians and the views of `g`
+// (capacities: the state's, or first-frame estimates); nothing is launched.
+hg_status ensure_workspace(hg_state* s, long long n, const hg::FrameGeom& g, const hg_render_opts* o,
+                           cudaStream_t st);
 hg_status enqueue_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg::FrameGeom& g,
                         float* out_rgb, float* out_T, cudaStream_t st);
 hg_status run_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg_camera* cams, int V,

@@ -23,6 +23,7 @@ struct ProjectArgs {
   int bin_mode;           // BIN_CLASSIC, BIN_CELLS_RECT or BIN_CELLS_ELLIPSE
   int macro_w, macro_h;   // render tiles per macro cell (cell binning records)
   hg_splat* splats;       // optional [V][n]
+  uint32_t wait_polls;    // mbarrier polls before a wait gives up (HG_ERR_DEVICE_TIMEOUT)
   FrameCounters* fc;
 };
 
@@ -55,6 +56,7 @@ struct PartitionArgs {
   uint32_t* rank_count;   // [MAX_RANKS + 1] scratch for the schedule
   int batch_cap;
   uint32_t cap_pairs, cap_batches, cap_tiles, cap_big_segs;
+  uint32_t* seg_hist;     // [cap_big_segs][8][256] onesweep digit histograms, zeroed here for the big segments
   FrameCounters* fc;
 };
 
@@ -82,9 +84,11 @@ struct SortArgs {
   const uint4* big_tiles;
   const uint32_t* big_segs;
   const uint32_t* big_tile_first;
-  uint32_t* seg_hist;         // [cap_big_segs][4][256]
-  uint32_t* lookback;         // [4][cap_tiles][256]
+  uint32_t* seg_hist;         // [cap_big_segs][8][256], zero on entry
+  uint32_t* lookback;         // [8][cap_tiles][256]
   uint32_t cap_tiles, cap_big_segs;
+  uint32_t wait_polls;        // look-back polls before a wait gives up
+  int os_ctas;                // cap of the onesweep grids (0: one full wave)
   FrameCounters* fc;
 };
 
@@ -107,7 +111,12 @@ struct RasterArgs {
   uint32_t* mode;             // [cap_batches] BATCH_CHAINED or BATCH_LOCAL
   float4* tile_state;         // [total tiles][64] (r, g, b, +-T) after the chained batches
   uint32_t* tile_rank;        // [total tiles] rank + 1 of the last chained batch that blended the tile, 0 = none
-  float4* prefix;             // optional [cap_batches][M][64]: (C, +-T) entering the batch (backward)
+  // optional [cap_batches][M][64], saved for the backward: per pixel of every
+  // tile the batch blended, {the batch's own colour (r, g, b), the
+  // transmittance after its last contributor in the batch} and the index in
+  // the batch of that contributor (NO_LAST16: none)
+  float4* exitrec;
+  uint16_t* exitlast;
   int persistent_ctas;
   int independent;            // never wait: every batch after the first renders from T = 1
   int fp16;                   // half2 alpha (HG_FLAG_FP16)
@@ -119,9 +128,12 @@ struct RasterArgs {
   float* out_T;
   float bg[3];
   int profile;                // accumulate phase cycles into FrameCounters::raster_cycles
+  uint32_t wait_polls;        // mbarrier polls before a wait gives up (HG_ERR_DEVICE_TIMEOUT)
+  uint32_t chain_polls;       // polls of the batch chain before a unit renders unchained
   FrameCounters* fc;
 };
 
+constexpr uint32_t NO_LAST = 0xffffu;  // exitlast: no gaussian of the batch contributed to the pixel (B_r <= 2048)
 constexpr uint32_t BATCH_CHAINED = 1;  // rendered from the exact transmittance entering it
 constexpr uint32_t BATCH_LOCAL = 2;    // rendered from T = 1; composited by the merge
 constexpr uint32_t CHAIN_BROKEN = 0x80000000u;
@@ -146,8 +158,6 @@ struct MergeArgs {
   float bg[3];
   float* out_rgb;
   float* out_T;
-  float4* prefix;             // optional [cap_batches][M][64]: (C, T) entering each batch (backward)
-  float4* final_px;           // optional [pixels]: (r, g, b, T) as written to the outputs (backward)
   FrameCounters* fc;
 };
 
@@ -160,12 +170,30 @@ struct BackwardArgs {
   const uint4* batches;
   const uint32_t* batch_order;
   const unsigned long long* active;
-  const float4* prefix;       // [cap_batches][M][64]
-  const float4* final_px;     // [pixels]
+  // [cap_batches][M][64] per blended (batch, tile, pixel), written by the
+  // forward as {the batch's colour, T after its last contributor} and turned
+  // by the suffix pass into {the colour behind the batch, T}
+  float4* exitrec;
+  const uint16_t* exitlast;   // [cap_batches][M][64] index of the last contributor, NO_LAST: none
   const float* dl_drgb;       // [pixels][3]
   float* g2d;                 // [V][n][9]: d mean2d (2), d conic A B C (3), d opacity, d rgb (3)
   int batch_cap;
   int macro_w, macro_h;
+  uint32_t wait_polls;        // mbarrier polls before a wait gives up (HG_ERR_DEVICE_TIMEOUT)
+  FrameCounters* fc;
+};
+
+// Colour behind every batch (the backward's suffix over a macro-tile's
+// batches): one warp per render tile.
+struct SuffixArgs {
+  const unsigned long long* active;
+  const uint32_t* first_batch;  // [S + 1]
+  float4* exitrec;
+  const ViewDesc* views;
+  int n_views;
+  int total_tiles;
+  int macro_w, macro_h;
+  float bg[3];
   FrameCounters* fc;
 };
 
@@ -204,9 +232,10 @@ struct PlainArgs {
   unsigned long long* keys_alt;
   uint32_t* vals_alt;
   uint2* ranges;              // [total tiles]
-  uint32_t* lookback;
+  uint32_t* lookback;         // [8][cap_tiles][256]
   uint32_t* digit_hist;       // [8][256]
   uint32_t cap_pairs, cap_tiles;
+  uint32_t wait_polls;        // look-back polls before a wait gives up
   float bg[3];
   float* out_rgb;
   float* out_T;
@@ -227,11 +256,14 @@ struct OsTileView {
 // Onesweep LSD radix sort of the tiles' segments over digit passes
 // [first_pass, first_pass + npass) of K keys with uint32 values; the result
 // is in (keys, vals) for an even pass count, else in the alternates.
+// seg_hist: [segments][NPASS][256] words (zeroed here when zero_hist, else
+// zero on entry); lookback: [NPASS][lb_stride] words, lb_stride >= 256 x
+// tiles (cleared by the histogram kernel).
 template <typename K, int NPASS>
 cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt,
-                            uint32_t* seg_hist, size_t seg_hist_words, uint32_t* lookback, size_t lookback_words,
-                            uint32_t* claims, int first_pass, int npass, FrameCounters* fc, cudaStream_t st,
-                            bool* result_in_alt);
+                            uint32_t* seg_hist, size_t seg_hist_words, bool zero_hist, uint32_t* lookback,
+                            size_t lb_stride, uint32_t* claims, int first_pass, int npass, uint32_t wait_polls,
+                            FrameCounters* fc, cudaStream_t st, bool* result_in_alt);
 
 // Host-side count of kernel launches issued by this library (all threads).
 void note_launch(int n = 1);
@@ -253,6 +285,7 @@ struct SortStreams {
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st, const SortStreams* ss);
 cudaError_t launch_raster(const RasterArgs& a, cudaStream_t st);
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
+cudaError_t launch_bwd_suffix(const SuffixArgs& a, cudaStream_t st);
 cudaError_t launch_raster_backward(const BackwardArgs& a, cudaStream_t st);
 cudaError_t launch_project_backward(const ProjectBackwardArgs& a, cudaStream_t st);
 // returns the key pointer that holds the sorted result through *sorted_keys / *sorted_vals

@@ -90,11 +90,6 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
       if (!((a.active[r] >> tl) & 1ull)) continue;
       const float4* src = a.partial + ((size_t)r * M + tl) * TILE_PX;
       const float4 q0 = src[lane], q1 = src[lane + 32];
-      if (a.prefix) {
-        float4* pre = a.prefix + ((size_t)r * M + tl) * TILE_PX;
-        pre[lane] = pixel_state(p0);
-        pre[lane + 32] = pixel_state(p1);
-      }
       bool need0, need1;
       apply_partial(p0, q0, need0);
       apply_partial(p1, q1, need1);
@@ -154,7 +149,6 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
       a.out_rgb[o * 3 + 1] = f.y;
       a.out_rgb[o * 3 + 2] = f.z;
       if (a.out_T) a.out_T[o] = tf;
-      if (a.final_px) a.final_px[o] = f;
     }
     if (in1) {
       const long long o = V.pix_base + (long long)(py + 4) * V.W + px;
@@ -164,7 +158,6 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
       a.out_rgb[o * 3 + 1] = f.y;
       a.out_rgb[o * 3 + 2] = f.z;
       if (a.out_T) a.out_T[o] = tf;
-      if (a.final_px) a.final_px[o] = f;
     }
   }
   if (lane == 0 && replays) atomicAdd(&a.fc->replays, replays);

@@ -134,7 +134,7 @@ hg_status spatial_order(hg_ctx* ctx, const float* means, long long n, int32_t* p
   const long long nt = (n + OS_TILE - 1) / OS_TILE;
   // scratch: counters | min/max | tiles | digit histogram | look-back | keys, vals, alternates
   const size_t fc_b = 256, mm_b = 256, tiles_b = sizeof(uint4) * (size_t)nt, hist_b = sizeof(uint32_t) * 4 * 256,
-               lb_b = sizeof(uint32_t) * 256 * (size_t)nt, kv_b = sizeof(uint32_t) * (size_t)n;
+               lb_b = sizeof(uint32_t) * 4 * 256 * (size_t)nt, kv_b = sizeof(uint32_t) * (size_t)n;
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t total = fc_b + mm_b + up(tiles_b) + hist_b + up(lb_b) + 4 * up(kv_b);
   unsigned char* base = (unsigned char*)ctx_alloc(ctx, total, st);
@@ -174,8 +174,8 @@ hg_status spatial_order(hg_ctx* ctx, const float* means, long long n, int32_t* p
   bool alt = false;
   if (e == cudaSuccess) {
     OsTileView tv{tiles, &fc->n_big_tiles, hist, nullptr, nullptr, nullptr};
-    e = launch_onesweep<uint32_t, 4>(tv, keys, vals, keys2, vals2, hist, 4 * 256, lb, (size_t)nt * 256, fc->os_claim,
-                                     0, 4, fc, st, &alt);
+    e = launch_onesweep<uint32_t, 4>(tv, keys, vals, keys2, vals2, hist, 4 * 256, true, lb, (size_t)nt * 256,
+                                     fc->os_claim, 0, 4, ctx->wait_polls, fc, st, &alt);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(perm, alt ? vals2 : vals, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);

@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
     if (over) set_status(a.fc, HG_ERR_CAPACITY);
   }
   if (over) return;
+  // the onesweep's digit histograms of the big segments start at zero
+  for (uint32_t w = tid; w < t_tier[TIER_OS] * 8u * 256u; w += NT) a.seg_hist[w] = 0;
   // raster schedule: batches of rank j = segments with more than j batches
   uint32_t hv[4], hs = 0;
 #pragma unroll

@@ -213,8 +213,8 @@ cudaError_t launch_plain(PlainArgs& a, cudaStream_t st, unsigned long long** sor
   OsTileView tv{tiles, &a.fc->n_big_tiles, a.digit_hist, nullptr, nullptr, nullptr};
   bool alt = false;
   e = launch_onesweep<unsigned long long, 8>(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.digit_hist, 8 * 256,
-                                             a.lookback, (size_t)a.cap_tiles * 256, a.fc->os_claim, 0, npass, a.fc,
-                                             st, &alt);
+                                             true, a.lookback, (size_t)a.cap_tiles * 256, a.fc->os_claim, 0, npass,
+                                             a.wait_polls, a.fc, st, &alt);
   if (e != cudaSuccess) return e;
   unsigned long long* sk = alt ? a.keys_alt : a.keys;
   uint32_t* sv = alt ? a.vals_alt : a.vals;

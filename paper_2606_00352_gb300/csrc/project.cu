@@ -223,8 +223,9 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
     uint32_t* dst = reinterpret_cast<uint32_t*>(s.views);
     for (int j = tid; j < words; j += PROJ_THREADS) dst[j] = src[j];
   }
-  if (full && !mbar_wait_bounded(&s.bar, 0)) {
+  if (full && !mbar_wait_bounded(&s.bar, 0, a.wait_polls)) {
     set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
+    atomicOr(&a.fc->timeout_where, 4u);
     // the copies were issued by this CTA: wait (bounded again) before exit
     mbar_wait_bounded(&s.bar, 0);
     return;

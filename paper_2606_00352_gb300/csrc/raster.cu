@@ -37,7 +37,6 @@ namespace {
 
 constexpr int RW = 8;  // warps per CTA
 constexpr int RT = RW * 32;
-constexpr uint32_t CHAIN_SPIN = 200000;  // ~0.1 s of polling before falling back
 
 // Final pixels of a tile (C + T bg, T) into the outputs.
 __device__ __forceinline__ void write_pixels(const RasterArgs& a, const ViewDesc& V, int px, int py, bool in0,
@@ -60,7 +59,10 @@ __device__ __forceinline__ void write_pixels(const RasterArgs& a, const ViewDesc
   }
 }
 
-template <int MW, int MH, bool SAVE, bool HALF>
+// STATS (HG_FLAG_PROFILE frames): also counts the intrinsic per-pixel work,
+// the support evaluations (q <= 9) of live pixels up to and including each
+// pixel's stop, and the contributing ones.
+template <int MW, int MH, bool SAVE, bool HALF, bool STATS>
 __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   constexpr int M = MW * MH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -82,11 +84,12 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   if (read_status(a.fc)) return;
   const uint32_t n_units = a.fc->n_batches;
   uint32_t phase = 0;
-  unsigned long long evals = 0;
+  unsigned long long evals = 0, e_sup = 0, e_con = 0;
 
   while (true) {
     if (tid == 0) {
-      s_unit = atomicAdd(&a.fc->raster_claim, 1u);
+      // a failed wait anywhere invalidates the frame: stop claiming units
+      s_unit = read_status(a.fc) ? 0xffffffffu : atomicAdd(&a.fc->raster_claim, 1u);
       s_qhead = 0;
       s_blended = 0;
       s_written = 0;
@@ -112,10 +115,10 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       const uint32_t id = a.vals[start + j];
       tma_load_1d(s_rec + (size_t)j * 3, rec_v + (size_t)id * REC_F4, 48u, &bar);
     }
-    if (!mbar_wait_bounded(&bar, phase)) {
+    if (!mbar_wait_bounded(&bar, phase, a.wait_polls)) {
       set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
       atomicOr(&a.fc->timeout_where, 2u);
-      mbar_wait_bounded(&bar, phase);
+      mbar_wait_bounded(&bar, phase);  // the copies in flight land before the CTA exits
       return;
     }
     phase ^= 1u;
@@ -127,9 +130,10 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     if (HALF) {
       // each thread rewrites the records of the gaussians it built masks for
       // (no other thread reads them before the barrier below) as half2 pairs
-      // relative to the macro-tile origin; the colour stays float32
+      // relative to the macro-tile centre (the smallest offsets, so the
+      // finest half-precision spacing); the colour stays float32
       __syncwarp();
-      const float ox = (float)(mtx0 * TILE), oy = (float)(mty0 * TILE);
+      const float ox = (float)((mtx0 + MW / 2) * TILE), oy = (float)((mty0 + MH / 2) * TILE);
       for (uint32_t j = (uint32_t)warp * 32 + lane; j < count; j += RT)
         half_record(s_rec + (size_t)j * 3, ox, oy);
     }
@@ -170,14 +174,20 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       uint32_t mode = BATCH_CHAINED;
       if (rank > 0) {
         mode = BATCH_LOCAL;
-        for (uint32_t it = 0; it < (a.independent ? 0u : CHAIN_SPIN); ++it) {
+        for (uint32_t it = 0; it < (a.independent ? 0u : a.chain_polls); ++it) {
           const uint32_t c = ld_acquire(&a.chain[seg]);
           if (c == rank) {
             mode = BATCH_CHAINED;
             break;
           }
-          if (c & CHAIN_BROKEN) break;
+          if ((c & CHAIN_BROKEN) || read_status(a.fc)) break;
           __nanosleep(256);
+        }
+        // the backward needs every batch chained: a frame saved for it whose
+        // chain wait gave up is invalid
+        if (SAVE && mode == BATCH_LOCAL) {
+          set_status(a.fc, HG_ERR_DEVICE_TIMEOUT);
+          atomicOr(&a.fc->timeout_where, 16u);
         }
       }
       __threadfence();
@@ -226,15 +236,21 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         continue;
       }
       if (lane == 0) atomicOr(&s_blended, 1ull << t);
+      // SAVE: the batch's own colour is accumulated from zero (the colour
+      // entering it is added back at the end), and the index of each pixel's
+      // last contributing gaussian in the batch is kept
+      uint32_t last0 = NO_LAST, last1 = NO_LAST;
+      float3 cin0 = make_float3(0.f, 0.f, 0.f), cin1 = cin0;
       if (SAVE) {
-        float4* pre = a.prefix + ((size_t)r * M + t) * TILE_PX;
-        pre[lane] = pixel_state(p0);
-        pre[lane + 32] = pixel_state(p1);
+        cin0 = make_float3(p0.r, p0.g, p0.b);
+        cin1 = make_float3(p1.r, p1.g, p1.b);
+        p0.r = p0.g = p0.b = p1.r = p1.g = p1.b = 0.f;
       }
       const float fpx = (float)px, fpy = (float)py, fpy1 = (float)(py + 4);
-      // macro-tile-relative pixel coordinates (half mode)
-      const __half2 hpx = __float2half2_rn((float)(px - mtx0 * TILE));
-      const __half2 hpy = __floats2half2_rn((float)(py - mty0 * TILE), (float)(py + 4 - mty0 * TILE));
+      // pixel coordinates relative to the macro-tile centre (half mode)
+      const int hox = (mtx0 + MW / 2) * TILE, hoy = (mty0 + MH / 2) * TILE;
+      const __half2 hpx = __float2half2_rn((float)(px - hox));
+      const __half2 hpy = __floats2half2_rn((float)(py - hoy), (float)(py + 4 - hoy));
       uint32_t n_blend = 0;
       // gaussians of this tile in depth order: the set bits of its per
       // mini-batch masks (warp-uniform), blended directly; the unanimous
@@ -256,18 +272,49 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
           } else {
             const float4 g0 = s_rec[j * 3 + 0], g1 = s_rec[j * 3 + 1], g2 = s_rec[j * 3 + 2];
             const float ub = g0.z * (fpx - g0.x);
+            if (STATS) {
+              // support (e <= 9 log2(e) / 2) of the pixels still live
+              const float dy0 = fpy - g0.y, dy1 = fpy1 - g0.y;
+              const float u0 = fmaf(g0.w, dy0, ub), w0 = g1.x * dy0, u1 = fmaf(g0.w, dy1, ub), w1 = g1.x * dy1;
+              e_sup += ((mt & bit) && pixel_live(p0) && fmaf(u0, u0, w0 * w0) <= SUPPORT_E) +
+                       ((mb & bit) && pixel_live(p1) && fmaf(u1, u1, w1 * w1) <= SUPPORT_E);
+            }
             // a half the gaussian cannot reach is skipped (its blend is a no-op)
             if (mt & bit) {
-              blend(p0, ub, fpy - g0.y, g0, g1, g2);
-              if (mb & bit) blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+              const float w0 = blend(p0, ub, fpy - g0.y, g0, g1, g2);
+              if (SAVE && w0 > 0.f) last0 = j;
+              if (STATS) e_con += w0 > 0.f;
+              if (mb & bit) {
+                const float w1 = blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+                if (SAVE && w1 > 0.f) last1 = j;
+                if (STATS) e_con += w1 > 0.f;
+              }
             } else {
-              blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+              const float w1 = blend(p1, ub, fpy1 - g0.y, g0, g1, g2);
+              if (SAVE && w1 > 0.f) last1 = j;
+              if (STATS) e_con += w1 > 0.f;
             }
           }
         } while (m);
         if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 32ull;
+      if (SAVE) {
+        // the backward walks the batch back to front from its colour and the
+        // transmittance after its last contributor
+        float4* ex = a.exitrec + ((size_t)r * M + t) * TILE_PX;
+        ex[lane] = make_float4(p0.r, p0.g, p0.b, pixel_final_T(p0));
+        ex[lane + 32] = make_float4(p1.r, p1.g, p1.b, pixel_final_T(p1));
+        uint16_t* la = a.exitlast + ((size_t)r * M + t) * TILE_PX;
+        la[lane] = (uint16_t)last0;
+        la[lane + 32] = (uint16_t)last1;
+        p0.r += cin0.x;
+        p0.g += cin0.y;
+        p0.b += cin0.z;
+        p1.r += cin1.x;
+        p1.g += cin1.y;
+        p1.b += cin1.z;
+      }
       if (write_out) {
         write_pixels(a, V, px, py, in0, in1, p0, p1);
         if (lane == 0) atomicOr(&s_written, 1ull << t);
@@ -325,31 +372,40 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
     }
   }
   if (lane == 0 && evals) atomicAdd(&a.fc->raster_evals, evals);
+  if (STATS) {
+    e_sup = warp_sum(e_sup);
+    e_con = warp_sum(e_con);
+    if (lane == 0) {
+      atomicAdd(&a.fc->pixel_support_evals, e_sup);
+      atomicAdd(&a.fc->pixel_contrib_evals, e_con);
+    }
+  }
 }
 
-template <int MW, int MH, bool SAVE, bool HALF>
+template <int MW, int MH, bool SAVE, bool HALF, bool STATS = false>
 cudaError_t launch_raster_kernel(const RasterArgs& a, int cap, cudaStream_t st) {
   constexpr int M = MW * MH;
   const size_t sm = (size_t)cap * 48 + (size_t)((cap + 31) / 32) * M * 8;
   cudaError_t e =
-      cudaFuncSetAttribute(k_raster<MW, MH, SAVE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_raster<MW, MH, SAVE, HALF, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1, dev = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raster<MW, MH, SAVE, HALF>, RT, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_raster<MW, MH, SAVE, HALF, STATS>, RT, sm);
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (occ < 1) occ = 1;
   const int grid = a.persistent_ctas > 0 ? a.persistent_ctas : sms * occ;
-  k_raster<MW, MH, SAVE, HALF><<<grid, RT, sm, st>>>(a, cap);
+  k_raster<MW, MH, SAVE, HALF, STATS><<<grid, RT, sm, st>>>(a, cap);
   note_launch();
   return cudaGetLastError();
 }
 
 template <int MW, int MH>
 cudaError_t launch_raster_shape(const RasterArgs& a, int cap, cudaStream_t st) {
-  if (a.prefix) return launch_raster_kernel<MW, MH, true, false>(a, cap, st);
-  return a.fp16 ? launch_raster_kernel<MW, MH, false, true>(a, cap, st)
-                : launch_raster_kernel<MW, MH, false, false>(a, cap, st);
+  if (a.exitrec) return launch_raster_kernel<MW, MH, true, false>(a, cap, st);
+  if (a.fp16) return launch_raster_kernel<MW, MH, false, true>(a, cap, st);
+  return a.profile ? launch_raster_kernel<MW, MH, false, false, true>(a, cap, st)
+                   : launch_raster_kernel<MW, MH, false, false>(a, cap, st);
 }
 
 }  // namespace

@@ -247,7 +247,8 @@ static void dispatcher(hg_server* S) {
 
 extern "C" hg_status hg_serve_create(hg_ctx* ctx, const hg_serve_config* cfg, hg_server** out) {
   if (!ctx || !cfg || !out || cfg->max_inflight < 1 || cfg->max_inflight > 64 || cfg->max_views_per_launch < 1 ||
-      cfg->max_views_per_launch > MAX_VIEWS) {
+      cfg->max_views_per_launch > MAX_VIEWS || cfg->presize_width < 0 || cfg->presize_height < 0 ||
+      cfg->presize_width > 16384 || cfg->presize_height > 16384) {
     hg_set_error("hg_serve_create: bad configuration");
     return HG_ERR_INVALID_ARG;
   }
@@ -270,11 +271,56 @@ extern "C" hg_status hg_serve_create(hg_ctx* ctx, const hg_serve_config* cfg, hg
   return HG_OK;
 }
 
+// Sizes a slot for a launch of max_views_per_launch views at the presize
+// resolution over n gaussians (pair capacity 3 n V and what follows from it),
+// so that no launch up to that size grows the slot on the request path.
+static hg_status presize_slot(hg_server* S, Slot& sl, long long n) {
+  const hg_serve_config& c = S->cfg;
+  hg_render_opts o = c.opts;
+  o.save_for_backward = 0;
+  o.flags = 0;
+  const int V = c.max_views_per_launch, W = c.presize_width, H = c.presize_height;
+  FrameGeom g;
+  g.V = V;
+  const int tx = (W + TILE - 1) / TILE, ty = (H + TILE - 1) / TILE;
+  const int mgx = (tx + o.macro_w - 1) / o.macro_w, mgy = (ty + o.macro_h - 1) / o.macro_h;
+  g.S = V * mgx * mgy;
+  g.total_tiles = V * tx * ty;
+  g.pixels = (long long)V * W * H;
+  g.max_nm = mgx * mgy;
+  hg_state* st = sl.state;
+  st->cap_pairs = std::max(st->cap_pairs, (size_t)(3 * n * V));
+  st->cap_batches = std::max(st->cap_batches, st->cap_pairs / (size_t)o.batch_cap + (size_t)g.S + 64);
+  st->cap_tiles = std::max(st->cap_tiles, st->cap_pairs / OS_TILE + 16);
+  st->cap_big_segs = std::max(st->cap_big_segs, std::min<size_t>((size_t)g.S, st->cap_pairs / TIER3_MAX + 16));
+  hg_status r = ensure_workspace(st, n, g, &o, sl.stream);
+  if (r != HG_OK) return r;
+  const size_t need = sizeof(float) * 3 * (size_t)g.pixels;
+  if (sl.out_bytes < need) {
+    if (sl.out) {
+      cudaStreamSynchronize(sl.stream);
+      ctx_free(S->ctx, sl.out, sl.out_bytes, sl.stream);
+    }
+    sl.out = (float*)ctx_alloc(S->ctx, need, sl.stream);
+    sl.out_bytes = sl.out ? need : 0;
+    if (!sl.out) return HG_ERR_OOM;
+  }
+  return HG_OK;
+}
+
 extern "C" hg_status hg_serve_add_scene(hg_server* S, hg_scene* scene, int* scene_id) {
   if (!S || !scene || !scene_id || scene->ctx != S->ctx) return HG_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(S->mu);
   S->scenes.push_back(scene);
   *scene_id = (int)S->scenes.size() - 1;
+  if (S->cfg.presize_width > 0 && S->cfg.presize_height > 0) {
+    long long n = 0;
+    for (const hg_scene* sc : S->scenes) n = std::max<long long>(n, sc->n);
+    for (Slot& sl : S->slots) {
+      const hg_status r = presize_slot(S, sl, n);
+      if (r != HG_OK) return r;
+    }
+  }
   return HG_OK;
 }
 

@@ -4,14 +4,20 @@
 //     (tiers <= 1K / 4K / 8K pairs), over the digits of (key - min key);
 //   * segments of 8K..16K pairs: one CTA sorts the two halves in shared
 //     memory the same way and merges them (merge path) into the output;
-//   * larger segments (> 16K): a segment-local onesweep (one kernel per 8-bit digit
-//     pass, decoupled look-back across the segment's tiles, tiles claimed in
-//     order through an atomic counter so every awaited predecessor is
-//     running), preceded by one histogram kernel for all four digits.
-// The fill pass writes a segment in a data-dependent order, so runs of equal
-// keys are re-sorted by id at the end (the id tie-break).
+//   * larger segments (> 16K): a segment-local onesweep (one kernel per 8-bit
+//     digit pass, decoupled look-back across the segment's tiles, tiles
+//     claimed in order through an atomic counter so every awaited
+//     predecessor is running), preceded by one histogram kernel for all
+//     digits.  Its passes are stable, so it sorts by the id's four digits
+//     first and then by the key's: (key, id) order with no fix-up.
+// The fill pass writes a segment in a data-dependent order, so the shared
+// memory tiers break key ties by id afterwards: runs of up to 32 equal keys
+// by insertion, and a segment with a longer run is sorted again by id, then
+// by key (stable passes), so the cost stays linear in the segment size
+// whatever the keys.
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -30,27 +36,15 @@ struct BlockSortSmem {
   uint32_t red[2][NT / 32];
 };
 
-__device__ __forceinline__ void sort_run_by_val(uint32_t* vals, int a, int b) {
-  for (int i = a + 1; i < b; ++i) {
-    uint32_t v = vals[i];
-    int j = i - 1;
-    while (j >= a && vals[j] > v) {
-      vals[j + 1] = vals[j];
-      --j;
-    }
-    vals[j + 1] = v;
-  }
-}
-
-// Sorts the n pairs of a shared-memory region ascending by (key, id): LSD
-// radix passes over the digits of (key - kmin) that can vary, the region's
-// n pairs spread evenly over the warps (rows = ceil(n / NT) item slots per
-// thread; slots [n, rows * NT) must hold key 0xffffffff and get digit 255,
-// so padding always ranks after the real pairs), then runs of equal keys
-// re-sorted by id (the fill order is data-dependent).
+// LSD radix passes over the digits of (x - xmin), x = keys[e] (by_val false)
+// or vals[e] (by_val true), of the n pairs of a shared-memory region, moving
+// both arrays: the region's pairs are spread evenly over the warps (rows =
+// ceil(n / NT) item slots per thread; slots [n, rows * NT) must hold key and
+// value 0xffffffff and get digit 255, so padding always ranks after the real
+// pairs).  Every pass is stable.
 template <int NT, int IPT>
-__device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int passes,
-                                            RankSmem<NT>& rank) {
+__device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int passes,
+                                             bool by_val, RankSmem<NT>& rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = (n + NT - 1) / NT;  // <= IPT
   for (int pass = 0; pass < passes; ++pass) {
@@ -62,7 +56,7 @@ __device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int 
       const int e = warp * 32 * rows + i * 32 + lane;
       k[i] = keys[e];
       v[i] = vals[e];
-      d[i] = e < n ? ((k[i] - kmin) >> shift) & 0xffu : 0xffu;
+      d[i] = e < n ? (((by_val ? v[i] : k[i]) - xmin) >> shift) & 0xffu : 0xffu;
     }
     block_rank_rows<NT, IPT>(d, p, rank, rows);
     __syncthreads();
@@ -74,15 +68,75 @@ __device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int 
     }
     __syncthreads();
   }
-  for (int j = tid; j < n; j += NT) {
-    const uint32_t kk = keys[j];
-    if ((j == 0 || keys[j - 1] != kk) && j + 1 < n && keys[j + 1] == kk) {
-      int e = j + 1;
-      while (e < n && keys[e] == kk) ++e;
-      sort_run_by_val(vals, j, e);
+}
+
+template <int NT>
+__device__ __forceinline__ void block_min_max(uint32_t& mn, uint32_t& mx, uint32_t (*red)[NT / 32]);
+__device__ __forceinline__ int radix_passes(uint32_t kmin, uint32_t kmax);
+
+// Longest run of equal keys whose ids one thread re-sorts by insertion.
+constexpr int TIE_RUN_MAX = 32;
+
+// Sorts the n pairs of a shared-memory region ascending by (key, id) (the
+// padding rule of radix_region applies): LSD passes over the digits of
+// (key - kmin), then the id tie-break.  Runs of equal keys of up to
+// TIE_RUN_MAX pairs are insertion-sorted by id, one thread per run; when the
+// region has a longer run it is sorted again from scratch, by id and then by
+// key, with stable passes (bounded work for any input: at most 8 passes).
+template <int NT, int IPT>
+__device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int passes,
+                                            RankSmem<NT>& rank, uint32_t (*red)[NT / 32], int* long_run) {
+  const int tid = threadIdx.x;
+  // stage 0: key passes; with a long tie run, stage 1: id passes, stage 2:
+  // key passes again (one copy of the pass loop serves all three)
+  uint32_t xmin = kmin;
+  for (int stage = 0;; ++stage) {
+    radix_region<NT, IPT>(keys, vals, n, xmin, passes, stage == 1, rank);
+    if (stage == 2) break;
+    if (stage == 1) {
+      uint32_t kmn = 0xffffffffu, kmx = 0;
+      for (int j = tid; j < n; j += NT) {
+        kmn = min(kmn, keys[j]);
+        kmx = max(kmx, keys[j]);
+      }
+      block_min_max<NT>(kmn, kmx, red);
+      xmin = kmn;
+      passes = radix_passes(kmn, kmx);
+      continue;
     }
+    if (tid == 0) *long_run = 0;
+    __syncthreads();
+    for (int j = tid; j < n; j += NT) {
+      const uint32_t kk = keys[j];
+      if ((j == 0 || keys[j - 1] != kk) && j + 1 < n && keys[j + 1] == kk) {
+        int e = j + 1;
+        while (e < n && e - j <= TIE_RUN_MAX && keys[e] == kk) ++e;
+        if (e - j > TIE_RUN_MAX) {
+          *long_run = 1;
+          continue;
+        }
+        for (int i = j + 1; i < e; ++i) {
+          const uint32_t v = vals[i];
+          int q = i - 1;
+          while (q >= j && vals[q] > v) {
+            vals[q + 1] = vals[q];
+            --q;
+          }
+          vals[q + 1] = v;
+        }
+      }
+    }
+    __syncthreads();
+    if (!*long_run) break;
+    uint32_t vmn = 0xffffffffu, vmx = 0;
+    for (int j = tid; j < n; j += NT) {
+      vmn = min(vmn, vals[j]);
+      vmx = max(vmx, vals[j]);
+    }
+    block_min_max<NT>(vmn, vmx, red);
+    xmin = vmn;
+    passes = radix_passes(vmn, vmx);
   }
-  __syncthreads();
 }
 
 // Block-wide min and max of one value per thread (red: [2][NT / 32]).
@@ -125,10 +179,11 @@ __device__ __forceinline__ uint32_t claim_segment(FrameCounters* fc, int tier, u
 // One CTA per segment (claimed from the tier's list): the segment is loaded
 // into shared memory, sorted there (sort_region) and written back.
 template <int NT, int IPT>
-__global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
+__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<NT, IPT>& s = *reinterpret_cast<BlockSortSmem<NT, IPT>*>(smem_raw);
   __shared__ uint32_t s_claim;
+  __shared__ int s_long_run;
   if (read_status(a.fc)) return;
   const uint32_t count = a.fc->tier_count[tier];
   const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
@@ -154,7 +209,7 @@ __global__ void __launch_bounds__(NT) k_block_sort(SortArgs a, int tier) {
       s.vals[j] = v;
     }
     block_min_max<NT>(kmin, kmax, s.red);
-    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_passes(kmin, kmax), s.rank);
+    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_passes(kmin, kmax), s.rank, s.red, &s_long_run);
     for (int j = tid; j < n; j += NT) {
       a.keys[start + j] = s.keys[j];
       a.vals[start + j] = s.vals[j];
@@ -187,6 +242,7 @@ __global__ void __launch_bounds__(NT) k_block_merge_sort(SortArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MergeSortSmem<NT, IPT>& s = *reinterpret_cast<MergeSortSmem<NT, IPT>*>(smem_raw);
   __shared__ uint32_t s_claim;
+  __shared__ int s_long_run;
   if (read_status(a.fc)) return;
   const uint32_t count = a.fc->tier_count[tier];
   const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
@@ -223,8 +279,8 @@ __global__ void __launch_bounds__(NT) k_block_merge_sort(SortArgs a, int tier) {
     }
     block_min_max<NT>(kmin, kmax, s.red);
     const int passes = radix_passes(kmin, kmax);
-    sort_region<NT, IPT>(s.keys, s.vals, hA, kmin, passes, s.rank);
-    sort_region<NT, IPT>(s.keys + H, s.vals + H, hB, kmin, passes, s.rank);
+    sort_region<NT, IPT>(s.keys, s.vals, hA, kmin, passes, s.rank, s.red, &s_long_run);
+    sort_region<NT, IPT>(s.keys + H, s.vals + H, hB, kmin, passes, s.rank, s.red, &s_long_run);
     const uint32_t *ka = s.keys, *va = s.vals, *kb = s.keys + H, *vb = s.vals + H;
     const int per = (n + NT - 1) / NT;
     const int d0 = min(n, tid * per), d1 = min(n, d0 + per);
@@ -269,20 +325,40 @@ struct OneSweepSmem {
 
 
 
+// Digit histograms of every pass for each onesweep segment, and the clearing
+// of the tiles' look-back words.  Pass p sorts by digit p % sizeof(K) of its
+// key word: with `lo` set (32-bit keys, NPASS = 8) passes 0-3 take the
+// digits of lo[] (the values, sorted first) and passes 4-7 those of keys[];
+// otherwise pass p takes digit p of keys[].  Every tile's look-back words of
+// every pass ([NPASS][lb_stride] words, 256 per tile) are zeroed here, so
+// the passes need no memset; seg_hist must be zero on entry.
 template <typename K, int NPASS>
-__global__ void __launch_bounds__(OS_THREADS) k_os_hist(OsTileView tv, const K* keys, uint32_t* seg_hist,
+__global__ void __launch_bounds__(OS_THREADS) k_os_hist(OsTileView tv, const K* keys, const uint32_t* lo,
+                                                        uint32_t* seg_hist, uint32_t* lookback, size_t lb_stride,
                                                         FrameCounters* fc) {
+  constexpr int DIG = (int)sizeof(K);
   __shared__ uint32_t h[NPASS][256];
   if (read_status(fc)) return;
   const uint32_t nt = *tv.tile_count;
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-    for (int j = threadIdx.x; j < NPASS * 256; j += OS_THREADS) (&h[0][0])[j] = 0;
+    for (int j = threadIdx.x; j < NPASS * 256; j += OS_THREADS) {
+      (&h[0][0])[j] = 0;
+      lookback[(size_t)(j >> 8) * lb_stride + (size_t)t * 256 + (j & 255)] = 0;
+    }
     __syncthreads();
     const uint4 td = tv.tiles[t];
     for (uint32_t j = threadIdx.x; j < td.z; j += OS_THREADS) {
-      K k = keys[td.y + j];
+      const K k = keys[td.y + j];
+      if (lo) {
+        const uint32_t l = lo[td.y + j];
 #pragma unroll
-      for (int p = 0; p < NPASS; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 0xffu], 1u);
+        for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(l >> (8 * p)) & 0xffu], 1u);
+#pragma unroll
+        for (int p = 4; p < NPASS; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * (p - 4))) & 0xffu], 1u);
+      } else {
+#pragma unroll
+        for (int p = 0; p < NPASS; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * (p % DIG))) & 0xffu], 1u);
+      }
     }
     __syncthreads();
     uint32_t* dst = seg_hist + (size_t)td.x * NPASS * 256;
@@ -294,15 +370,21 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_hist(OsTileView tv, const K* 
   }
 }
 
+// One stable pass: every tile of the segments is ranked by digit
+// pass % sizeof(K) of src_k in shared memory and scattered to the segment's
+// output ranges (digit offsets from the segment histogram of this pass plus
+// the exclusive prefix of the earlier tiles, found by decoupled look-back in
+// this pass's look-back words).
 template <typename K, int NPASS>
 __global__ void __launch_bounds__(OS_THREADS) k_os_pass(OsTileView tv, const K* src_k, const uint32_t* src_v,
                                                         K* dst_k, uint32_t* dst_v, uint32_t* lookback,
-                                                        uint32_t* claim, int pass, FrameCounters* fc) {
+                                                        uint32_t* claim, int pass, uint32_t wait_polls,
+                                                        FrameCounters* fc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   OneSweepSmem<K>& s = *reinterpret_cast<OneSweepSmem<K>*>(smem_raw);
   if (read_status(fc)) return;
   const uint32_t nt = *tv.tile_count;
-  const int shift = 8 * pass;
+  const int shift = 8 * (pass % (int)sizeof(K));
   const int tid = threadIdx.x;
   while (true) {
     if (tid == 0) s.tile_claim = atomicAdd(claim, 1u);
@@ -346,7 +428,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(OsTileView tv, const K* 
           uint32_t val = *w;
           uint32_t it = 0;
           while ((val & ~LB_MASK) == 0) {
-            if (++it > SPIN_LIMIT) {
+            if (++it > wait_polls) {
               ok = false;
               break;
             }
@@ -405,26 +487,6 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(OsTileView tv, const K* 
   }
 }
 
-// equal keys inside big segments: order by id (runs may cross tiles)
-__global__ void k_os_fixup(OsTileView tv, uint32_t* keys, uint32_t* vals, FrameCounters* fc) {
-  if (read_status(fc)) return;
-  const uint32_t nt = *tv.tile_count;
-  for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
-    const uint4 td = tv.tiles[t];
-    const uint32_t seg = tv.big_segs[td.x];
-    const uint32_t s0 = tv.seg_off[seg], s1 = tv.seg_off[seg + 1];
-    for (uint32_t j = threadIdx.x; j < td.z; j += blockDim.x) {
-      uint32_t g = td.y + j;
-      uint32_t kk = keys[g];
-      if ((g == s0 || keys[g - 1] != kk) && g + 1 < s1 && keys[g + 1] == kk) {
-        uint32_t e = g + 1;
-        while (e < s1 && keys[e] == kk) ++e;
-        sort_run_by_val(vals, (int)g, (int)e);
-      }
-    }
-  }
-}
-
 static int g_sms = 0;
 static int num_sms() {
   if (!g_sms) {
@@ -447,50 +509,93 @@ static cudaError_t launch_tier(const SortArgs& a, int tier, int blocks_per_sm, c
 }
 
 template <typename K, int NPASS>
-cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt,
-                            uint32_t* seg_hist, size_t seg_hist_words, uint32_t* lookback, size_t lookback_words,
-                            uint32_t* claims, int first_pass, int npass, FrameCounters* fc, cudaStream_t st,
-                            bool* result_in_alt) {
-  cudaError_t e = cudaMemsetAsync(seg_hist, 0, seg_hist_words * 4, st);
-  if (e != cudaSuccess) return e;
-  const int grid = num_sms() * 2;
-  k_os_hist<K, NPASS><<<grid, OS_THREADS, 0, st>>>(tv, keys, seg_hist, fc);
+static cudaError_t os_passes(const OsTileView& tv, const K* keys, const uint32_t* lo, uint32_t* seg_hist,
+                             size_t seg_hist_words, bool zero_hist, uint32_t* lookback, size_t lb_stride,
+                             FrameCounters* fc, cudaStream_t st, int* occ_out, int max_ctas = 0) {
+  cudaError_t e;
+  if (zero_hist && (e = cudaMemsetAsync(seg_hist, 0, seg_hist_words * 4, st)) != cudaSuccess) return e;
+  const int hgrid = max_ctas > 0 ? min(max_ctas, num_sms() * 2) : num_sms() * 2;
+  k_os_hist<K, NPASS><<<hgrid, OS_THREADS, 0, st>>>(tv, keys, lo, seg_hist, lookback, lb_stride, fc);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  size_t sm = sizeof(OneSweepSmem<K>);
+  const size_t sm = sizeof(OneSweepSmem<K>);
   e = cudaFuncSetAttribute(k_os_pass<K, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_os_pass<K, NPASS>, OS_THREADS, sm);
-  if (occ < 1) occ = 1;
+  *occ_out = occ < 1 ? 1 : occ;
+  return cudaSuccess;
+}
+
+template <typename K, int NPASS>
+cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt,
+                            uint32_t* seg_hist, size_t seg_hist_words, bool zero_hist, uint32_t* lookback,
+                            size_t lb_stride, uint32_t* claims, int first_pass, int npass, uint32_t wait_polls,
+                            FrameCounters* fc, cudaStream_t st, bool* result_in_alt) {
+  int occ = 1;
+  cudaError_t e = os_passes<K, NPASS>(tv, keys, nullptr, seg_hist, seg_hist_words, zero_hist, lookback, lb_stride,
+                                      fc, st, &occ);
+  if (e != cudaSuccess) return e;
+  const size_t sm = sizeof(OneSweepSmem<K>);
   K* sk = keys;
   uint32_t* sv = vals;
   K* dk = keys_alt;
   uint32_t* dv = vals_alt;
   for (int p = first_pass; p < first_pass + npass; ++p) {
-    e = cudaMemsetAsync(lookback, 0, lookback_words * 4, st);
-    if (e != cudaSuccess) return e;
-    k_os_pass<K, NPASS><<<num_sms() * occ, OS_THREADS, sm, st>>>(tv, sk, sv, dk, dv, lookback, claims + p, p, fc);
+    k_os_pass<K, NPASS><<<num_sms() * occ, OS_THREADS, sm, st>>>(tv, sk, sv, dk, dv, lookback + (size_t)p * lb_stride,
+                                                                claims + p, p, wait_polls, fc);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    K* tk = sk;
-    sk = dk;
-    dk = tk;
-    uint32_t* tvv = sv;
-    sv = dv;
-    dv = tvv;
+    std::swap(sk, dk);
+    std::swap(sv, dv);
   }
   *result_in_alt = (npass & 1) != 0;
   return cudaSuccess;
 }
 
 template cudaError_t launch_onesweep<unsigned long long, 8>(const OsTileView&, unsigned long long*, uint32_t*,
-                                                            unsigned long long*, uint32_t*, uint32_t*, size_t,
-                                                            uint32_t*, size_t, uint32_t*, int, int,
+                                                            unsigned long long*, uint32_t*, uint32_t*, size_t, bool,
+                                                            uint32_t*, size_t, uint32_t*, int, int, uint32_t,
                                                             FrameCounters*, cudaStream_t, bool*);
 template cudaError_t launch_onesweep<uint32_t, 4>(const OsTileView&, uint32_t*, uint32_t*, uint32_t*, uint32_t*,
-                                                  uint32_t*, size_t, uint32_t*, size_t, uint32_t*, int, int,
-                                                  FrameCounters*, cudaStream_t, bool*);
+                                                  uint32_t*, size_t, bool, uint32_t*, size_t, uint32_t*, int, int,
+                                                  uint32_t, FrameCounters*, cudaStream_t, bool*);
+
+// Segments sorted ascending by (key, value): four stable passes over the
+// value's digits, then four over the key's (8 passes, so the result ends in
+// keys / vals).  seg_hist holds [segments][8][256] words, lookback
+// [8][lb_stride] words.  max_ctas > 0 caps the persistent grids: any grid is
+// correct (tiles are claimed in order, so every awaited predecessor is held
+// by a running CTA), and a small one keeps the passes of a frame without
+// big segments from taking SM slots the shared-memory tiers run on.
+static cudaError_t launch_onesweep_by_val_key(const OsTileView& tv, uint32_t* keys, uint32_t* vals,
+                                              uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* seg_hist,
+                                              size_t seg_hist_words, bool zero_hist, uint32_t* lookback,
+                                              size_t lb_stride, uint32_t* claims, uint32_t wait_polls,
+                                              FrameCounters* fc, cudaStream_t st, int max_ctas = 0) {
+  int occ = 1;
+  cudaError_t e = os_passes<uint32_t, 8>(tv, keys, vals, seg_hist, seg_hist_words, zero_hist, lookback, lb_stride,
+                                         fc, st, &occ, max_ctas);
+  if (e != cudaSuccess) return e;
+  const size_t sm = sizeof(OneSweepSmem<uint32_t>);
+  const int grid = max_ctas > 0 ? min(max_ctas, num_sms() * occ) : num_sms() * occ;
+  uint32_t *ck = keys, *cv = vals, *ak = keys_alt, *av = vals_alt;
+  for (int p = 0; p < 8; ++p) {
+    // value passes move (value, key) pairs, key passes (key, value) pairs
+    uint32_t* sk = p < 4 ? cv : ck;
+    uint32_t* sv = p < 4 ? ck : cv;
+    uint32_t* dk = p < 4 ? av : ak;
+    uint32_t* dv = p < 4 ? ak : av;
+    k_os_pass<uint32_t, 8><<<grid, OS_THREADS, sm, st>>>(tv, sk, sv, dk, dv,
+                                                                    lookback + (size_t)p * lb_stride, claims + p, p,
+                                                                    wait_polls, fc);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::swap(ck, ak);
+    std::swap(cv, av);
+  }
+  return cudaSuccess;
+}
 
 template <int NT, int IPT>
 static cudaError_t launch_merge_tier(const SortArgs& a, int tier, cudaStream_t st) {
@@ -513,14 +618,9 @@ static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaS
   if ((e = launch_tier<512, 8>(a, 1, 2, s1)) != cudaSuccess) return e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
-  bool alt = false;
-  e = launch_onesweep<uint32_t, 4>(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist,
-                                   (size_t)a.cap_big_segs * 4 * 256, a.lookback, (size_t)a.cap_tiles * 256,
-                                   a.fc->os_claim, 0, 4, a.fc, st, &alt);
-  if (e != cudaSuccess) return e;
-  k_os_fixup<<<num_sms() * 4, 256, 0, st>>>(tv, a.keys, a.vals, a.fc);
-  note_launch();
-  return cudaGetLastError();
+  // the partition zeroed the big segments' histograms
+  return launch_onesweep_by_val_key(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist, 0, false, a.lookback,
+                                    (size_t)a.cap_tiles * 256, a.fc->os_claim, a.wait_polls, a.fc, st, a.os_ctas);
 }
 
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st, const SortStreams* ss) {
@@ -556,8 +656,9 @@ constexpr uint32_t NA_MAX_TILES = NA_MAX_PAIRS / OS_TILE + NA_MAX_SEGS;
 constexpr size_t NA_FC_WORDS = 64;
 constexpr size_t NA_TILE_WORDS = (size_t)NA_MAX_TILES * 4;
 constexpr size_t NA_SEGS_WORDS = (size_t)NA_MAX_SEGS * 2;
-constexpr size_t NA_HIST_WORDS = (size_t)NA_MAX_SEGS * 4 * 256;
-constexpr size_t NA_LB_WORDS = (size_t)NA_MAX_TILES * 256;
+constexpr size_t NA_HIST_WORDS = (size_t)NA_MAX_SEGS * 8 * 256;     // [segment][pass][digit]
+constexpr size_t NA_LB_STRIDE = (size_t)NA_MAX_TILES * 256;           // look-back words of one pass
+constexpr size_t NA_LB_WORDS = 8 * NA_LB_STRIDE;
 constexpr size_t NA_PP_WORDS = (size_t)NA_MAX_PAIRS * 2;
 constexpr size_t NA_WORDS = NA_FC_WORDS + NA_TILE_WORDS + NA_SEGS_WORDS + NA_HIST_WORDS + NA_LB_WORDS + NA_PP_WORDS;
 
@@ -612,6 +713,12 @@ static void* noalloc_scratch(int dev, hg_status* st) {
   return addr[dev];
 }
 
+// [a, a + n) and [b, b + n) share a byte
+static bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
 extern "C" hg_status hg_segmented_sort_noalloc(const uint32_t* d_seg_off, int n_seg, int64_t n_pairs,
                                                const uint32_t* d_keys_in, const uint32_t* d_vals_in,
                                                uint32_t* d_keys_out, uint32_t* d_vals_out, void* stream) {
@@ -625,13 +732,37 @@ extern "C" hg_status hg_segmented_sort_noalloc(const uint32_t* d_seg_off, int n_
                  std::to_string(n_pairs) + " pairs, " + std::to_string(n_seg) + " segments)");
     return HG_ERR_INVALID_ARG;
   }
+  const size_t bytes = 4 * (size_t)n_pairs;
+  if (n_pairs > 0) {
+    // an output may be its own input (in place); no other overlap
+    const bool in_place = d_keys_in == d_keys_out && d_vals_in == d_vals_out;
+    const bool bad = overlaps(d_keys_out, d_vals_out, bytes) ||
+                     (!in_place && (overlaps(d_keys_out, d_keys_in, bytes) || overlaps(d_keys_out, d_vals_in, bytes) ||
+                                    overlaps(d_vals_out, d_keys_in, bytes) || overlaps(d_vals_out, d_vals_in, bytes))) ||
+                     (in_place && overlaps(d_keys_in, d_vals_in, bytes));
+    if (bad) {
+      hg_set_error("hg_segmented_sort_noalloc: overlapping buffers (only keys_out == keys_in together with "
+                   "vals_out == vals_in is allowed)");
+      return HG_ERR_INVALID_ARG;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    // the call synchronises the stream, which a capture cannot do
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc");
+    if (cs != cudaStreamCaptureStatusNone) {
+      hg_set_error("hg_segmented_sort_noalloc: the stream is capturing; the call synchronises it");
+      return HG_ERR_INVALID_ARG;
+    }
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc");
   hg_status st;
   uint32_t* base = (uint32_t*)noalloc_scratch(dev, &st);
   if (!base) return st;
-  cudaStream_t s = (cudaStream_t)stream;
   // the segment table must be an ordered partition of [0, n_pairs)
   uint32_t off[NA_MAX_SEGS + 1];
   if ((e = cudaMemcpyAsync(off, d_seg_off, sizeof(uint32_t) * (n_seg + 1), cudaMemcpyDeviceToHost, s)) !=
@@ -657,23 +788,23 @@ extern "C" hg_status hg_segmented_sort_noalloc(const uint32_t* d_seg_off, int n_
   uint32_t* pp_k = lb + NA_LB_WORDS;
   uint32_t* pp_v = pp_k + NA_MAX_PAIRS;
   // the array keeps the previous call's contents: clear what starts at zero
-  if ((e = cudaMemsetAsync(fc, 0, NA_FC_WORDS * 4, s)) != cudaSuccess)
+  // (the counters and the digit histograms; the histogram kernel clears the
+  // look-back words of the tiles it finds)
+  if ((e = cudaMemsetAsync(fc, 0, NA_FC_WORDS * 4, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(hist, 0, (size_t)n_seg * 8 * 256 * 4, s)) != cudaSuccess)
     return hg_cuda_status(e, "hg_segmented_sort_noalloc clear");
-  if ((e = cudaMemcpyAsync(d_keys_out, d_keys_in, 4 * (size_t)n_pairs, cudaMemcpyDeviceToDevice, s)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(d_vals_out, d_vals_in, 4 * (size_t)n_pairs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+  if (d_keys_out != d_keys_in &&
+      ((e = cudaMemcpyAsync(d_keys_out, d_keys_in, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(d_vals_out, d_vals_in, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess))
     return hg_cuda_status(e, "hg_segmented_sort_noalloc copy");
   k_na_tiles<<<1, 1024, 0, s>>>(d_seg_off, n_seg, tiles, segs, tile_first, fc);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc tiles");
   OsTileView tv{tiles, &fc->n_big_tiles, hist, d_seg_off, segs, tile_first};
-  bool alt = false;
-  e = launch_onesweep<uint32_t, 4>(tv, d_keys_out, d_vals_out, pp_k, pp_v, hist, NA_HIST_WORDS, lb, NA_LB_WORDS,
-                                   fc->os_claim, 0, 4, fc, s, &alt);
+  // by value, then by key: (key, value) order for any input, no fix-up
+  e = launch_onesweep_by_val_key(tv, d_keys_out, d_vals_out, pp_k, pp_v, hist, 0, false, lb, NA_LB_STRIDE,
+                                 fc->os_claim, SPIN_LIMIT, fc, s);
   if (e != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc passes");
-  k_os_fixup<<<num_sms() * 4, 256, 0, s>>>(tv, d_keys_out, d_vals_out, fc);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return hg_cuda_status(e, "hg_segmented_sort_noalloc fixup");
   int status = 0;
   if ((e = cudaMemcpyAsync(&status, &fc->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)

@@ -22,7 +22,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error"
 PATH_HIGS, PATH_PLAIN = 0, 1
 BIN_RECT, BIN_ELLIPSE = 0, 1
 FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT, FLAG_PROFILE, FLAG_FP16 = 1, 2, 4, 8, 16, 32
-BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE = range(6)
+(BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE, BUF_PLAIN_KEYS, BUF_PLAIN_IDS,
+ BUF_TILE_RANGES, BUF_GRAD2D) = range(10)
 
 EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",
            "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",
@@ -31,7 +32,16 @@ EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_
            "hg_kernel_launches", "hg_segmented_sort_noalloc", "hg_render_backward", "hg_autotune",
            "hg_serve_create", "hg_serve_add_scene", "hg_serve_submit", "hg_serve_poll", "hg_serve_wait",
            "hg_serve_cancel", "hg_serve_stats", "hg_serve_reset_stats", "hg_serve_destroy", "hg_l2_loss",
-           "hg_adam_step", "hg_scene_sh_codec", "hg_spatial_order", "hg_scene_order"]
+           "hg_adam_step", "hg_scene_sh_codec", "hg_spatial_order", "hg_scene_order", "hg_ctx_set_wait_limits"]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class AllocatorC(C.Structure):
+    """hg_allocator: device memory callbacks of a context."""
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
 
 
 class AdamOpts(C.Structure):
@@ -69,7 +79,8 @@ class RenderOpts(C.Structure):
 
 class ServeConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("max_views_per_launch", C.c_int32), ("mem_budget_bytes", C.c_int64),
-                ("batch_window_us", C.c_int32), ("pad", C.c_int32), ("opts", RenderOpts)]
+                ("batch_window_us", C.c_int32), ("presize_width", C.c_int32), ("presize_height", C.c_int32),
+                ("pad", C.c_int32), ("opts", RenderOpts)]
 
 
 class ServeStats(C.Structure):
@@ -93,7 +104,8 @@ class FrameStats(C.Structure):
                 ("n_replays", C.c_int64), ("raster_evals", C.c_int64), ("status", C.c_int32),
                 ("pad", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
                 ("ms_sort", C.c_float), ("ms_raster", C.c_float), ("ms_merge", C.c_float),
-                ("ms_total", C.c_float), ("raster_cycles", C.c_int64 * 6)]
+                ("ms_total", C.c_float), ("raster_cycles", C.c_int64 * 6), ("pixel_support_evals", C.c_int64),
+                ("pixel_contrib_evals", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "seg_by_tier", "raster_cycles")}
@@ -170,6 +182,8 @@ def load(path: str = LIB_PATH):
     lib.hg_segmented_sort_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p]
     lib.hg_ctx_create.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.hg_ctx_set_wait_limits.restype = C.c_int
+    lib.hg_ctx_set_wait_limits.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
     lib.hg_ctx_destroy.argtypes = [C.c_void_p]
     lib.hg_create_scene.argtypes = [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(C.c_void_p)]
     lib.hg_destroy_scene.argtypes = [C.c_void_p]
@@ -237,15 +251,56 @@ class Options:
         return o
 
 
-class Context:
-    """hg_ctx on one CUDA device (workspace from cudaMalloc)."""
+def torch_allocator(device: int):
+    """(alloc, free) callbacks of an hg_allocator backed by the torch caching
+    allocator on `device`: workspace and scene memory of the library then
+    comes from (and returns to) the same pool as the caller's tensors.  The
+    library frees a buffer only after the work that used it has finished
+    (it synchronises first), so a block may be reused on any stream."""
+    import torch
 
-    def __init__(self, device: int = 0):
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:  # out of memory (or any failure): the library reports HG_ERR_OOM
+            return None
+
+    def free(ptr, nbytes, stream, user):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+    return alloc, free
+
+
+class Context:
+    """hg_ctx on one CUDA device.  allocator: "torch" (default) backs the
+    library's device memory with the torch caching allocator; "cuda" lets
+    the library call cudaMalloc / cudaFree; or an (alloc, free) pair of
+    Python callables with the hg_allocator signatures (alloc(bytes, stream,
+    user) -> device address or None; free(ptr, bytes, stream, user))."""
+
+    def __init__(self, device: int = 0, allocator="torch"):
         self.lib = load()
         h = C.c_void_p()
-        check(self.lib.hg_ctx_create(device, None, C.byref(h)))
+        self._alloc = None
+        if allocator == "torch":
+            allocator = torch_allocator(device)
+        if allocator == "cuda" or allocator is None:
+            check(self.lib.hg_ctx_create(device, None, C.byref(h)))
+        else:
+            fa, ff = allocator
+            # the callbacks must outlive the context: kept on self
+            self._alloc = AllocatorC(ALLOC_FN(fa), FREE_FN(ff), None)
+            check(self.lib.hg_ctx_create(device, C.byref(self._alloc), C.byref(h)))
         self.h = h
         self.device = device
+
+    def set_wait_limits(self, wait_polls: int = -1, chain_polls: int = -1):
+        """hg_ctx_set_wait_limits: polls before a bounded device wait gives
+        up (mbarrier / look-back) and before a batch renders unchained; 0
+        gives up at once, -1 restores the default."""
+        check(self.lib.hg_ctx_set_wait_limits(self.h, int(wait_polls), int(chain_polls)))
 
     def close(self):
         if self.h:
@@ -409,9 +464,38 @@ class Graph:
             pass
 
 
+def check_sort_args(seg_off, keys, vals, keys_out, vals_out, require_cuda: bool = True):
+    """Raise ValueError unless the five tensors of segmented_sort_noalloc fit
+    the entry point: contiguous 4-byte integer tensors (seg_off int32 or
+    uint32 with at least 2 entries, the pairs int32 / uint32 / float32 bit
+    patterns), keys, vals, keys_out and vals_out of the same length, and, with
+    require_cuda, all on the current CUDA device."""
+    import torch
+    named = (("seg_off", seg_off), ("keys", keys), ("vals", vals), ("keys_out", keys_out), ("vals_out", vals_out))
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if require_cuda:
+            if not t.is_cuda or t.device.index != torch.cuda.current_device():
+                raise ValueError(f"{name} must be a CUDA tensor on the current device")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if seg_off.dtype not in (torch.int32, torch.uint32):
+        raise ValueError("seg_off must be int32 or uint32")
+    if seg_off.numel() < 2:
+        raise ValueError("seg_off needs at least 2 entries (one segment)")
+    for name, t in named[1:]:
+        if t.dtype not in (torch.int32, torch.uint32, torch.float32):
+            raise ValueError(f"{name} must have a 4-byte dtype (int32, uint32 or float32)")
+        if t.numel() != keys.numel():
+            raise ValueError(f"{name} has {t.numel()} elements, keys has {keys.numel()}")
+
+
 def segmented_sort_noalloc(seg_off, keys, vals, keys_out, vals_out, stream=None) -> int:
     """hg_segmented_sort_noalloc on device int32/uint32 tensors; returns the
-    hg_status (no exception) so callers can inspect rejections."""
+    hg_status (no exception) so callers can inspect rejections.  Malformed
+    tensors raise ValueError before the library is called."""
+    check_sort_args(seg_off, keys, vals, keys_out, vals_out)
     return int(load().hg_segmented_sort_noalloc(C.c_void_p(seg_off.data_ptr()), int(seg_off.numel()) - 1,
                                                 int(keys.numel()), C.c_void_p(keys.data_ptr()),
                                                 C.c_void_p(vals.data_ptr()), C.c_void_p(keys_out.data_ptr()),
@@ -574,10 +658,13 @@ class Server:
     """Continuous-batching render server (hg_serve_*)."""
 
     def __init__(self, ctx: Context, max_inflight: int = 4, max_views_per_launch: int = 8, mem_budget_bytes: int = 0,
-                 batch_window_us: int = 0, opts: Options | None = None):
+                 batch_window_us: int = 0, opts: Options | None = None, presize=(0, 0)):
+        """presize=(W, H): size every slot, when a scene is added, for
+        max_views_per_launch views at W x H (no workspace growth while
+        serving up to that size)."""
         self.ctx, self.lib = ctx, ctx.lib
-        cfg = ServeConfig(max_inflight, max_views_per_launch, mem_budget_bytes, batch_window_us, 0,
-                          (opts or Options()).struct())
+        cfg = ServeConfig(max_inflight, max_views_per_launch, mem_budget_bytes, batch_window_us, int(presize[0]),
+                          int(presize[1]), 0, (opts or Options()).struct())
         h = C.c_void_p()
         check(self.lib.hg_serve_create(ctx.h, C.byref(cfg), C.byref(h)))
         self.h = h

@@ -160,6 +160,25 @@ def cluster_scene(n: int, n_clusters: int, zipf: float, seed: int = 0,
                          "extent": extent}))
 
 
+# Higher-order SH whose energy falls with the degree: band l >= 1 drawn from
+# N(0, 0.2 * DECAY^l).  A stand-in for trained scenes, whose view-dependent
+# colour is a small correction of the base colour (the i.i.d. N(0, 0.2) of
+# the configs gives every band the DC band's spread).
+SH_DECAY = 0.25
+
+
+def decaying_sh(scene: Scene, seed: int = 5, decay: float = SH_DECAY) -> Scene:
+    """Copy of a degree-3 scene with its bands 1-3 redrawn from N(0, 0.2
+    decay^l) (the DC band kept)."""
+    g = rng(seed)
+    out = scene.copy()
+    sh = out.sh.copy()
+    for l in range(1, scene.sh_degree + 1):
+        sh[:, l * l:(l + 1) * (l + 1)] = g.normal(0.0, 0.2 * decay ** l, sh[:, l * l:(l + 1) * (l + 1)].shape)
+    out.sh = sh.astype(np.float32)
+    return out
+
+
 def perturbed(scene: Scene, seed: int = 1, mean_sigma: float = 1e-3,
               logit_sigma: float = 0.1) -> Scene:
     """Copy with means + N(0, mean_sigma) and opacity logits + N(0, logit_sigma)."""

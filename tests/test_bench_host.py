@@ -16,7 +16,7 @@ def test_roofline_figures_follow_the_stated_bytes_and_ops():
     n, vis, pairs, evals = 1_000_000, 3_000_000, 4_000_000, 350_000_000
     stage_ms = {"project": 0.2, "partition": 0.1, "sort": 0.15, "raster": 0.6, "merge": 0.03}
     pk = {"hbm_gbs": 6795.8, "sm_max_mhz": 2070.0}
-    top, out = bench.roofline(stage_ms, _stats(vis, pairs, evals), n, pk, 2070.0)
+    top, out = bench.roofline(stage_ms, _stats(vis, pairs, evals), n, pk, 2070.0, 152)
     assert top == "raster"
     vis_bits = bench.VIEWS * ((n + 31) // 32) * 4
     # projection: 236 bytes read per gaussian, 68 written per visible entry
@@ -33,6 +33,9 @@ def test_roofline_figures_follow_the_stated_bytes_and_ops():
     assert out["raster"]["achieved"] == pytest.approx(ops / 0.6e-3 / 1e12, abs=0.01)
     assert out["raster"]["frac"] == pytest.approx(out["raster"]["achieved"] / peak, abs=1e-3)
     assert {v["bound"] for v in out.values()} == {"hbm", "alu"}
+    # the SM count is the device's, not a constant
+    _, out148 = bench.roofline(stage_ms, _stats(vis, pairs, evals), n, pk, 2070.0, 148)
+    assert out148["raster"]["peak"] == pytest.approx(148 * 128 * 2070e6 / 1e12, abs=0.05)
 
 
 def test_captured_traffic_only_for_the_sources_it_was_taken_on(monkeypatch):

@@ -57,3 +57,27 @@ def test_binding_refuses_missing_library(tmp_path):
             higs.load(str(tmp_path / "nope.so"))
     finally:
         higs._lib = saved
+
+
+def test_noalloc_sort_argument_checks_without_gpu():
+    """The binding rejects malformed tensors before it calls the library."""
+    import torch
+    from paper_2606_00352_gb300 import higs
+    n = 16
+    off = torch.tensor([0, n], dtype=torch.int32)
+    k = torch.zeros(n, dtype=torch.int32)
+    good = (off, k, k.clone(), k.clone(), k.clone())
+    higs.check_sort_args(*good, require_cuda=False)
+    with pytest.raises(ValueError, match="CUDA"):
+        higs.check_sort_args(*good)
+    bad_cases = [
+        ((off.to(torch.int64),) + good[1:], "seg_off must be int32"),
+        ((off[:1],) + good[1:], "at least 2"),
+        ((off, k.to(torch.int64)) + good[2:], "4-byte"),
+        ((off, k, k[:n - 1].clone(), k.clone(), k.clone()), "elements"),
+        ((off, k, k.clone(), torch.zeros(2 * n, dtype=torch.int32)[::2], k.clone()), "contiguous"),
+        ((off, k, k.clone(), k.clone(), k[:4].clone()), "elements"),
+    ]
+    for args, msg in bad_cases:
+        with pytest.raises(ValueError, match=msg):
+            higs.check_sort_args(*args, require_cuda=False)

@@ -187,6 +187,54 @@ def test_discrete_stages_all_tiers(lib, ctx):
     assert all(st["seg_by_tier"][t] > 0 for t in range(5))
 
 
+def _plain_gate(lib, ctx, projs, cams):
+    """Render oracle records through the plain per-tile path (hg_render_splats,
+    PATH_PLAIN) and compare its sorted 64-bit keys, record ids and tile
+    ranges bit-exactly with the oracle's per-tile pair list."""
+    import torch
+    n = projs[0]["n"]
+    d = lib.splats_to_device(splat_records(projs, lib.SPLAT_DTYPE))
+    st = lib.State(ctx)
+    lib.render_splats(ctx, d, n, cams, lib.Options(path=lib.PATH_PLAIN), state=st)
+    torch.cuda.synchronize()
+    keys = st.read(lib.BUF_PLAIN_KEYS, np.uint64)
+    ids = st.read(lib.BUF_PLAIN_IDS).astype(np.int64)
+    ranges = st.read(lib.BUF_TILE_RANGES).reshape(-1, 2).astype(np.int64)
+    ref_k, ref_i, ref_r = BN.plain_tile_pairs([BN.records_f32(p) for p in projs], [(c.width, c.height) for c in cams])
+    assert len(keys) == len(ref_k) > 0
+    assert np.array_equal(keys, ref_k)
+    assert np.array_equal(ids, ref_i)
+    assert np.array_equal(ranges, ref_r)
+    with pytest.raises(lib.HgError):
+        st.read(lib.BUF_SEG_OFF)  # a HiGS buffer of a plain frame
+    return st.stats()
+
+
+def test_plain_path_discrete_stages_tiny_and_multiview(lib, ctx):
+    scene, cams = scenes.tiny_workload()
+    _plain_gate(lib, ctx, [P.project(scene, cams[0])], cams)
+    scene = scenes.uniform_scene(20_000, seed=4)
+    cams = [scenes.look_at((3, 0, 0), width=256, height=256),
+            scenes.look_at((0, 3, 0.5), width=200, height=120),
+            scenes.look_at((-2, -2, 1), width=97, height=61)]
+    _plain_gate(lib, ctx, [P.project(scene, c) for c in cams], cams)
+
+
+def test_plain_path_discrete_stages_ties_and_dense_tiles(lib, ctx):
+    """300K records on a 130 x 70 image with 3,000 distinct depth keys: dense
+    tiles, heavy key ties (ordered by record index), a global sort of many
+    onesweep tiles."""
+    cam = scenes.look_at((3, 0, 0), width=130, height=70)
+    st = _plain_gate(lib, ctx, [_synthetic_records(300_000, 130, 70, 3000, seed=0)], [cam])
+    assert st["n_pairs"] > 8192 * 4
+
+
+def test_plain_path_discrete_stages_cluster_scene_1080p(lib, ctx):
+    scene = scenes.cluster_scene(60_000, 16, 1.4, seed=3, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    cam = scenes.scene_orbit(8, 1920, 1080)[3]
+    _plain_gate(lib, ctx, [P.project(scene, cam)], [cam])
+
+
 # ------------------------------------------------------------ images
 @pytest.mark.parametrize("path", ["higs", "plain"])
 def test_image_tiny(lib, ctx, path):
@@ -275,24 +323,25 @@ def test_half_precision_sh_storage(lib, ctx, storage):
         lib.render_backward(st, gs, torch.zeros(sum(c.width * c.height for c in cams) * 3, device="cuda"))
 
 
-def _codec_scene(seed, sigma_high):
+def _codec_scene(seed, sh_kind):
     scene = scenes.cluster_scene(30_000, 8, 1.2, seed=seed, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
-    if sigma_high is not None:
-        g = np.random.default_rng(seed)
-        scene.sh[:, 1:] = g.normal(0, sigma_high, scene.sh[:, 1:].shape).astype(np.float32)
-    return scene
+    return scenes.decaying_sh(scene, seed=seed) if sh_kind == "decaying" else scene
 
 
-@pytest.mark.parametrize("sigma_high", [None, 0.02])
-def test_packed_sh_codec(lib, ctx, sigma_high):
+@pytest.mark.parametrize("sh_kind", ["iid", "decaying"])
+def test_packed_sh_codec(lib, ctx, sh_kind):
     """32-byte packed SH (Sec. 4.2): the device encoder gives the oracle
     encoder's codes for the device's scales (bit for bit), the scales are the
     99.5th percentile within one histogram bin, and the image equals the
     oracle's on the decoded coefficients.  The image's PSNR against the
-    float32 coefficients is measured (it depends on the SH distribution: the
-    benchmark's N(0, 0.2) higher-order coefficients, or N(0, 0.02))."""
+    float32 coefficients depends on the SH distribution: with higher-order
+    energy falling with the degree (band l ~ N(0, 0.2 * 0.25^l), the
+    stand-in for trained scenes) it must reach the paper's level, 55 dB
+    (Tab. iq: 55.59 dB); with the configs' i.i.d. N(0, 0.2) bands, whose
+    view-dependent colour spans the whole range, 4-bit chroma steps of up to
+    29% of the scale bound it far lower (measured)."""
     from oracle import sh_codec as SC
-    scene = _codec_scene(21, sigma_high)
+    scene = _codec_scene(21, sh_kind)
     gs = lib.GpuScene.from_scene(ctx, scene, sh_storage=lib.SH_CODEC32)
     scales, codes = gs.sh_codec()
     sh = scene.sh.reshape(-1, 16, 3)
@@ -309,16 +358,17 @@ def test_packed_sh_codec(lib, ctx, sigma_high):
         full = C.render(P.project(scene, cam))["rgb"]
         mse.append(np.mean((imgs[v].reshape(full.shape) - full) ** 2))
     psnr = 10 * np.log10(1.0 / max(np.mean(mse), 1e-30))
-    print(f"packed SH, higher-order sigma {sigma_high or 0.2}: PSNR {psnr:.1f} dB against float32 coefficients")
-    assert psnr > (40.0 if sigma_high else 28.0)
+    print(f"packed SH, {sh_kind} higher-order bands: PSNR {psnr:.1f} dB against float32 coefficients")
+    assert psnr >= (55.0 if sh_kind == "decaying" else 40.0)
 
 
 @pytest.mark.parametrize("macro", [(4, 4), (8, 4)])
 def test_half_precision_rasterisation(lib, ctx, macro):
     """HG_FLAG_FP16 (Sec. 3.5 / 4.5): alpha in half2 from the prescaled
-    Cholesky factors and macro-tile-relative positions.  Its tolerance is
-    image fidelity, not the float32 bounds: PSNR against the float64 oracle
-    of at least 50 dB.  It does not save for the backward."""
+    Cholesky factors and positions relative to the macro-tile centre.  Its
+    tolerance is image fidelity, not the float32 bounds: PSNR against the
+    float64 oracle of at least 55 dB (the paper's level, Tab. iq).  It does
+    not save for the backward."""
     import torch
     scene = scenes.cluster_scene(40_000, 8, 1.2, seed=14, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
     cams = scenes.scene_orbit(8, 320, 200)[4:6]
@@ -330,7 +380,7 @@ def test_half_precision_rasterisation(lib, ctx, macro):
         mse.append(np.mean((imgs[v].reshape(ref["rgb"].shape) - ref["rgb"]) ** 2))
     psnr = 10 * np.log10(1.0 / np.mean(mse))
     print(f"fp16 rasterisation {macro}: PSNR {psnr:.1f} dB against the float64 oracle")
-    assert psnr >= 50.0
+    assert psnr >= 55.0
     with pytest.raises(lib.HgError):
         lib.render(gs, cams, lib.Options(flags=lib.FLAG_FP16, save_for_backward=True))
 

@@ -57,6 +57,59 @@ def test_results_equal_alone_and_in_the_mix(lib, ctx, scene_set):
     srv.close()
 
 
+def test_mixed_resolution_launch_matches_oracle(lib, ctx):
+    """Requests of one scene at four resolutions submitted in one burst are
+    served by multi-view launches that mix resolutions (a launch shape only
+    the server makes); every served image matches the float64 oracle."""
+    import torch
+    from oracle import composite as C
+    from oracle import project as P
+    from tests.helpers import compare_image
+    scene = scenes.cluster_scene(20_000, 8, 1.2, seed=23, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    srv = lib.Server(ctx, max_inflight=1, max_views_per_launch=8, batch_window_us=20_000)
+    sid = srv.add_scene(gs)
+    res = [(96, 64), (64, 48), (120, 72), (33, 17)]
+    reqs = []
+    for k in range(8):
+        w, h = res[k % len(res)]
+        cam = scenes.orbit(8, scenes.ORBIT_RADIUS, w, h)[k]
+        out = torch.empty(w * h * 3, device="cuda")
+        reqs.append((srv.submit(sid, cam, out), cam, out))
+    for rid, _, _ in reqs:
+        assert srv.wait(rid, 60_000) == 0
+    st = srv.stats()
+    assert st["launches"] < len(reqs) and st["mean_views_per_launch"] > 1.0, st
+    for _, cam, out in reqs:
+        img = out.view(cam.height, cam.width, 3).cpu().numpy()
+        compare_image(img, None, C.render(P.project(scene, cam)))
+    srv.close()
+
+
+def test_presized_slots_never_grow(lib, ctx, scene_set):
+    """presize=(W, H): adding a scene sizes every slot for a full launch at
+    that resolution, so bursts of full launches hold no more memory than
+    after the sizing (no workspace growth on the request path), and the
+    results equal renders alone."""
+    import torch
+    srv = lib.Server(ctx, max_inflight=2, max_views_per_launch=4, batch_window_us=2000, presize=(640, 360))
+    sid = srv.add_scene(scene_set[1])
+    held0 = srv.stats()["held_bytes"]
+    assert held0 > 0
+    cams = scenes.scene_orbit(16, 640, 360)
+    outs = [torch.empty(640 * 360 * 3, device="cuda") for _ in cams]
+    for k0 in range(0, len(cams), 8):
+        ids = [srv.submit(sid, cams[k], outs[k]) for k in range(k0, k0 + 8)]
+        for r in ids:
+            assert srv.wait(r, 60_000) == 0
+    st = srv.stats()
+    assert st["held_bytes"] == held0, (st["held_bytes"], held0)
+    assert st["mean_views_per_launch"] > 1.0
+    for c, o in zip(cams, outs):
+        assert np.array_equal(o.cpu().numpy(), _alone(lib, scene_set[1], c))
+    srv.close()
+
+
 def test_host_outputs_cancel_and_errors(lib, ctx, scene_set):
     import torch
     srv = lib.Server(ctx, max_inflight=1, max_views_per_launch=2)

@@ -158,3 +158,41 @@ def test_gradient_restricted_to_tiles_equals_full():
     for k in full:
         assert np.array_equal(full[k], part[k]), k
         assert np.abs(full[k]).max() > 0, k
+
+
+def test_mean_gradients_are_ill_conditioned_in_screen_position():
+    """Why the end-to-end per-element comparison of the mean gradients has a
+    floor: a gaussian's mean gradient sums per-pixel terms that cancel around
+    its centre, so shifting every projected position by 1e-5 px (a sixth of
+    the float32 spacing at 1080p coordinates) moves some mean gradients by
+    more than 1e-3 of their value, in the float64 oracle itself, and half
+    the float32 spacing at 1080p (3e-5 px) moves more than 0.1% of them;
+    the conic, perturbed by 1e-6 relative, moves none."""
+    from paper_2606_00352_gb300 import scenes
+    from oracle import composite as C
+    scene = scenes.cluster_scene(2000, 16, 1.2, seed=7, sigma_range=(0.3, 1.5), extent=1.0)
+    target = scenes.perturbed(scene, seed=3, mean_sigma=1e-3, logit_sigma=0.1)
+    cams = [scenes.look_at((3.0, 0.5, 0.0), width=64, height=48), scenes.look_at((0.2, -3.0, 0.6), width=64, height=48)]
+    refs = [C.render(P.project(scene, c)) for c in cams]
+    amb = [(r["m_q"] < 5e-5) | (r["m_alpha"] < 5e-5) | (r["m_T"] < 1e-5) for r in refs]
+    vs = [np.where(~a[..., None], r["rgb"] - C.render(P.project(target, c))["rgb"], 0.0)
+          for r, a, c in zip(refs, amb, cams)]
+
+    def means_grad(shift=0.0, conic_rel=0.0):
+        g = np.random.default_rng(0)
+        out = 0.0
+        for cam, v in zip(cams, vs):
+            pr = P.project(scene, cam)
+            pp = dict(pr)
+            pp["mean2d"] = pr["mean2d"] + g.normal(0.0, 1.0, pr["mean2d"].shape) * shift
+            pp["conic"] = pr["conic"] * (1.0 + g.normal(0.0, 1.0, pr["conic"].shape) * conic_rel)
+            out = out + G.project_grads(scene, cam, pr, G.pixel_grads(pp, v))["means"]
+        return out.reshape(-1)
+
+    def share_within(a, b):
+        ok = np.abs(a - b) <= 1e-3 * np.maximum(np.abs(b), 1e-3 * np.abs(b).max()) + 1e-7
+        return ok.mean()
+    base = means_grad()
+    s1, s3 = share_within(means_grad(shift=1e-5), base), share_within(means_grad(shift=3e-5), base)
+    assert s1 < 1.0 and s3 < 0.999 and s3 < s1, (s1, s3)
+    assert share_within(means_grad(conic_rel=1e-6), base) == 1.0

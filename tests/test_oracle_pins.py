@@ -356,6 +356,47 @@ def test_binning_matches_pixel_enumeration():
     assert got == want
 
 
+def test_plain_tile_pairs_against_pixel_enumeration_and_candidates():
+    """The plain path's per-tile pair list (Sec. 2 / 5 baseline) over two
+    views: each tile's (gaussian) set equals the tiles met by enumerating the
+    pixels of each gaussian's rectangle, every tile's list is ascending in
+    (depth key, record) and equals the compositing oracle's own rect
+    candidates (an independent expression of the same rule), record ids are
+    v n + i, and the ranges cover exactly the pairs of each tile."""
+    scene, cams = tiny_workload()
+    cam2 = look_at((0.4, 3.0, 0.6), width=72, height=40)
+    cams = [cams[0], cam2]
+    prs = [P.project(scene, c) for c in cams]
+    views = [BN.records_f32(p) for p in prs]
+    keys64, ids, ranges = BN.plain_tile_pairs(views, [(c.width, c.height) for c in cams])
+    n = scene.n
+    tiles_v = [(-(-c.width // 8)) * (-(-c.height // 8)) for c in cams]
+    assert len(ranges) == sum(tiles_v)
+    assert np.all(keys64[1:] >= keys64[:-1])
+    tile = (keys64 >> np.uint64(32)).astype(np.int64)
+    key = (keys64 & np.uint64(0xffffffff)).astype(np.uint32)
+    base = 0
+    for v, (cam, pr) in enumerate(zip(cams, prs)):
+        gw, gh, off, gid = C.tile_candidates(pr, 8)
+        mx, my, r, k = views[v]
+        want = set()
+        for i in np.nonzero(r > 0)[0]:
+            x0, y0 = math.floor(float(mx[i])), math.floor(float(my[i]))
+            for y in range(max(0, y0 - r[i]), min(cam.height - 1, y0 + r[i]) + 1):
+                for x in range(max(0, x0 - r[i]), min(cam.width - 1, x0 + r[i]) + 1):
+                    want.add((base + (y // 8) * gw + x // 8, v * n + i))
+        got = set()
+        for t in range(gw * gh):
+            a, b = ranges[base + t]
+            assert np.all(tile[a:b] == base + t)
+            got.update((base + t, int(i)) for i in ids[a:b])
+            assert np.array_equal(ids[a:b] - v * n, gid[off[t]:off[t + 1]])
+            assert np.array_equal(key[a:b], k[gid[off[t]:off[t + 1]]])
+        assert got == want
+        base += gw * gh
+    assert sum(int(b - a) for a, b in ranges) == len(ids)
+
+
 def test_macro_pairs_never_exceed_tile_pairs():
     """Coarser binning never creates more pairs (Table 1 ordering)."""
     scene, cams = tiny_workload()
