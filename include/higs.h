@@ -383,9 +383,11 @@ hg_status hg_graph_launch(hg_graph* graph, void* stream);
 /* New poses with the captured count and resolutions for the next replay;
  * call only when no replay is pending (after hg_graph_sync). */
 hg_status hg_graph_set_cameras(hg_graph* graph, const hg_camera* cams, int n_views);
-/* Wait for the last replay and return its device status; HG_ERR_CAPACITY
- * means a pose binned more pairs than the capture allows: create the graph
- * again from that pose. */
+/* Wait for the last replay (its own completion, not later work queued on
+ * the same stream: two graphs over two states can be kept in flight on one
+ * stream, each synchronised on its own) and return its device status;
+ * HG_ERR_CAPACITY means a pose binned more pairs than the capture allows:
+ * create the graph again from that pose. */
 hg_status hg_graph_sync(hg_graph* graph);
 /* Kernels one replay launches. */
 int64_t hg_graph_kernels(const hg_graph* graph);

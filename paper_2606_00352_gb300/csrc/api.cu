@@ -310,6 +310,7 @@ hg_status state_create(hg_ctx* ctx, hg_state** out) {
   }
   memset(s->fc_host, 0, sizeof(FrameCounters));
   for (int i = 0; i < N_EVENTS; ++i) cudaEventCreate(&s->ev[i]);
+  cudaEventCreateWithFlags(&s->frame_done, cudaEventDisableTiming);
   {
     SortStreams& ss = s->sort_streams;
     bool ok = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess;
@@ -333,6 +334,7 @@ extern "C" void hg_state_free(hg_state* s) {
   cudaDeviceSynchronize();
   for (int i = 0; i < BUF_COUNT; ++i) ctx_free(s->ctx, s->bufs[i].p, s->bufs[i].bytes, nullptr);
   for (int i = 0; i < N_EVENTS; ++i) cudaEventDestroy(s->ev[i]);
+  if (s->frame_done) cudaEventDestroy(s->frame_done);
   {
     SortStreams& ss = s->sort_streams;
     if (ss.fork) cudaEventDestroy(ss.fork);
@@ -346,10 +348,15 @@ extern "C" void hg_state_free(hg_state* s) {
   delete s;
 }
 
+cudaError_t state_wait(hg_state* s) {
+  if (s->frame_in_graph && s->frame_done) return cudaEventSynchronize(s->frame_done);
+  return cudaStreamSynchronize(s->last_stream);
+}
+
 extern "C" hg_status hg_state_sync(hg_state* s) {
   if (!s) return HG_ERR_INVALID_ARG;
   cudaSetDevice(s->ctx->device);
-  HG_TRY(cudaStreamSynchronize(s->last_stream), "hg_state_sync");
+  HG_TRY(state_wait(s), "hg_state_sync");
   return (hg_status)s->fc_host->status;
 }
 
@@ -722,6 +729,7 @@ hg_status run_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o,
   s->scene = in.scene;
   s->last_stream = st;
   s->has_frame = true;
+  s->frame_in_graph = false;
   s->has_grad2d = false;
   ++s->frame_id;
   const bool async = (o->flags & HG_FLAG_ASYNC) != 0;
@@ -807,7 +815,7 @@ extern "C" hg_status hg_render_splats(hg_ctx* ctx, const hg_splat* d_splats, int
 extern "C" hg_status hg_render_stats(hg_state* s, hg_frame_stats* out) {
   if (!s || !out || !s->has_frame) return HG_ERR_INVALID_ARG;
   cudaSetDevice(s->ctx->device);
-  HG_TRY(cudaStreamSynchronize(s->last_stream), "stats");
+  HG_TRY(state_wait(s), "stats");
   const FrameCounters& f = *s->fc_host;
   memset(out, 0, sizeof(*out));
   out->n_views = s->geom.V;

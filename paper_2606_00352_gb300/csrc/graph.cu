@@ -99,9 +99,11 @@ extern "C" hg_status hg_graph_launch(hg_graph* G, void* stream) {
   if (!G) return HG_ERR_INVALID_ARG;
   cudaStream_t st = stream ? (cudaStream_t)stream : G->st;
   cudaError_t e = cudaGraphLaunch(G->ge, st);
+  if (e == cudaSuccess) e = cudaEventRecord(G->state->frame_done, st);
   if (e != cudaSuccess) return hg_cuda_status(e, "graph launch");
   G->state->last_stream = st;
   G->state->has_frame = true;
+  G->state->frame_in_graph = true;
   ++G->state->frame_id;  // a new frame (a saved one needs its own backward suffix)
   G->state->has_grad2d = false;
   return HG_OK;
@@ -126,7 +128,7 @@ extern "C" hg_status hg_graph_set_cameras(hg_graph* G, const hg_camera* cams, in
 
 extern "C" hg_status hg_graph_sync(hg_graph* G) {
   if (!G) return HG_ERR_INVALID_ARG;
-  cudaError_t e = cudaStreamSynchronize(G->state->last_stream);
+  cudaError_t e = state_wait(G->state);
   if (e != cudaSuccess) return hg_cuda_status(e, "graph sync");
   const int status = G->state->fc_host->status;
   if (status != HG_OK) hg_set_error(std::string("device status: ") + hg_status_str((hg_status)status));

@@ -90,6 +90,10 @@ struct hg_state {
   // the backward already turned into colours behind the batches
   uint64_t frame_id = 0, bwd_suffix_done = 0;
   bool has_grad2d = false;  // a backward of the current frame wrote G_DMEANS2
+  // set by hg_graph_launch: the replay's completion event (waiting on it
+  // waits for this frame only, not for later work queued on the stream)
+  cudaEvent_t frame_done = nullptr;
+  bool frame_in_graph = false;
 };
 
 void hg_set_error(const std::string& s);
@@ -115,5 +119,8 @@ hg_status ensure_workspace(hg_state* s, long long n, const hg::FrameGeom& g, con
                            cudaStream_t st);
 hg_status enqueue_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg::FrameGeom& g,
                         float* out_rgb, float* out_T, cudaStream_t st);
+// Waits for the last frame of `s` (its replay event after a graph launch,
+// else its stream).
+cudaError_t state_wait(hg_state* s);
 hg_status run_frame(hg_state* s, const hg::FrameInputs& in, const hg_render_opts* o, const hg_camera* cams, int V,
                     float* out_rgb, float* out_T, cudaStream_t st);

@@ -15,7 +15,8 @@ from oracle import project as P
 AMB_Q, AMB_ALPHA, AMB_T = 5e-5, 5e-5, 1e-5
 IMG_TOL = 2e-4          # max abs per channel outside ambiguous pixels
 AMB_JUMP = 0.02         # bound for a single flipped decision (worst measured 6.0e-3)
-AMB_FRACTION = 0.01     # default share of pixels allowed to be decision-ambiguous
+AMB_FRACTION = 0.01     # default share of decision-ambiguous pixels; each parity test passes its own
+                        # cap, about twice the share it measures
 
 
 def ambiguous(ref):

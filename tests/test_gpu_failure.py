@@ -43,12 +43,12 @@ def test_chain_wait_gives_up_and_the_merge_replays(lib):
     assert stats["n_batches"] > stats["n_segments"], stats
     assert stats["n_replays"] > 0, stats
     img, t = _img(lib, rgb, T, cam)
-    compare_image(img, t, ref)
+    compare_image(img, t, ref, max_amb=0.004)  # measured 0.18%
     ctx.set_wait_limits()
     rgb2, T2 = lib.render(gs, [cam], opts, state=st)
     assert st.stats()["n_replays"] == 0
     img2, t2 = _img(lib, rgb2, T2, cam)
-    compare_image(img2, t2, ref)
+    compare_image(img2, t2, ref, max_amb=0.004)
 
 
 def test_mbarrier_wait_gives_up_with_a_status(lib):
@@ -67,7 +67,7 @@ def test_mbarrier_wait_gives_up_with_a_status(lib):
     ctx.set_wait_limits()
     rgb, T = lib.render(gs, [cam], lib.Options())
     img, t = _img(lib, rgb, T, cam)
-    compare_image(img, t, C.render(P.project(scene, cam)))
+    compare_image(img, t, C.render(P.project(scene, cam)), max_amb=0.004)
 
 
 def test_allocator_out_of_memory_is_a_status(lib):

@@ -243,7 +243,7 @@ def test_image_tiny(lib, ctx, path):
     p = lib.PATH_HIGS if path == "higs" else lib.PATH_PLAIN
     imgs, ts = render_np(lib, gs, cams, path=p)
     ref = C.render(P.project(scene, cams[0]))
-    compare_image(imgs[0], ts[0], ref)
+    compare_image(imgs[0], ts[0], ref, max_amb=0.002)  # measured 0.09%
 
 
 @pytest.mark.parametrize("independent", [False, True])
@@ -260,7 +260,7 @@ def test_image_invariant_to_macro_shape_and_cap(lib, ctx, macro, cap, independen
     imgs, ts = render_np(lib, gs, [cam], macro_w=macro[0], macro_h=macro[1], batch_cap=cap, state=st,
                          flags=lib.FLAG_INDEPENDENT if independent else 0)
     ref = C.render(P.project(scene, cam))
-    compare_image(imgs[0], ts[0], ref)
+    compare_image(imgs[0], ts[0], ref, max_amb=0.004)  # measured 0.20%
     if cap <= 64:
         assert (st.stats()["n_replays"] > 0) == independent
 
@@ -283,7 +283,7 @@ def test_image_ellipse_binning_equals_rect(lib, ctx, macro, cap):
     assert np.array_equal(out[lib.BIN_RECT][1], out[lib.BIN_ELLIPSE][1])
     assert out[lib.BIN_ELLIPSE][2] < out[lib.BIN_RECT][2]
     ref = C.render(P.project(scene, cam))
-    compare_image(out[lib.BIN_ELLIPSE][0], out[lib.BIN_ELLIPSE][1], ref)
+    compare_image(out[lib.BIN_ELLIPSE][0], out[lib.BIN_ELLIPSE][1], ref, max_amb=0.0005)  # measured 0.02%
 
 
 def test_image_ellipse_binning_independent_batches(lib, ctx):
@@ -293,7 +293,7 @@ def test_image_ellipse_binning_independent_batches(lib, ctx):
     gs = lib.GpuScene.from_scene(ctx, scene)
     imgs, ts = render_np(lib, gs, [cam], macro_w=8, macro_h=4, batch_cap=64, bin_test=lib.BIN_ELLIPSE,
                          flags=lib.FLAG_INDEPENDENT)
-    compare_image(imgs[0], ts[0], C.render(P.project(scene, cam)))
+    compare_image(imgs[0], ts[0], C.render(P.project(scene, cam)), max_amb=0.004)  # measured 0.20%
 
 
 def _round_sh(sh, storage):
@@ -318,7 +318,7 @@ def test_half_precision_sh_storage(lib, ctx, storage):
     ref_scene = scene.copy()
     ref_scene.sh = _round_sh(scene.sh, storage)
     for v, cam in enumerate(cams):
-        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)))
+        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)), max_amb=0.001)  # measured 0.03%
     with pytest.raises(lib.HgError):
         lib.render_backward(st, gs, torch.zeros(sum(c.width * c.height for c in cams) * 3, device="cuda"))
 
@@ -354,7 +354,7 @@ def test_packed_sh_codec(lib, ctx, sh_kind):
     imgs, ts = render_np(lib, gs, cams)
     mse = []
     for v, cam in enumerate(cams):
-        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)))
+        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)), max_amb=0.001)  # measured 0.03%
         full = C.render(P.project(scene, cam))["rgb"]
         mse.append(np.mean((imgs[v].reshape(full.shape) - full) ** 2))
     psnr = 10 * np.log10(1.0 / max(np.mean(mse), 1e-30))
@@ -396,7 +396,7 @@ def test_image_background_and_multiview(lib, ctx):
         imgs, ts = render_np(lib, gs, cams, path=path, bg=bg)
         for v, cam in enumerate(cams):
             ref = C.render(P.project(scene, cam), bg=bg)
-            compare_image(imgs[v], ts[v], ref)
+            compare_image(imgs[v], ts[v], ref, max_amb=0.008)  # measured 0.36%
 
 
 def test_edge_cases_empty_culled_single(lib, ctx):
@@ -445,7 +445,7 @@ def test_image_1m_scene_sampled_tiles(lib, ctx):
         for v, cam in enumerate(cams):
             tiles = sample_tiles(1920, 1080, 48, seed=v)
             ref = C.render(P.project(scene, cam), tiles=tiles)
-            compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles))
+            compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles), max_amb=0.001)  # measured 0.03%
 
 
 def test_image_5m8_scene_bench_configuration(lib, ctx):
@@ -467,4 +467,4 @@ def test_image_5m8_scene_bench_configuration(lib, ctx):
     for v in (0, 3):
         tiles = sample_tiles(1920, 1080, 24, seed=100 + v)
         ref = C.render(P.project(ref_scene, cams[v]), tiles=tiles)
-        compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles))
+        compare_image(imgs[v], ts[v], ref, mask=tiles_mask(1920, 1080, tiles), max_amb=0.005)  # measured 0.25%

@@ -70,7 +70,7 @@ def test_spatial_scene_renders_the_permuted_scene(lib, ctx, macro):
     imgs = [x.detach().cpu().numpy() for x in lib.split_views(rgb, cams, 3)]
     ts = [x.detach().cpu().numpy() for x in lib.split_views(T, cams, 1)]
     for v, cam in enumerate(cams):
-        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)))
+        compare_image(imgs[v], ts[v], C.render(P.project(ref_scene, cam)), max_amb=0.001)  # measured 0.04%
     gs.close()
 
 
