@@ -15,14 +15,18 @@ constexpr int BIN_CLASSIC = 0;  // {mx, my, radius, key} (plain path)
 constexpr int BIN_CELLS_RECT = 1;
 constexpr int BIN_CELLS_ELLIPSE = 2;
 
+// bw and bh, the macro cell's size in pixels, are powers of two (macro
+// tiles of 4 or 8 render tiles of 8 pixels), so the cell of a pixel
+// coordinate is an arithmetic shift (the floor for negative coordinates too).
 __device__ __forceinline__ bool macro_rect(int px, int py, int rad, int bw, int bh, int gx, int gy, int& x0, int& x1,
                                            int& y0, int& y1) {
   if (rad <= 0) return false;
   const int xl = px - rad, xh = px + rad, yl = py - rad, yh = py + rad;
-  x0 = xl < 0 ? 0 : xl / bw;
-  x1 = xh < 0 ? -1 : min(xh / bw, gx - 1);
-  y0 = yl < 0 ? 0 : yl / bh;
-  y1 = yh < 0 ? -1 : min(yh / bh, gy - 1);
+  const int sw = 31 - __clz(bw), sh = 31 - __clz(bh);
+  x0 = xl < 0 ? 0 : xl >> sw;
+  x1 = xh < 0 ? -1 : min(xh >> sw, gx - 1);
+  y0 = yl < 0 ? 0 : yl >> sh;
+  y1 = yh < 0 ? -1 : min(yh >> sh, gy - 1);
   return x0 <= x1 && y0 <= y1;
 }
 
@@ -131,8 +135,9 @@ __device__ __forceinline__ uint4 bin_cells(float mx, float my, int rad, float L0
     for (int y = y0; y <= y1; ++y) {
       float xl, xr;
       if (!ell_span(g, mx, my, L1, L2, (float)(y * bh), (float)(y * bh + bh - 1), E > 0.f, xl, xr)) continue;
-      const int c0 = max(x0, floordiv((int)ceilf(xl), bw));
-      const int c1 = min(x1, floordiv((int)floorf(xr), bw));
+      const int sw = 31 - __clz(bw);
+      const int c0 = max(x0, (int)ceilf(xl) >> sw);
+      const int c1 = min(x1, (int)floorf(xr) >> sw);
       if (c0 > c1) continue;
       m |= ((1ull << (c1 - c0 + 1)) - 1ull) << ((y - y0) * nx + (c0 - x0));
     }

@@ -77,11 +77,6 @@ __device__ __forceinline__ int read_status(const FrameCounters* fc) {
   return *((volatile const int*)&fc->status);
 }
 
-// floor(a / b) for b > 0
-__device__ __forceinline__ int floordiv(int a, int b) {
-  return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -186,6 +186,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   const int cnt = (int)min((long long)PROJ_THREADS, a.n - i0);
   const bool full = cnt == PROJ_THREADS;
   const int nv = a.n_views;
+  // visible-entry count of the CTA: one global atomic per CTA (a counter
+  // updated by every warp and view serialises at its L2 slice)
+  __shared__ uint32_t s_nvis, s_warps_done;
+  if (tid == 0) s_nvis = s_warps_done = 0;
 
   if (full) {
     // TMA: five contiguous slices, one mbarrier
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
   const int lane = tid & 31;
   float px = 0.f, py = 0.f, pz = 0.f, op = 0.f;
   unsigned long long vbits = 0;  // views in which the gaussian is visible
+  uint32_t warp_vis = 0;         // lane 0: visible entries of the warp
   {
     float sx = 1.f, sy = 1.f, sz = 1.f;
     float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -343,8 +348,16 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(ProjectArgs a) {
       if (lane == 0) {
         const long long word = (long long)v * a.vis_words + (gi >> 5);
         if (i0 + (tid & ~31) < a.n) a.vis[word] = ballot;
-        if (ballot) atomicAdd(&a.fc->n_visible, __popc(ballot));
+        warp_vis += (uint32_t)__popc(ballot);
       }
+    }
+  }
+  if (lane == 0) {
+    if (warp_vis) atomicAdd(&s_nvis, warp_vis);
+    __threadfence_block();
+    if (atomicAdd(&s_warps_done, 1u) == PROJ_THREADS / 32 - 1) {
+      const uint32_t total = atomicAdd(&s_nvis, 0u);
+      if (total) atomicAdd(&a.fc->n_visible, total);
     }
   }
 

@@ -32,23 +32,27 @@ template <int NT, int IPT>
 struct BlockSortSmem {
   uint32_t keys[NT * IPT];
   uint32_t vals[NT * IPT];
-  RankSmem<NT> rank;
+  RowRankSmem<NT> rank;
   uint32_t red[2][NT / 32];
 };
 
-// LSD radix passes over the digits of (x - xmin), x = keys[e] (by_val false)
-// or vals[e] (by_val true), of the n pairs of a shared-memory region, moving
-// both arrays: the region's pairs are spread evenly over the warps (rows =
-// ceil(n / NT) item slots per thread; slots [n, rows * NT) must hold key and
-// value 0xffffffff and get digit 255, so padding always ranks after the real
-// pairs).  Every pass is stable.
+// LSD radix passes over the `bits` low bits of (x - xmin), x = keys[e]
+// (by_val false) or vals[e] (by_val true), of the n pairs of a shared-memory
+// region, moving both arrays: the region's pairs are spread evenly over the
+// warps (rows = ceil(n / NT) item slots per thread; slots [n, rows * NT) must
+// hold key and value 0xffffffff and get the largest digit, so padding always
+// ranks after the real pairs).  Spans of 25 to 27 bits take three 9-bit
+// passes, others ceil(bits / 8) 8-bit passes.  Every pass is stable.
 template <int NT, int IPT>
-__device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int passes,
-                                             bool by_val, RankSmem<NT>& rank) {
+__device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int bits,
+                                             bool by_val, RowRankSmem<NT>& rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = (n + NT - 1) / NT;  // <= IPT
+  const bool wide = bits > 24 && bits <= 27;
+  const int dbits = wide ? 9 : 8, passes = wide ? 3 : (bits + 7) / 8;
+  const uint32_t dmask = wide ? 0x1ffu : 0xffu;
   for (int pass = 0; pass < passes; ++pass) {
-    const int shift = 8 * pass;
+    const int shift = dbits * pass;
     uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -56,10 +60,11 @@ __device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int
       const int e = warp * 32 * rows + i * 32 + lane;
       k[i] = keys[e];
       v[i] = vals[e];
-      d[i] = e < n ? (((by_val ? v[i] : k[i]) - xmin) >> shift) & 0xffu : 0xffu;
+      d[i] = e < n ? (((by_val ? v[i] : k[i]) - xmin) >> shift) & dmask : dmask;
     }
-    block_rank_rows<NT, IPT>(d, p, rank, rows);
-    __syncthreads();
+    // every thread has read its items before the ranking's first barrier,
+    // so the scatter needs no barrier of its own before it
+    block_rank_rows<NT, IPT>(d, p, rank, rows, wide);
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       if (i >= rows) break;
@@ -72,7 +77,7 @@ __device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int
 
 template <int NT>
 __device__ __forceinline__ void block_min_max(uint32_t& mn, uint32_t& mx, uint32_t (*red)[NT / 32]);
-__device__ __forceinline__ int radix_passes(uint32_t kmin, uint32_t kmax);
+__device__ __forceinline__ int radix_bits(uint32_t kmin, uint32_t kmax);
 
 // Longest run of equal keys whose ids one thread re-sorts by insertion.
 constexpr int TIE_RUN_MAX = 32;
@@ -84,14 +89,14 @@ constexpr int TIE_RUN_MAX = 32;
 // region has a longer run it is sorted again from scratch, by id and then by
 // key, with stable passes (bounded work for any input: at most 8 passes).
 template <int NT, int IPT>
-__device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int passes,
-                                            RankSmem<NT>& rank, uint32_t (*red)[NT / 32], int* long_run) {
+__device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int bits,
+                                            RowRankSmem<NT>& rank, uint32_t (*red)[NT / 32], int* long_run) {
   const int tid = threadIdx.x;
   // stage 0: key passes; with a long tie run, stage 1: id passes, stage 2:
   // key passes again (one copy of the pass loop serves all three)
   uint32_t xmin = kmin;
   for (int stage = 0;; ++stage) {
-    radix_region<NT, IPT>(keys, vals, n, xmin, passes, stage == 1, rank);
+    radix_region<NT, IPT>(keys, vals, n, xmin, bits, stage == 1, rank);
     if (stage == 2) break;
     if (stage == 1) {
       uint32_t kmn = 0xffffffffu, kmx = 0;
@@ -101,7 +106,7 @@ __device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int 
       }
       block_min_max<NT>(kmn, kmx, red);
       xmin = kmn;
-      passes = radix_passes(kmn, kmx);
+      bits = radix_bits(kmn, kmx);
       continue;
     }
     if (tid == 0) *long_run = 0;
@@ -135,7 +140,7 @@ __device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int 
     }
     block_min_max<NT>(vmn, vmx, red);
     xmin = vmn;
-    passes = radix_passes(vmn, vmx);
+    bits = radix_bits(vmn, vmx);
   }
 }
 
@@ -163,9 +168,10 @@ __device__ __forceinline__ void block_min_max(uint32_t& mn, uint32_t& mx, uint32
   __syncthreads();
 }
 
-__device__ __forceinline__ int radix_passes(uint32_t kmin, uint32_t kmax) {
+// Significant bits of the span kmax - kmin (0 when every key is equal).
+__device__ __forceinline__ int radix_bits(uint32_t kmin, uint32_t kmax) {
   const uint32_t span = kmax - kmin;
-  return span ? (32 - __clz(span) + 7) / 8 : 0;
+  return span ? 32 - __clz(span) : 0;
 }
 
 // Next entry of a tier's segment list for this CTA (dynamic claiming: the
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a
       s.vals[j] = v;
     }
     block_min_max<NT>(kmin, kmax, s.red);
-    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_passes(kmin, kmax), s.rank, s.red, &s_long_run);
+    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_bits(kmin, kmax), s.rank, s.red, &s_long_run);
     for (int j = tid; j < n; j += NT) {
       a.keys[start + j] = s.keys[j];
       a.vals[start + j] = s.vals[j];
@@ -228,7 +234,7 @@ template <int NT, int IPT>
 struct MergeSortSmem {
   uint32_t keys[2 * NT * IPT];
   uint32_t vals[2 * NT * IPT];
-  RankSmem<NT> rank;
+  RowRankSmem<NT> rank;
   uint32_t red[2][NT / 32];
 };
 
@@ -278,9 +284,10 @@ __global__ void __launch_bounds__(NT) k_block_merge_sort(SortArgs a, int tier) {
       s.vals[H + j] = v;
     }
     block_min_max<NT>(kmin, kmax, s.red);
-    const int passes = radix_passes(kmin, kmax);
-    sort_region<NT, IPT>(s.keys, s.vals, hA, kmin, passes, s.rank, s.red, &s_long_run);
-    sort_region<NT, IPT>(s.keys + H, s.vals + H, hB, kmin, passes, s.rank, s.red, &s_long_run);
+    const int bits = radix_bits(kmin, kmax);
+    // one inlined copy of the region sort serves both halves
+    for (int h = 0; h < 2; ++h)
+      sort_region<NT, IPT>(s.keys + h * H, s.vals + h * H, h ? hB : hA, kmin, bits, s.rank, s.red, &s_long_run);
     const uint32_t *ka = s.keys, *va = s.vals, *kb = s.keys + H, *vb = s.vals + H;
     const int per = (n + NT - 1) / NT;
     const int d0 = min(n, tid * per), d1 = min(n, d0 + per);
@@ -613,7 +620,7 @@ static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaS
   cudaError_t e;
   // the largest tiers first, each on its own stream when s1..s3 differ from
   // st: their tails overlap
-  if ((e = launch_merge_tier<512, 16>(a, 3, s3)) != cudaSuccess) return e;
+  if ((e = launch_merge_tier<1024, 8>(a, 3, s3)) != cudaSuccess) return e;
   if ((e = launch_tier<1024, 8>(a, 2, 1, s2)) != cudaSuccess) return e;
   if ((e = launch_tier<512, 8>(a, 1, 2, s1)) != cudaSuccess) return e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;

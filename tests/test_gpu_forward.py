@@ -146,11 +146,13 @@ def test_discrete_stages_ellipse_cluster_scene(lib, ctx):
     assert 0 < st_e["n_pairs"] < st_r["n_pairs"]
 
 
-def _synthetic_records(n, w, h, n_keys, seed, rad_max=3):
+def _synthetic_records(n, w, h, n_keys, seed, rad_max=3, depth_range=(2.0, 3.0)):
     """Hand-made records: dense screen positions, few distinct depth keys
-    (ties), so segments exceed the shared-memory tiers."""
+    (ties), so segments exceed the shared-memory tiers.  Depths are drawn
+    log-uniformly from depth_range."""
     g = np.random.default_rng(seed)
-    keys = np.sort(g.uniform(2.0, 3.0, n_keys)).astype(np.float32).view(np.uint32)
+    lo, hi = np.log2(depth_range[0]), np.log2(depth_range[1])
+    keys = np.sort(np.exp2(g.uniform(lo, hi, n_keys))).astype(np.float32).view(np.uint32)
     pr = {"n": n, "mean2d": np.stack([g.uniform(0, w, n), g.uniform(0, h, n)], 1),
           "conic": np.tile([0.5, 0.0, 0.5], (n, 1)), "opacity": np.full(n, 0.5), "rgb": np.full((n, 3), 0.5),
           "depth_key": keys[g.integers(0, n_keys, n)], "radius": g.integers(1, rad_max + 1, n),
@@ -185,6 +187,31 @@ def test_discrete_stages_all_tiers(lib, ctx):
     st = _gate(lib, ctx, [pr], [cam])
     # <= 1K, <= 4K, <= 8K, <= 16K (halves + merge) and onesweep
     assert all(st["seg_by_tier"][t] > 0 for t in range(5))
+
+
+@pytest.mark.parametrize("octaves,bits", [(2, 24), (3, 25), (5, 26), (9, 27), (17, 28)])
+def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
+    """Depth keys spanning 24 to 28 bits in every shared-memory tier (the
+    tiers sort spans of 25 to 27 bits with 9-bit digits, others with 8-bit
+    ones), with ties."""
+    cam = scenes.look_at((3, 0, 0), width=512, height=96)
+    g = np.random.default_rng(100 + octaves)
+    parts = []
+    for n, w in ((400, 64), (3000, 128), (6000, 256), (12000, 384)):
+        p = _synthetic_records(n, 64, 32, n // 3, seed=int(g.integers(1 << 30)),
+                               depth_range=(1.0, 2.0 ** octaves))
+        k = p["depth_key"]
+        k[:2] = np.float32(1.0).view(np.uint32), np.float32(2.0 ** octaves * (1 - 2 ** -20)).view(np.uint32)
+        p["radius"][:2] = 3
+        p["mean2d"][:2] = 32.0, 16.0  # both span ends in the segment of every macro cell the part covers
+        p["mean2d"][:, 0] += w - 64
+        parts.append(p)
+    pr = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if k != "n"}
+    pr["n"] = len(pr["radius"])
+    st = _gate(lib, ctx, [pr], [cam])
+    assert all(st["seg_by_tier"][t] > 0 for t in range(4))
+    span = int(pr["depth_key"].max()) - int(pr["depth_key"].min())
+    assert span.bit_length() == bits
 
 
 def _plain_gate(lib, ctx, projs, cams):
