@@ -360,12 +360,19 @@ hg_status hg_render_stats(hg_state* state, hg_frame_stats* out);
  * HG_BUF_VIEW_SEG_BASE (uint32 [V+1]).  After hg_render_backward:
  * HG_BUF_GRAD2D (float32 [V][n][9], the gradient with respect to each
  * view's projected record: d mean2d x, y, d conic A, B, C of q = A dx^2 +
- * 2 B dx dy + C dy^2, d opacity, d rgb).  A buffer of the other path (or a
- * gradient before any backward) is HG_ERR_UNSUPPORTED.  *bytes_needed
- * receives the size; dst may be NULL to query it. */
+ * 2 B dx dy + C dy^2, d opacity, d rgb).  Both paths, the projection's
+ * outputs: HG_BUF_RECORDS (float32 [V][n][16], the raster record of every
+ * (view, gaussian): {mx, my, l0', l1'} {l2', o, radius bits, depth key
+ * bits} {r, g, b, blend level} {0}, l' the Cholesky factors of the conic
+ * prescaled by sqrt(log2(e) / 2); the records of culled entries are
+ * unspecified) and HG_BUF_VISIBILITY (uint32 [V][ceil(n / 32)], bit i % 32
+ * of word i / 32 set when gaussian i is visible in the view).  A buffer of
+ * the other path (or a gradient before any backward) is
+ * HG_ERR_UNSUPPORTED.  *bytes_needed receives the size; dst may be NULL to
+ * query it. */
 enum { HG_BUF_SEG_OFF = 0, HG_BUF_PAIR_KEYS = 1, HG_BUF_PAIR_IDS = 2, HG_BUF_BATCHES = 3,
        HG_BUF_SPLATS = 4, HG_BUF_VIEW_SEG_BASE = 5, HG_BUF_PLAIN_KEYS = 6, HG_BUF_PLAIN_IDS = 7,
-       HG_BUF_TILE_RANGES = 8, HG_BUF_GRAD2D = 9 };
+       HG_BUF_TILE_RANGES = 8, HG_BUF_GRAD2D = 9, HG_BUF_RECORDS = 10, HG_BUF_VISIBILITY = 11 };
 hg_status hg_state_read(hg_state* state, int which, void* dst, size_t dst_bytes,
                         size_t* bytes_needed);
 

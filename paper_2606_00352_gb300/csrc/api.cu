@@ -902,6 +902,14 @@ extern "C" hg_status hg_state_read(hg_state* s, int which, void* dst, size_t dst
       bytes = sizeof(uint32_t) * 2 * (size_t)g.total_tiles;
       src = s->bufs[P_RANGES].p;
       break;
+    case HG_BUF_RECORDS:
+      bytes = sizeof(float4) * REC_F4 * (size_t)s->n * g.V;
+      src = s->bufs[B_REC].p;
+      break;
+    case HG_BUF_VISIBILITY:
+      bytes = sizeof(uint32_t) * (size_t)((s->n + 31) / 32) * g.V;
+      src = s->bufs[B_VIS].p;
+      break;
     case HG_BUF_GRAD2D:
       if (!s->has_grad2d) return HG_ERR_UNSUPPORTED;
       bytes = sizeof(float) * 9 * (size_t)s->n * g.V;

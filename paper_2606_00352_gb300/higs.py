@@ -23,7 +23,7 @@ PATH_HIGS, PATH_PLAIN = 0, 1
 BIN_RECT, BIN_ELLIPSE = 0, 1
 FLAG_ASYNC, FLAG_TIMING, FLAG_KEEP_SPLATS, FLAG_INDEPENDENT, FLAG_PROFILE, FLAG_FP16 = 1, 2, 4, 8, 16, 32
 (BUF_SEG_OFF, BUF_PAIR_KEYS, BUF_PAIR_IDS, BUF_BATCHES, BUF_SPLATS, BUF_VIEW_SEG_BASE, BUF_PLAIN_KEYS, BUF_PLAIN_IDS,
- BUF_TILE_RANGES, BUF_GRAD2D) = range(10)
+ BUF_TILE_RANGES, BUF_GRAD2D, BUF_RECORDS, BUF_VISIBILITY) = range(12)
 
 EXPORTS = ["hg_status_str", "hg_last_error", "hg_version", "hg_ctx_create", "hg_ctx_destroy",
            "hg_create_scene", "hg_destroy_scene", "hg_scene_size", "hg_render", "hg_render_splats",

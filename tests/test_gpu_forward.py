@@ -78,6 +78,46 @@ def test_projection_sh3_colour(lib, ctx):
         assert np.array_equal(sp[v]["depth_key"][ok], pr["depth_key"][ok])
 
 
+def _projection_views(lib, st, n, n_views):
+    """Oracle binning inputs from the projection's own float32 raster records
+    and visibility bits (culled entries get radius 0)."""
+    rec = st.read(lib.BUF_RECORDS, np.float32).reshape(n_views, n, 16)
+    vis = st.read(lib.BUF_VISIBILITY).reshape(n_views, -1)
+    views = []
+    for v in range(n_views):
+        on = np.unpackbits(vis[v].view(np.uint8), bitorder="little")[:n].astype(bool)
+        r = np.where(on[:, None], rec[v], 0.0).astype(np.float32)
+        rad = np.where(on, r[:, 6].view(np.int32), 0).astype(np.int64)
+        views.append((r[:, 0].copy(), r[:, 1].copy(), rad, r[:, 7].view(np.uint32).copy(),
+                      (r[:, 2].copy(), r[:, 3].copy(), r[:, 4].copy(), r[:, 5].copy())))
+    return views
+
+
+@pytest.mark.parametrize("macro", [(8, 4), (4, 4), (8, 8)])
+def test_projection_binning_matches_oracle(lib, ctx, macro):
+    """Pairs of the projection path with the ellipse test (the binning record
+    made in the projection, refined for the entries that need it after the
+    view loop) equal the oracle's binning stages run on the projection's own
+    float32 records: bit-exact segments, keys and ids, over 4 views."""
+    import torch
+    scene = scenes.cluster_scene(120_000, 24, 1.4, seed=9, sigma_range=scenes.CLUSTER_SIGMA, extent=scenes.EXTENT)
+    cams = scenes.scene_orbit(4, 960, 540)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    st = lib.State(ctx)
+    lib.render(gs, cams, lib.Options(macro_w=macro[0], macro_h=macro[1], bin_test=lib.BIN_ELLIPSE), state=st)
+    torch.cuda.synchronize()
+    n = scene.means.shape[0]
+    ref = BN.segments(_projection_views(lib, st, n, len(cams)), [(c.width, c.height) for c in cams],
+                      macro[0] * 8, macro[1] * 8)
+    assert np.array_equal(st.read(lib.BUF_SEG_OFF).astype(np.int64), ref["seg_off"])
+    assert np.array_equal(st.read(lib.BUF_PAIR_KEYS), ref["keys"])
+    assert np.array_equal(st.read(lib.BUF_PAIR_IDS).astype(np.int64), ref["ids"])
+    # the ellipse test dropped cells of multi-cell rectangles
+    rect = BN.segments([vw[:4] for vw in _projection_views(lib, st, n, len(cams))],
+                       [(c.width, c.height) for c in cams], macro[0] * 8, macro[1] * 8)
+    assert 0 < len(ref["keys"]) < len(rect["keys"])
+
+
 # ------------------------------------------------------------ discrete stages
 def _oracle_views(projs, ellipse):
     """Oracle binning inputs from the same float32 values the splats carry."""
