@@ -104,6 +104,11 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
   if (tid == 0) rank_last = 0;
   __syncthreads();
   uint32_t c_pairs = 0, c_batches = 0, c_tier[N_TIERS] = {}, c_tiles = 0, mx = 0;
+  // segments of 1 to 4 batches (nearly all) are counted in registers and
+  // summed per warp: shared-memory atomics on the same few counters from
+  // every thread serialise
+  constexpr int FEW = 4;
+  uint32_t few[FEW] = {};
   for (int s = s0; s < s1; ++s) {
     const uint32_t n = a.seg_tot[s];
     const uint32_t nb = (n + cap - 1) / cap;
@@ -113,10 +118,17 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
     c_tier[t]++;
     if (t == TIER_OS) c_tiles += (n + OS_TILE - 1) / OS_TILE;
     mx = max(mx, n);
-    if (nb > 0) {
+#pragma unroll
+    for (int k = 0; k < FEW; ++k) few[k] += nb == (uint32_t)(k + 1);
+    if (nb > (uint32_t)FEW) {
       atomicAdd(&rank_hist[min(nb, (uint32_t)MAX_RANKS - 1)], 1u);
       if (nb > (uint32_t)MAX_RANKS - 1) atomicAdd(&rank_last, nb - (MAX_RANKS - 1));
     }
+  }
+#pragma unroll
+  for (int k = 0; k < FEW; ++k) {
+    const uint32_t w = warp_sum(few[k]);
+    if ((tid & 31) == 0 && w) atomicAdd(&rank_hist[k + 1], w);
   }
   uint32_t t_pairs, t_batches, t_tier[N_TIERS], t_tiles;
   const uint32_t o_pairs = block_excl_scan(c_pairs, tmp, &t_pairs);
@@ -249,11 +261,21 @@ __global__ void k_batches(PartitionArgs a) {
   const uint32_t cap = (uint32_t)a.batch_cap;
   const uint32_t st = a.seg_off[s], n = a.seg_off[s + 1] - st;
   const uint32_t nb = (n + cap - 1) / cap, fb = a.first_batch[s];
-  for (uint32_t j = 0; j < nb; ++j) {
+  const uint32_t active = __activemask();
+  const int lane = threadIdx.x & 31;
+  for (uint32_t j = 0;; ++j) {
+    // every lane still in the loop takes a slot of rank j: one atomic per
+    // warp and rank (the ranks' cursors are shared by all segments)
+    const uint32_t m = __ballot_sync(active, j < nb);
+    if (!m) break;
+    if (j >= nb) continue;
     const uint32_t r = fb + j;
     a.batches[r] = make_uint4((uint32_t)s, st + j * cap, min(cap, n - j * cap), j);
-    const uint32_t pos = atomicAdd(&a.rank_count[min(j, (uint32_t)MAX_RANKS - 1)], 1u);
-    a.batch_order[pos] = r;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&a.rank_count[min(j, (uint32_t)MAX_RANKS - 1)], (uint32_t)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    a.batch_order[base + __popc(m & lanemask_lt())] = r;
   }
 }
 

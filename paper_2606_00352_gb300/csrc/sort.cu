@@ -41,14 +41,16 @@ struct BlockSortSmem {
 // region, moving both arrays: the region's pairs are spread evenly over the
 // warps (rows = ceil(n / NT) item slots per thread; slots [n, rows * NT) must
 // hold key and value 0xffffffff and get the largest digit, so padding always
-// ranks after the real pairs).  Spans of 25 to 27 bits take three 9-bit
-// passes, others ceil(bits / 8) 8-bit passes.  Every pass is stable.
+// ranks after the real pairs).  In CTAs of 512 threads or more, spans of
+// 25 to 27 bits take three 9-bit passes; otherwise ceil(bits / 8) 8-bit
+// passes (the 9-bit passes' 512 counters per warp cost more than the pass
+// they save in the small tier).  Every pass is stable.
 template <int NT, int IPT>
 __device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int bits,
                                              bool by_val, RowRankSmem<NT>& rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = (n + NT - 1) / NT;  // <= IPT
-  const bool wide = bits > 24 && bits <= 27;
+  const bool wide = NT >= 512 && bits > 24 && bits <= 27;
   const int dbits = wide ? 9 : 8, passes = wide ? 3 : (bits + 7) / 8;
   const uint32_t dmask = wide ? 0x1ffu : 0xffu;
   for (int pass = 0; pass < passes; ++pass) {

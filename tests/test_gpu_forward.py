@@ -232,8 +232,8 @@ def test_discrete_stages_all_tiers(lib, ctx):
 @pytest.mark.parametrize("octaves,bits", [(2, 24), (3, 25), (5, 26), (9, 27), (17, 28)])
 def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
     """Depth keys spanning 24 to 28 bits in every shared-memory tier (the
-    tiers sort spans of 25 to 27 bits with 9-bit digits, others with 8-bit
-    ones), with ties."""
+    tiers of 512 and 1,024 threads sort spans of 25 to 27 bits with 9-bit
+    digits, other spans and the <=1K tier with 8-bit ones), with ties."""
     cam = scenes.look_at((3, 0, 0), width=512, height=96)
     g = np.random.default_rng(100 + octaves)
     parts = []
