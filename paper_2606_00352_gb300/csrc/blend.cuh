@@ -62,14 +62,22 @@ __device__ __forceinline__ void pixel_load(PixelAcc& p, bool inside, const float
 // when e >= E', and no float lies between E and E'.  (Only for E < 2^-40,
 // alpha within a factor 2^(2^-40) of 1/255, does it accept e up to 2^-40.)
 // Returns alpha, or 0 when the gaussian fails the test; raw = o 2^-e.
-__device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g0, const float4& g1,
-                                          const float4& g2, float& raw) {
+// alpha_terms also returns ex = 2^-e, the derivative of raw with respect to
+// the opacity (the backward's d alpha / d o).
+__device__ __forceinline__ float alpha_terms(float ubase, float dy, const float4& g0, const float4& g1,
+                                             const float4& g2, float& raw, float& ex) {
   const float u = fmaf(g0.w, dy, ubase);
   const float w = g1.x * dy;
   const float e = fmaf(u, u, w * w);
-  raw = g1.y * ex2_approx(-e);
+  ex = ex2_approx(-e);
+  raw = g1.y * ex;
   const float f = __saturatef(fmaf(e, -18446744073709551616.f, g2.w));
   return fminf(ALPHA_MAX, raw) * f;
+}
+__device__ __forceinline__ float alpha_of(float ubase, float dy, const float4& g0, const float4& g1,
+                                          const float4& g2, float& raw) {
+  float ex;
+  return alpha_terms(ubase, dy, g0, g1, g2, raw, ex);
 }
 
 // Per-gaussian level of the blend test as the record stores it (g2.w):
