@@ -435,11 +435,12 @@ def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# each stage's kernels on this workload (spatially ordered scene), from one
-# ncu capture of `bench.py --case 5m8 --macro 4x4 --steps 1 --warmup 1`
-# (summary under profiles/), valid while the CUDA sources hash to `digest`.
-MEASURED_TRAFFIC = {"digest": "38ef430349f69fce",
-                    "bytes": {"project": 2926.4e6, "partition": 913.5e6, "sort": 231.5e6, "raster": 2202.5e6,
+# each stage's kernels on this workload (spatially ordered scene), from ncu
+# captures of the first frame of `bench.py --case 5m8 --macro 4x4 --steps 1
+# --warmup 1`, one stage's kernels per capture (summary under profiles/),
+# valid while the CUDA sources hash to `digest`.
+MEASURED_TRAFFIC = {"digest": "1d02c804a5b6e5e9",
+                    "bytes": {"project": 2929.0e6, "partition": 916.1e6, "sort": 231.8e6, "raster": 2181.6e6,
                               "merge": 0.05e6}}
 
 
