@@ -122,8 +122,11 @@ def _workload_records(scene, cam):
 @pytest.mark.parametrize("seed", [5, 6])
 def test_ellipse_pairs_cover_blend_support(bw, bh, seed):
     """Every pixel where the float64 blend test passes (q <= 9 and alpha >=
-    1/255) lies in a macro-tile paired with the gaussian, and the ellipse
-    pairs are a subset of the rectangle pairs."""
+    1/255) lies in a macro-tile paired with the gaussian, the ellipse pairs
+    are a subset of the rectangle pairs, and they are tight: at most 1% more
+    than the pixel-exact float64 pairs (measured at most 0.8%, at 8x8 cells
+    where the rectangle gives 60-70% more), so a span widened beyond its
+    stated margins fails here."""
     w = h = 96
     sc, cam = _tiny_random(n=300, w=w, h=h, seed=seed)
     pr, (mx, my, r, key), ell = _workload_records(sc, cam)
@@ -142,6 +145,7 @@ def test_ellipse_pairs_cover_blend_support(bw, bh, seed):
             need.add(((y // bh) * gw + x // bw, int(i)))
     assert need <= got
     assert len(need) > 50
+    assert len(got) <= 1.01 * len(need)
 
 
 def test_ellipse_reduces_macro_pairs():
