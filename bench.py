@@ -830,7 +830,14 @@ def gpu_arm(args):
             "pixel_support_evals_first_step": prof["pixel_support_evals"],
             "pixel_contrib_evals_first_step": prof["pixel_contrib_evals"],
             "raster_evals_first_step": prof["raster_evals"],
+            "pixel_live_evals_first_step": prof["pixel_live_evals"],
             "intrinsic_share_of_raster_evals": round(prof["pixel_support_evals"] / max(1, prof["raster_evals"]), 4),
+            # the other evaluations: live pixels outside the support, and
+            # pixels that stopped before their tile's last live pixel
+            "live_outside_support_share": round((prof["pixel_live_evals"] - prof["pixel_support_evals"])
+                                                / max(1, prof["raster_evals"]), 4),
+            "stopped_pixel_share": round((prof["raster_evals"] - prof["pixel_live_evals"])
+                                         / max(1, prof["raster_evals"]), 4),
             "raster_phase_cycles_first_step": dict(zip(("gather", "masks", "chain_wait", "blend_warps",
                                                         "end_barrier_warps", "units"), prof["raster_cycles"])),
         } | (amb_stats or {}),

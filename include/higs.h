@@ -212,8 +212,10 @@ typedef struct {
   /* with HG_FLAG_PROFILE (float32 rasteriser): the intrinsic per-pixel work,
    * the (pixel, gaussian) evaluations a per-pixel renderer cannot skip
    * (support q <= 9 while the pixel is live, up to and including its stop),
-   * and those of them that contributed a colour */
-  int64_t pixel_support_evals, pixel_contrib_evals;
+   * and those of them that contributed a colour; and the rasteriser's
+   * evaluations of pixels still live, in or out of the support (its other
+   * evaluations are of pixels that had stopped) */
+  int64_t pixel_support_evals, pixel_contrib_evals, pixel_live_evals;
 } hg_frame_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -183,6 +183,38 @@ def render(proj: dict, bg=(0.0, 0.0, 0.0), tiles=None, tile: int = 8, cand=None)
     return out
 
 
+def pixel_work(proj: dict, tiles=None, tile: int = 8, cand=None):
+    """Per-pixel work counts of the compositing definition (Sec. 3.4), the
+    intrinsic work a per-pixel renderer cannot skip: n_support [H, W], the
+    gaussians with q <= 9 at the pixel up to and including the one that
+    stops it (all of them when it never stops), and n_contrib [H, W], the
+    gaussians blended into it (q <= 9 and alpha >= 1/255, before the stop).
+    Pixels of tiles not listed are -1."""
+    w, h = proj["width"], proj["height"]
+    n_sup = np.full((h, w), -1, np.int64)
+    n_con = np.full((h, w), -1, np.int64)
+    gw, gh, off, gid = tile_candidates(proj, tile) if cand is None else cand
+    todo = range(gw * gh) if tiles is None else tiles
+    for t in todo:
+        tx, ty = t % gw, t // gw
+        px, py = _tile_pixels(tx, ty, tile, w, h)
+        ids = gid[off[t]:off[t + 1]]
+        n = len(ids)
+        if n == 0:
+            n_sup[py, px] = 0
+            n_con[py, px] = 0
+            continue
+        q, alpha = alpha_at(proj, ids, px.astype(np.float64), py.astype(np.float64))
+        contrib = (q <= SUPPORT_Q) & (alpha >= ALPHA_MIN)
+        t_after = np.cumprod(1.0 - np.where(contrib, alpha, 0.0), axis=0)
+        stop_here = contrib & (t_after < T_EPS)
+        stop = np.where(stop_here.any(axis=0), np.argmax(stop_here, axis=0), n)
+        i = np.arange(n)[:, None]
+        n_sup[py, px] = ((q <= SUPPORT_Q) & (i <= stop[None, :])).sum(axis=0)
+        n_con[py, px] = (contrib & (i < stop[None, :])).sum(axis=0)
+    return n_sup, n_con
+
+
 def pixel_brute_force(proj: dict, px: int, py: int, bg=(0.0, 0.0, 0.0)):
     """One pixel, every visible gaussian considered, explicit loop."""
     vis = np.nonzero(proj["visible"])[0]

@@ -833,6 +833,7 @@ extern "C" hg_status hg_render_stats(hg_state* s, hg_frame_stats* out) {
   for (int k = 0; k < 6; ++k) out->raster_cycles[k] = (int64_t)f.raster_cycles[k];
   out->pixel_support_evals = (int64_t)f.pixel_support_evals;
   out->pixel_contrib_evals = (int64_t)f.pixel_contrib_evals;
+  out->pixel_live_evals = (int64_t)f.pixel_live_evals;
   if (s->opts.flags & HG_FLAG_TIMING) {
     float ms[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&ms[k], s->ev[k], s->ev[k + 1]);

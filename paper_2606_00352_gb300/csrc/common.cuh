@@ -64,6 +64,7 @@ struct FrameCounters {
   // evaluations of live pixels up to their stop; contributing ones)
   unsigned long long pixel_support_evals;
   unsigned long long pixel_contrib_evals;
+  unsigned long long pixel_live_evals;  // evaluations of pixels still live
   // rasteriser phase cycles summed over units (HG_FLAG_PROFILE): load, masks,
   // chain wait, blend (per warp, summed), end barrier (per warp, summed), units
   unsigned long long raster_cycles[6];

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   if (read_status(a.fc)) return;
   const uint32_t n_units = a.fc->n_batches;
   uint32_t phase = 0;
-  unsigned long long evals = 0, e_sup = 0, e_con = 0;
+  unsigned long long evals = 0, e_sup = 0, e_con = 0, e_live = 0;
 
   while (true) {
     if (tid == 0) {
@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
               const float u0 = fmaf(g0.w, dy0, ub), w0 = g1.x * dy0, u1 = fmaf(g0.w, dy1, ub), w1 = g1.x * dy1;
               e_sup += ((mt & bit) && pixel_live(p0) && fmaf(u0, u0, w0 * w0) <= SUPPORT_E) +
                        ((mb & bit) && pixel_live(p1) && fmaf(u1, u1, w1 * w1) <= SUPPORT_E);
+              e_live += ((mt & bit) && pixel_live(p0)) + ((mb & bit) && pixel_live(p1));
             }
             // a half the gaussian cannot reach is skipped (its blend is a no-op)
             if (mt & bit) {
@@ -375,9 +376,11 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
   if (STATS) {
     e_sup = warp_sum(e_sup);
     e_con = warp_sum(e_con);
+    e_live = warp_sum(e_live);
     if (lane == 0) {
       atomicAdd(&a.fc->pixel_support_evals, e_sup);
       atomicAdd(&a.fc->pixel_contrib_evals, e_con);
+      atomicAdd(&a.fc->pixel_live_evals, e_live);
     }
   }
 }

@@ -105,7 +105,7 @@ class FrameStats(C.Structure):
                 ("pad", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
                 ("ms_sort", C.c_float), ("ms_raster", C.c_float), ("ms_merge", C.c_float),
                 ("ms_total", C.c_float), ("raster_cycles", C.c_int64 * 6), ("pixel_support_evals", C.c_int64),
-                ("pixel_contrib_evals", C.c_int64)]
+                ("pixel_contrib_evals", C.c_int64), ("pixel_live_evals", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "seg_by_tier", "raster_cycles")}

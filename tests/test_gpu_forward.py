@@ -11,7 +11,7 @@ from paper_2606_00352_gb300 import scenes
 from oracle import binning as BN
 from oracle import composite as C
 from oracle import project as P
-from tests.helpers import compare_image, splat_records, sample_tiles, tiles_mask
+from tests.helpers import ambiguous, compare_image, splat_records, sample_tiles, tiles_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -490,6 +490,46 @@ def test_edge_cases_empty_culled_single(lib, ctx):
         for path in (lib.PATH_HIGS, lib.PATH_PLAIN):
             imgs, ts = render_np(lib, gs, [cam], path=path)
             compare_image(imgs[0], ts[0], C.render(P.project(sc, cam)))
+
+
+@pytest.mark.parametrize("which", ["tiny", "cluster"])
+def test_profiled_work_counts_match_oracle(lib, ctx, which):
+    """HG_FLAG_PROFILE counters against the oracle's per-pixel work: the
+    (pixel, gaussian) contributions equal the oracle's count (up to the
+    decision-ambiguous pixels); the support evaluations lie between the
+    contributions and the oracle's support count (the rasteriser evaluates
+    only inside its masks, which hold every gaussian that can blend); the
+    live-pixel evaluations and all evaluations bound them from above."""
+    import torch
+    if which == "tiny":
+        scene, cams = scenes.tiny_workload()
+        opts = lib.Options(flags=lib.FLAG_PROFILE)
+    else:
+        scene = scenes.cluster_scene(40_000, 16, 1.4, seed=11, sigma_range=scenes.CLUSTER_SIGMA,
+                                     extent=scenes.EXTENT)
+        cams = [scenes.scene_orbit(8, 320, 240)[2]]
+        opts = lib.Options(flags=lib.FLAG_PROFILE, macro_w=4, macro_h=4, batch_cap=256,
+                           bin_test=lib.BIN_ELLIPSE)
+    gs = lib.GpuScene.from_scene(ctx, scene)
+    st = lib.State(ctx)
+    lib.render(gs, cams, opts, state=st)
+    torch.cuda.synchronize()
+    s = st.stats()
+    pr = P.project(scene, cams[0])
+    n_sup, n_con = C.pixel_work(pr)
+    ref_con, ref_sup = int(n_con.sum()), int(n_sup.sum())
+    amb = int(ambiguous(C.render(pr)).sum())
+    print("work counts", which, s["pixel_contrib_evals"], ref_con, s["pixel_support_evals"], ref_sup,
+          s["pixel_live_evals"], s["raster_evals"], "ambiguous pixels", amb)  # pytest -s
+    assert ref_con > 1000 and s["n_replays"] == 0
+    # float32 against float64 decides a few (pixel, gaussian) alpha and
+    # support tests differently, also where the oracle calls the effect on
+    # the pixel insignificant: a small absolute allowance besides the
+    # ambiguous pixels
+    slack = 1e-4 * ref_con + 8 * amb + 10
+    assert abs(s["pixel_contrib_evals"] - ref_con) <= slack
+    assert s["pixel_contrib_evals"] <= s["pixel_support_evals"] <= ref_sup + slack
+    assert s["pixel_support_evals"] <= s["pixel_live_evals"] <= s["raster_evals"]
 
 
 def test_deterministic(lib, ctx):

@@ -185,6 +185,50 @@ def test_render_equals_brute_force(seed):
         assert stops > 10  # the termination rule is exercised
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pixel_work_equals_sequential_loop(seed):
+    """Per-pixel work counts of the tile-pruned oracle == an explicit loop
+    over every visible gaussian in (key, id) order: contributions as the
+    sequential compositing loop counts them, support evaluations (q <= 9)
+    up to and including the stopping gaussian."""
+    sc, cam = _tiny_random(seed=seed)
+    pr = P.project(sc, cam)
+    n_sup, n_con = C.pixel_work(pr)
+    vis = np.nonzero(pr["visible"])[0]
+    order = vis[np.lexsort((vis, pr["depth_key"][vis]))]
+    stops = 0
+    for y in range(cam.height):
+        for x in range(cam.width):
+            q, al = C.alpha_at(pr, order, np.array([float(x)]), np.array([float(y)]))
+            q, al = q[:, 0], al[:, 0]
+            _, _, st, nc = C.composite_sequence(al, q, pr["rgb"][order])
+            t, sup = 1.0, 0
+            for i in range(len(order)):
+                if q[i] > 9.0:
+                    continue
+                sup += 1
+                if al[i] < 1.0 / 255.0:
+                    continue
+                t *= 1.0 - al[i]
+                if t < 1e-4:
+                    break
+            assert n_con[y, x] == nc and n_sup[y, x] == sup, (x, y)
+            stops += st
+    assert stops > 10 or seed != 0
+
+
+def test_pixel_work_of_the_termination_stack():
+    """Five alpha = 0.95 layers at the centre pixel: three are blended and
+    the fourth stops the pixel, so 3 contributions and 4 support
+    evaluations."""
+    cam = axis_camera(w=16, h=16, f=16.0, cx=8.5, cy=8.5)
+    n = 5
+    sc = one_scene([[0, 0, 2.0 + 0.1 * i] for i in range(n)], [[-2] * 3] * n,
+                   [[1, 0, 0, 0]] * n, [math.log(0.95 / 0.05)] * n, [[0.4, 0.4, 0.4]] * n)
+    n_sup, n_con = C.pixel_work(P.project(sc, cam))
+    assert n_con[8, 8] == 3 and n_sup[8, 8] == 4
+
+
 def test_two_gaussian_depth_order():
     """C = c1 a1 + c2 a2 (1 - a1) with the nearer gaussian first."""
     o1, o2 = 0.6, 0.7
