@@ -78,6 +78,13 @@ __device__ __forceinline__ int read_status(const FrameCounters* fc) {
   return *((volatile const int*)&fc->status);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel of its stream is still
+// finishing; it calls pdl_wait() before it reads anything that kernel
+// wrote (the previous grid has then completed and its writes are visible).
+// Without that launch attribute the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

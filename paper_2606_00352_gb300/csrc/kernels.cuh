@@ -269,6 +269,26 @@ cudaError_t launch_onesweep(const OsTileView& tv, K* keys, uint32_t* vals, K* ke
 void note_launch(int n = 1);
 long long launches_issued();
 
+// Launch with programmatic stream serialization: the kernel's CTAs may be
+// scheduled while the stream's previous kernel drains; the kernel must call
+// pdl_wait() before reading that kernel's results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_splats_to_records(const hg_splat* sp, long long n, int n_views, long long vis_words,
                                      const ProjectArgs& out, cudaStream_t st);

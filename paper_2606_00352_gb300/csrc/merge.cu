@@ -54,6 +54,7 @@ __device__ __forceinline__ float4 shfl4(const float4& v, int src) {
 
 template <int MW, int MH>
 __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
+  pdl_wait();
   constexpr int M = MW * MH;
   if (read_status(a.fc)) return;
   const int lane = threadIdx.x & 31;
@@ -170,9 +171,8 @@ cudaError_t launch_merge_shape(const MergeArgs& a, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int blocks = min((a.total_tiles + 7) / 8, sms * 8);
   if (blocks < 1) blocks = 1;
-  k_merge<MW, MH><<<blocks, 256, 0, st>>>(a);
-  note_launch();
-  return cudaGetLastError();
+  // launches while the rasteriser drains (programmatic dependent launch)
+  return launch_pdl(k_merge<MW, MH>, dim3(blocks), dim3(256), 0, st, a);
 }
 
 }  // namespace

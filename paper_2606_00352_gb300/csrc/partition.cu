@@ -26,6 +26,7 @@ constexpr int PART_THREADS = 512;
 constexpr int UNR = 2;  // entries per thread per round in count / fill
 
 __global__ void __launch_bounds__(PART_THREADS) k_count(PartitionArgs a) {
+  pdl_wait();
   extern __shared__ uint32_t hist[];
   if (read_status(a.fc)) return;
   const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_count(PartitionArgs a) {
 
 // 32 columns x 32 batch chunks per CTA.
 __global__ void __launch_bounds__(1024) k_colscan(PartitionArgs a) {
+  pdl_wait();
   __shared__ uint32_t part[32][33];
   if (read_status(a.fc)) return;
   const int sx = threadIdx.x, cy = threadIdx.y;
@@ -91,6 +93,7 @@ __device__ __forceinline__ int seg_tier(uint32_t n) {
 }
 
 __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
+  pdl_wait();
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t rank_hist[MAX_RANKS];
   __shared__ uint32_t rank_last;
@@ -216,6 +219,7 @@ __global__ void __launch_bounds__(1024) k_segscan(PartitionArgs a) {
 }
 
 __global__ void __launch_bounds__(PART_THREADS) k_fill(PartitionArgs a) {
+  pdl_wait();
   extern __shared__ uint32_t cursor[];
   if (read_status(a.fc)) return;
   const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_fill(PartitionArgs a) {
 }
 
 __global__ void k_batches(PartitionArgs a) {
+  pdl_wait();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.n_seg || read_status(a.fc)) return;
   const uint32_t cap = (uint32_t)a.batch_cap;
@@ -292,21 +297,13 @@ cudaError_t launch_partition(const PartitionArgs& a, cudaStream_t st) {
   }
   if (a.n_pb == 0 || a.n_seg == 0) return cudaSuccess;
   dim3 g(a.n_pb, a.n_views);
-  k_count<<<g, PART_THREADS, sm, st>>>(a);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_colscan<<<(a.n_seg + 31) / 32, dim3(32, 32), 0, st>>>(a);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_segscan<<<1, 1024, 0, st>>>(a);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_fill<<<g, PART_THREADS, sm, st>>>(a);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_batches<<<(a.n_seg + 255) / 256, 256, 0, st>>>(a);
-  note_launch();
-  return cudaGetLastError();
+  // each kernel of the chain launches while the previous one drains
+  // (programmatic dependent launch) and waits for it before its first read
+  if ((e = launch_pdl(k_count, g, dim3(PART_THREADS), sm, st, a)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_colscan, dim3((a.n_seg + 31) / 32), dim3(32, 32), 0, st, a)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_segscan, dim3(1), dim3(1024), 0, st, a)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_fill, g, dim3(PART_THREADS), sm, st, a)) != cudaSuccess) return e;
+  return launch_pdl(k_batches, dim3((a.n_seg + 255) / 256), dim3(256), 0, st, a);
 }
 
 }  // namespace hg
