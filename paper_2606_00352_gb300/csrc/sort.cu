@@ -1,9 +1,11 @@
 // Segmented depth sort (Sec. 3.3, 4.4).  Every (view, macro-tile) segment of
 // (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
-//   * segments of <= 8K pairs: one CTA sorts the segment in shared memory
-//     (tiers <= 1K / 4K / 8K pairs), over the digits of (key - min key);
-//   * segments of 8K..16K pairs: one CTA sorts the two halves in shared
-//     memory the same way and merges them (merge path) into the output;
+//   * segments of <= 1K pairs: one CTA of 128 threads sorts the segment in
+//     shared memory, over the digits of (key - min key);
+//   * segments of 1K..4K, 4K..8K and 8K..16K pairs: one CTA (256, 512 or
+//     1,024 threads) sorts the two halves in shared memory the same way and
+//     merges them (merge path) into the output; the smaller CTAs fit more
+//     segments per SM than one CTA over the whole segment would;
 //   * larger segments (> 16K): a segment-local onesweep (one kernel per 8-bit
 //     digit pass, decoupled look-back across the segment's tiles, tiles
 //     claimed in order through an atomic counter so every awaited
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a
   }
 }
 
-// Segments of 8K..16K pairs: the two halves are sorted in their own
+// Segments of 1K..16K pairs: the two halves are sorted in their own
 // shared-memory regions of NT * IPT slots (sort_region), then merged by the
 // merge path straight into the output: thread t finds, by binary search on
 // its output diagonal, how many of its first outputs come from each half
@@ -245,7 +247,7 @@ __device__ __forceinline__ bool pair_less(uint32_t ka, uint32_t va, uint32_t kb,
 }
 
 template <int NT, int IPT>
-__global__ void __launch_bounds__(NT) k_block_merge_sort(SortArgs a, int tier) {
+__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_merge_sort(SortArgs a, int tier) {
   constexpr int H = NT * IPT;  // one half's region
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MergeSortSmem<NT, IPT>& s = *reinterpret_cast<MergeSortSmem<NT, IPT>*>(smem_raw);
@@ -607,12 +609,12 @@ static cudaError_t launch_onesweep_by_val_key(const OsTileView& tv, uint32_t* ke
 }
 
 template <int NT, int IPT>
-static cudaError_t launch_merge_tier(const SortArgs& a, int tier, cudaStream_t st) {
+static cudaError_t launch_merge_tier(const SortArgs& a, int tier, int blocks_per_sm, cudaStream_t st) {
   size_t sm = sizeof(MergeSortSmem<NT, IPT>);
   cudaError_t e =
       cudaFuncSetAttribute(k_block_merge_sort<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_block_merge_sort<NT, IPT><<<num_sms(), NT, sm, st>>>(a, tier);
+  k_block_merge_sort<NT, IPT><<<num_sms() * blocks_per_sm, NT, sm, st>>>(a, tier);
   note_launch();
   return cudaGetLastError();
 }
@@ -622,9 +624,9 @@ static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaS
   cudaError_t e;
   // the largest tiers first, each on its own stream when s1..s3 differ from
   // st: their tails overlap
-  if ((e = launch_merge_tier<1024, 8>(a, 3, s3)) != cudaSuccess) return e;
-  if ((e = launch_tier<1024, 8>(a, 2, 1, s2)) != cudaSuccess) return e;
-  if ((e = launch_tier<512, 8>(a, 1, 2, s1)) != cudaSuccess) return e;
+  if ((e = launch_merge_tier<1024, 8>(a, 3, 1, s3)) != cudaSuccess) return e;
+  if ((e = launch_merge_tier<512, 8>(a, 2, 2, s2)) != cudaSuccess) return e;
+  if ((e = launch_merge_tier<256, 8>(a, 1, 4, s1)) != cudaSuccess) return e;
   if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   // the partition zeroed the big segments' histograms
