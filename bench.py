@@ -17,6 +17,7 @@ the FP64 CPU oracle on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import math
 import os
@@ -406,10 +407,16 @@ def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
     copied = [torch.cuda.Event() for _ in range(2)]
     state = lib.State(gs.ctx)
 
-    def step(k):
+    # the warm-up frames size the workspace (synchronous calls); the timed
+    # ones are asynchronous, so the host enqueues the next frame while the
+    # device renders, as a throughput client of hg_render would
+    async_opts = copy.copy(opts)
+    async_opts.flags = opts.flags | lib.FLAG_ASYNC
+
+    def step(k, o=opts):
         b = k % 2
         stream.wait_event(copied[b])  # the buffer's previous read-back is done
-        lib.render(gs, pose_batch(cams, k, rank), opts, state=state, stream=stream, out_rgb=rgb[b], with_T=False)
+        lib.render(gs, pose_batch(cams, k, rank), o, state=state, stream=stream, out_rgb=rgb[b], with_T=False)
         rendered[b].record(stream)
         copy_stream.wait_event(rendered[b])
         with torch.cuda.stream(copy_stream):
@@ -425,11 +432,14 @@ def time_e2e(lib, gs, cams, opts, steps, warmup, rank, stream):
         stream.synchronize()
         t0 = time.perf_counter()
         for k in range(steps):
-            step(warmup + k)
+            step(warmup + k, async_opts)
         copy_stream.synchronize()
         stream.synchronize()
         dt = time.perf_counter() - t0
+    status = state.sync()
     state.close()
+    if status != 0:
+        raise RuntimeError(f"asynchronous frames ended with device status {status}")
     view_desc_bytes = 144  # camera table entry uploaded per view by hg_render
     return {"seconds": dt, "h2d": VIEWS * view_desc_bytes, "d2h": pix * 3 * 4}
 

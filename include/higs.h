@@ -270,6 +270,9 @@ int64_t hg_scene_size(const hg_scene* scene);
  *  Unless HG_FLAG_ASYNC is set the call synchronises `stream` and returns
  *  the device status; when a workspace buffer was too small it grows it and
  *  renders again, so HG_ERR_CAPACITY is only seen in asynchronous use.
+ *  Asynchronous frames may follow one another on one state and stream (the
+ *  call waits, on the host, only until the previous frame's camera table has
+ *  been uploaded); hg_state_sync then returns the last frame's status.
  * Errors: HG_ERR_INVALID_ARG (bad sizes or options), HG_ERR_OOM,
  *  HG_ERR_CUDA, HG_ERR_DEVICE_TIMEOUT. */
 hg_status hg_render(hg_scene* scene, const hg_camera* cams, int n_views,

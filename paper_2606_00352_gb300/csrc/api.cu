@@ -311,6 +311,7 @@ hg_status state_create(hg_ctx* ctx, hg_state** out) {
   memset(s->fc_host, 0, sizeof(FrameCounters));
   for (int i = 0; i < N_EVENTS; ++i) cudaEventCreate(&s->ev[i]);
   cudaEventCreateWithFlags(&s->frame_done, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&s->views_uploaded, cudaEventDisableTiming);
   {
     SortStreams& ss = s->sort_streams;
     bool ok = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess;
@@ -335,6 +336,7 @@ extern "C" void hg_state_free(hg_state* s) {
   for (int i = 0; i < BUF_COUNT; ++i) ctx_free(s->ctx, s->bufs[i].p, s->bufs[i].bytes, nullptr);
   for (int i = 0; i < N_EVENTS; ++i) cudaEventDestroy(s->ev[i]);
   if (s->frame_done) cudaEventDestroy(s->frame_done);
+  if (s->views_uploaded) cudaEventDestroy(s->views_uploaded);
   {
     SortStreams& ss = s->sort_streams;
     if (ss.fork) cudaEventDestroy(ss.fork);
@@ -522,6 +524,11 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
   if (timing) HG_TRY(record_stage(s->ev[0], st), "stage event 0");
   HG_TRY(cudaMemsetAsync(fc, 0, sizeof(FrameCounters), st), "memset counters");
   HG_TRY(cudaMemcpyAsync(views, s->views_host, sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, st), "upload views");
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HG_TRY(cudaStreamIsCapturing(st, &cs), "capture status");
+    if (cs == cudaStreamCaptureStatusNone) HG_TRY(cudaEventRecord(s->views_uploaded, st), "views uploaded");
+  }
   ProjectArgs pj{};
   pj.n = n;
   pj.views = views;
@@ -720,6 +727,9 @@ hg_status enqueue_frame(hg_state* s, const FrameInputs& in, const hg_render_opts
 
 hg_status run_frame(hg_state* s, const FrameInputs& in, const hg_render_opts* o, const hg_camera* cams, int V,
                     float* out_rgb, float* out_T, cudaStream_t st) {
+  // the previous frame's view table must have been uploaded before it is
+  // overwritten (an asynchronous frame may still wait in its stream)
+  HG_TRY(cudaEventSynchronize(s->views_uploaded), "view table in use");
   FrameGeom g;
   hg_status r = build_views(s, cams, V, o, g);
   if (r != HG_OK) return r;

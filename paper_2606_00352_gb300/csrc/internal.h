@@ -72,6 +72,10 @@ struct hg_state {
   hg::Buf bufs[hg::BUF_COUNT];
   hg::FrameCounters* fc_host = nullptr;  // pinned
   hg::ViewDesc* views_host = nullptr;    // pinned, MAX_VIEWS entries
+  // recorded after the view table's upload of the last frame enqueued
+  // outside a capture: the next frame writes views_host only once that
+  // upload has run (asynchronous frames queue behind one another)
+  cudaEvent_t views_uploaded = nullptr;
   cudaEvent_t ev[hg::N_EVENTS] = {};
   hg::SortStreams sort_streams{};  // side streams of the sort tiers
   bool has_sort_streams = false;
