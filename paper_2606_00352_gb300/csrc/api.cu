@@ -840,6 +840,7 @@ extern "C" hg_status hg_render_stats(hg_state* s, hg_frame_stats* out) {
   out->n_replays = (int64_t)f.replays;
   out->raster_evals = (int64_t)f.raster_evals;
   out->status = f.status;
+  out->sort_resorts = (int32_t)f.sort_resorts;
   for (int k = 0; k < 6; ++k) out->raster_cycles[k] = (int64_t)f.raster_cycles[k];
   out->pixel_support_evals = (int64_t)f.pixel_support_evals;
   out->pixel_contrib_evals = (int64_t)f.pixel_contrib_evals;

@@ -1,7 +1,9 @@
 // Segmented depth sort (Sec. 3.3, 4.4).  Every (view, macro-tile) segment of
 // (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
 //   * segments of <= 1K pairs: one CTA of 128 threads sorts the segment in
-//     shared memory, over the digits of (key - min key);
+//     shared memory, over the top 16 bits of (key - min key) (two 8-bit
+//     passes), then puts the short runs of equal high bits in (key, id)
+//     order by insertion;
 //   * segments of 1K..4K, 4K..8K and 8K..16K pairs: one CTA (256, 512 or
 //     1,024 threads) sorts the two halves in shared memory the same way and
 //     merges them (merge path) into the output; the smaller CTAs fit more
@@ -12,11 +14,12 @@
 //     predecessor is running), preceded by one histogram kernel for all
 //     digits.  Its passes are stable, so it sorts by the id's four digits
 //     first and then by the key's: (key, id) order with no fix-up.
-// The fill pass writes a segment in a data-dependent order, so the shared
-// memory tiers break key ties by id afterwards: runs of up to 32 equal keys
-// by insertion, and a segment with a longer run is sorted again by id, then
-// by key (stable passes), so the cost stays linear in the segment size
-// whatever the keys.
+// The tiers of 512 and 1,024 threads sort the top 18 bits (two 9-bit
+// passes).  The run fix-up also breaks key ties by id (the fill pass writes
+// a segment in a data-dependent order).  A region with a run of more than
+// 32 equal high parts is sorted again over every key bit, and one with more
+// than 32 equal keys by id and then by key (stable passes), so the cost
+// stays linear in the segment size whatever the keys.
 #include <mutex>
 #include <string>
 #include <utility>
@@ -38,25 +41,27 @@ struct BlockSortSmem {
   uint32_t red[2][NT / 32];
 };
 
-// LSD radix passes over the `bits` low bits of (x - xmin), x = keys[e]
+// LSD radix passes over bits [lo, bits) of (x - xmin), x = keys[e]
 // (by_val false) or vals[e] (by_val true), of the n pairs of a shared-memory
 // region, moving both arrays: the region's pairs are spread evenly over the
 // warps (rows = ceil(n / NT) item slots per thread; slots [n, rows * NT) must
 // hold key and value 0xffffffff and get the largest digit, so padding always
-// ranks after the real pairs).  In CTAs of 512 threads or more, spans of
-// 25 to 27 bits take three 9-bit passes; otherwise ceil(bits / 8) 8-bit
-// passes (the 9-bit passes' 512 counters per warp cost more than the pass
-// they save in the small tier).  Every pass is stable.
+// ranks after the real pairs).  In CTAs of 512 threads or more a span that
+// 9-bit digits cover in fewer passes than 8-bit ones (9, 17-18, 25-27 bits)
+// takes 9-bit passes; otherwise ceil(span / 8) 8-bit passes (the 9-bit
+// passes' 512 counters per warp cost more than the pass they save in the
+// small tiers).  Every pass is stable.
 template <int NT, int IPT>
-__device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int bits,
+__device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int lo, int bits,
                                              bool by_val, RowRankSmem<NT>& rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = (n + NT - 1) / NT;  // <= IPT
-  const bool wide = NT >= 512 && bits > 24 && bits <= 27;
-  const int dbits = wide ? 9 : 8, passes = wide ? 3 : (bits + 7) / 8;
+  const int span = bits - lo;
+  const bool wide = NT >= 512 && span > 8 && (span + 8) / 9 < (span + 7) / 8;
+  const int dbits = wide ? 9 : 8, passes = wide ? (span + 8) / 9 : (span + 7) / 8;
   const uint32_t dmask = wide ? 0x1ffu : 0xffu;
   for (int pass = 0; pass < passes; ++pass) {
-    const int shift = dbits * pass;
+    const int shift = lo + dbits * pass;
     uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -83,60 +88,84 @@ template <int NT>
 __device__ __forceinline__ void block_min_max(uint32_t& mn, uint32_t& mx, uint32_t (*red)[NT / 32]);
 __device__ __forceinline__ int radix_bits(uint32_t kmin, uint32_t kmax);
 
-// Longest run of equal keys whose ids one thread re-sorts by insertion.
+// Longest run of pairs one thread puts in order by insertion after the
+// radix passes.
 constexpr int TIE_RUN_MAX = 32;
 
+__device__ __forceinline__ bool pair_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
 // Sorts the n pairs of a shared-memory region ascending by (key, id) (the
-// padding rule of radix_region applies): LSD passes over the digits of
-// (key - kmin), then the id tie-break.  Runs of equal keys of up to
-// TIE_RUN_MAX pairs are insertion-sorted by id, one thread per run; when the
-// region has a longer run it is sorted again from scratch, by id and then by
-// key, with stable passes (bounded work for any input: at most 8 passes).
+// padding rule of radix_region applies).  The radix passes cover only the
+// high bits of the span (key - kmin): its top 16 bits (18 in CTAs of 512
+// threads or more, two 9-bit passes), which leaves a segment's pairs in runs
+// of equal high parts that are short (2^16 and more buckets for at most
+// 16K pairs); one thread per run then insertion-sorts the run by
+// (key, id), which also breaks key ties by id.  If a run is longer than
+// TIE_RUN_MAX the region is sorted again over all key bits and the runs,
+// now of equal keys, are fixed up the same way; if one of those is still
+// longer, the region is sorted from scratch by id and then by key with
+// stable passes.  The cost stays linear in the region size for any keys
+// (at most 2 + 4 + 8 passes), and the order is exactly (key, id).
 template <int NT, int IPT>
 __device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int bits,
-                                            RowRankSmem<NT>& rank, uint32_t (*red)[NT / 32], int* long_run) {
+                                            RowRankSmem<NT>& rank, uint32_t (*red)[NT / 32], int* long_run,
+                                            uint32_t* resorts) {
   const int tid = threadIdx.x;
-  // stage 0: key passes; with a long tie run, stage 1: id passes, stage 2:
-  // key passes again (one copy of the pass loop serves all three)
+  constexpr int HIGH = NT >= 512 ? 18 : 16;
+  // stage 0: key passes over the high bits; stage 1: key passes over every
+  // bit; stage 2: id passes; stage 3: key passes (one inlined copy of the
+  // pass loop and of the run fix-up serves every stage)
+  int lo = bits > HIGH ? bits - HIGH : 0;
+  int stage = 0;
   uint32_t xmin = kmin;
-  for (int stage = 0;; ++stage) {
-    radix_region<NT, IPT>(keys, vals, n, xmin, bits, stage == 1, rank);
-    if (stage == 2) break;
-    if (stage == 1) {
-      uint32_t kmn = 0xffffffffu, kmx = 0;
-      for (int j = tid; j < n; j += NT) {
-        kmn = min(kmn, keys[j]);
-        kmx = max(kmx, keys[j]);
-      }
-      block_min_max<NT>(kmn, kmx, red);
-      xmin = kmn;
-      bits = radix_bits(kmn, kmx);
+  int xbits = bits;
+  for (;;) {
+    radix_region<NT, IPT>(keys, vals, n, xmin, lo, xbits, stage == 2, rank);
+    if (stage == 3) break;
+    if (stage == 2) {
+      stage = 3;
+      xmin = kmin;
+      xbits = bits;
       continue;
     }
+    // runs of equal (key - kmin) >> lo: insertion by (key, id)
     if (tid == 0) *long_run = 0;
     __syncthreads();
+    const int sh = lo;
     for (int j = tid; j < n; j += NT) {
-      const uint32_t kk = keys[j];
-      if ((j == 0 || keys[j - 1] != kk) && j + 1 < n && keys[j + 1] == kk) {
+      const uint32_t hk = (keys[j] - kmin) >> sh;
+      if ((j == 0 || ((keys[j - 1] - kmin) >> sh) != hk) && j + 1 < n && ((keys[j + 1] - kmin) >> sh) == hk) {
         int e = j + 1;
-        while (e < n && e - j <= TIE_RUN_MAX && keys[e] == kk) ++e;
+        while (e < n && e - j <= TIE_RUN_MAX && ((keys[e] - kmin) >> sh) == hk) ++e;
         if (e - j > TIE_RUN_MAX) {
           *long_run = 1;
           continue;
         }
         for (int i = j + 1; i < e; ++i) {
-          const uint32_t v = vals[i];
+          const uint32_t k = keys[i], v = vals[i];
           int q = i - 1;
-          while (q >= j && vals[q] > v) {
+          while (q >= j && pair_less(k, v, keys[q], vals[q])) {
+            keys[q + 1] = keys[q];
             vals[q + 1] = vals[q];
             --q;
           }
+          keys[q + 1] = k;
           vals[q + 1] = v;
         }
       }
     }
     __syncthreads();
     if (!*long_run) break;
+    if (tid == 0 && resorts) atomicAdd(resorts, 1u);
+    if (lo > 0) {
+      // a long run of equal high parts: every key bit, then the equal-key runs
+      lo = 0;
+      stage = 1;
+      continue;
+    }
+    // a long run of equal keys: by id, then by key
     uint32_t vmn = 0xffffffffu, vmx = 0;
     for (int j = tid; j < n; j += NT) {
       vmn = min(vmn, vals[j]);
@@ -144,7 +173,8 @@ __device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int 
     }
     block_min_max<NT>(vmn, vmx, red);
     xmin = vmn;
-    bits = radix_bits(vmn, vmx);
+    xbits = radix_bits(vmn, vmx);
+    stage = 2;
   }
 }
 
@@ -219,7 +249,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a
       s.vals[j] = v;
     }
     block_min_max<NT>(kmin, kmax, s.red);
-    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_bits(kmin, kmax), s.rank, s.red, &s_long_run);
+    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_bits(kmin, kmax), s.rank, s.red, &s_long_run,
+                         &a.fc->sort_resorts);
     for (int j = tid; j < n; j += NT) {
       a.keys[start + j] = s.keys[j];
       a.vals[start + j] = s.vals[j];
@@ -241,10 +272,6 @@ struct MergeSortSmem {
   RowRankSmem<NT> rank;
   uint32_t red[2][NT / 32];
 };
-
-__device__ __forceinline__ bool pair_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
-  return ka < kb || (ka == kb && va < vb);
-}
 
 template <int NT, int IPT>
 __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_merge_sort(SortArgs a, int tier) {
@@ -291,7 +318,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_merge_sort(Sort
     const int bits = radix_bits(kmin, kmax);
     // one inlined copy of the region sort serves both halves
     for (int h = 0; h < 2; ++h)
-      sort_region<NT, IPT>(s.keys + h * H, s.vals + h * H, h ? hB : hA, kmin, bits, s.rank, s.red, &s_long_run);
+      sort_region<NT, IPT>(s.keys + h * H, s.vals + h * H, h ? hB : hA, kmin, bits, s.rank, s.red, &s_long_run,
+                           &a.fc->sort_resorts);
     const uint32_t *ka = s.keys, *va = s.vals, *kb = s.keys + H, *vb = s.vals + H;
     const int per = (n + NT - 1) / NT;
     const int d0 = min(n, tid * per), d1 = min(n, d0 + per);

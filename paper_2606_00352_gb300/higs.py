@@ -102,13 +102,13 @@ class FrameStats(C.Structure):
                 ("n_pairs", C.c_int64), ("n_segments", C.c_int64), ("n_batches", C.c_int64),
                 ("max_segment", C.c_int64), ("seg_by_tier", C.c_int64 * 6), ("n_sort_tiles", C.c_int64),
                 ("n_replays", C.c_int64), ("raster_evals", C.c_int64), ("status", C.c_int32),
-                ("pad", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
+                ("sort_resorts", C.c_int32), ("ms_project", C.c_float), ("ms_partition", C.c_float),
                 ("ms_sort", C.c_float), ("ms_raster", C.c_float), ("ms_merge", C.c_float),
                 ("ms_total", C.c_float), ("raster_cycles", C.c_int64 * 6), ("pixel_support_evals", C.c_int64),
                 ("pixel_contrib_evals", C.c_int64), ("pixel_live_evals", C.c_int64)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "seg_by_tier", "raster_cycles")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("seg_by_tier", "raster_cycles")}
         d["seg_by_tier"] = list(self.seg_by_tier)
         d["raster_cycles"] = list(self.raster_cycles)
         return d

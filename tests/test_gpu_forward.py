@@ -232,8 +232,9 @@ def test_discrete_stages_all_tiers(lib, ctx):
 @pytest.mark.parametrize("octaves,bits", [(2, 24), (3, 25), (5, 26), (9, 27), (17, 28)])
 def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
     """Depth keys spanning 24 to 28 bits in every shared-memory tier (the
-    tiers of 512 and 1,024 threads sort spans of 25 to 27 bits with 9-bit
-    digits, other spans and the <=1K tier with 8-bit ones), with ties."""
+    tiers of 512 and 1,024 threads sort the top 18 bits of the span with
+    9-bit digits, the smaller tiers the top 16 with 8-bit ones, and fix up
+    the runs of equal high bits), with ties."""
     cam = scenes.look_at((3, 0, 0), width=512, height=96)
     g = np.random.default_rng(100 + octaves)
     parts = []
@@ -252,6 +253,35 @@ def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
     assert all(st["seg_by_tier"][t] > 0 for t in range(4))
     span = int(pr["depth_key"].max()) - int(pr["depth_key"].min())
     assert span.bit_length() == bits
+
+
+def test_discrete_stages_dense_key_runs(lib, ctx):
+    """Keys spanning 25 bits with nearly all of them packed into a few
+    thousand consecutive float values (about four pairs per value): the
+    shared-memory tiers' passes over the high key bits leave runs of more
+    than 32 pairs with equal high bits, so every tier sorts such a segment
+    again over every key bit and breaks the ties by id (sort_resorts > 0);
+    the order is still exactly the oracle's."""
+    cam = scenes.look_at((3, 0, 0), width=512, height=96)
+    g = np.random.default_rng(77)
+    base = int(np.float32(2.5).view(np.uint32))
+    parts = []
+    for n, w in ((400, 64), (3000, 128), (6000, 256), (12000, 384)):
+        p = _synthetic_records(n, 64, 32, n, seed=int(g.integers(1 << 30)), depth_range=(1.0, 8.0))
+        k = (base + g.integers(0, max(8, n // 4), n)).astype(np.uint32)
+        k[:2] = np.float32(1.0).view(np.uint32), np.float32(8.0 * (1 - 2 ** -20)).view(np.uint32)
+        p["depth_key"] = k
+        p["radius"][:2] = 3
+        p["mean2d"][:2] = 32.0, 16.0  # both span ends in the segment of every macro cell the part covers
+        p["mean2d"][:, 0] += w - 64
+        parts.append(p)
+    pr = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if k != "n"}
+    pr["n"] = len(pr["radius"])
+    st = _gate(lib, ctx, [pr], [cam])
+    assert all(st["seg_by_tier"][t] > 0 for t in range(4))
+    assert st["sort_resorts"] > 0
+    span = int(pr["depth_key"].max()) - int(pr["depth_key"].min())
+    assert span.bit_length() == 25
 
 
 def _plain_gate(lib, ctx, projs, cams):
