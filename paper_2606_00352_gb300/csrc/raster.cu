@@ -21,7 +21,9 @@
 //           the tile's 64 pixels (two per lane) front to back over the set
 //           bits of the tile's mini-batch masks (warp-uniform words, so the
 //           gaussians are taken straight from the masks), with a unanimous
-//           vote per mini-batch as the early out when every pixel has stopped
+//           vote per mini-batch and tile half: a half (4 pixel rows) whose
+//           pixels have all stopped takes no more gaussians, and the tile
+//           ends when both have
 //   store   chained: the new per-tile state, or, for the last batch of the
 //           macro-tile, the final pixels straight into the image (the
 //           macro-tile's other tiles from their state or the background; the
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
 
     // phase 1: per-gaussian tile masks, transposed to per-tile masks
     const int K = (int)((count + 31) / 32);
-    build_tile_masks<MW, MH>(s_rec, s_top, s_bot, count, V, mtx0, mty0, RW, s_cnt);
+    build_tile_masks<MW, MH, true>(s_rec, s_top, s_bot, count, V, mtx0, mty0, RW, s_cnt);
     if (HALF) {
       // each thread rewrites the records of the gaussians it built masks for
       // (no other thread reads them before the barrier below) as half2 pairs
@@ -227,8 +229,12 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
         pixel_load(p0, in0, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane]));
         pixel_load(p1, in1, __ldcg(&a.tile_state[(size_t)gt * TILE_PX + lane + 32]));
       }
+      // halves (4 pixel rows) with a live pixel; a half whose pixels have
+      // all stopped takes no more gaussians (its blends would be no-ops)
+      uint32_t on_t = __any_sync(0xffffffffu, pixel_live(p0)) ? ~0u : 0u;
+      uint32_t on_b = __any_sync(0xffffffffu, pixel_live(p1)) ? ~0u : 0u;
       // every pixel already stopped in an earlier batch: nothing to blend
-      if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) {
+      if (!(on_t | on_b)) {
         if (write_out) {
           write_pixels(a, V, px, py, in0, in1, p0, p1);
           if (lane == 0) atomicOr(&s_written, 1ull << t);
@@ -253,17 +259,20 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
       const __half2 hpy = __floats2half2_rn((float)(py - hoy), (float)(py + 4 - hoy));
       uint32_t n_blend = 0;
       // gaussians of this tile in depth order: the set bits of its per
-      // mini-batch masks (warp-uniform), blended directly; the unanimous
-      // early-out vote runs once per mini-batch
+      // mini-batch masks (warp-uniform, bit-reversed: the highest set bit is
+      // the nearest gaussian), blended directly; the per-half votes run
+      // once per mini-batch
       for (int k = 0; k < K; ++k) {
-        const uint32_t mt = s_top[k * M + t], mb = s_bot[k * M + t];
+        const uint32_t mt = s_top[k * M + t] & on_t, mb = s_bot[k * M + t] & on_b;
         uint32_t m = mt | mb;
         if (!m) continue;
         n_blend += __popc(mt) + __popc(mb);  // half-tiles evaluated (32 pixels each)
+        const uint32_t jk = (uint32_t)k * 32 + 31;
         do {
-          const uint32_t bit = m & (0u - m);
+          const int hb = 31 - __clz(m);
+          const uint32_t bit = 1u << hb;
           m ^= bit;
-          const uint32_t j = (uint32_t)k * 32 + (__ffs(bit) - 1);
+          const uint32_t j = jk - (uint32_t)hb;
           if (HALF) {
             const float2 al = half_alpha2(s_rec + (size_t)j * 3, hpx, hpy);
             const float4 g2 = s_rec[j * 3 + 2];
@@ -297,7 +306,9 @@ __global__ void __launch_bounds__(RT) k_raster(RasterArgs a, int cap) {
             }
           }
         } while (m);
-        if (!__any_sync(0xffffffffu, pixel_live(p0) || pixel_live(p1))) break;
+        on_t = __any_sync(0xffffffffu, pixel_live(p0)) ? ~0u : 0u;
+        on_b = __any_sync(0xffffffffu, pixel_live(p1)) ? ~0u : 0u;
+        if (!(on_t | on_b)) break;
       }
       if (lane == 0) evals += (unsigned long long)n_blend * 32ull;
       if (SAVE) {

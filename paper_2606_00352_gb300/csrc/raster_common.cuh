@@ -36,8 +36,10 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 // the row's 8 pixel rows; a half keeps those columns when its 4 pixel rows
 // meet the ellipse's y extent.  With s_cnt, lane t also adds the number of
 // (gaussian, half) entries of tile t to s_cnt[t] (the tile's work, for the
-// queue order).
-template <int MW, int MH>
+// queue order).  With REV the mask words are stored bit-reversed (gaussian
+// j of a mini-batch in bit 31 - j), so a front-to-back walk takes the
+// highest set bit first (one leading-bit search per gaussian).
+template <int MW, int MH, bool REV = false>
 __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* s_top, uint32_t* s_bot,
                                                  uint32_t count, const ViewDesc& V, int mtx0, int mty0,
                                                  int n_warps, uint32_t* s_cnt = nullptr) {
@@ -83,21 +85,21 @@ __device__ __forceinline__ void build_tile_masks(const float4* s_rec, uint32_t* 
       // lane t < 16 receives tile t's top masks, lane 16 + t its bottom ones
       const uint32_t tb = transpose32((uint32_t)gt | ((uint32_t)gb << 16), lane);
       if ((lane & 15) < M) {
-        (lane < 16 ? s_top : s_bot)[k * M + (lane & 15)] = tb;
+        (lane < 16 ? s_top : s_bot)[k * M + (lane & 15)] = REV ? __brev(tb) : tb;
         if (s_cnt) atomicAdd(&s_cnt[lane & 15], (uint32_t)__popc(tb));
       }
       continue;
     }
     const uint32_t tlo = transpose32((uint32_t)gt, lane), blo = transpose32((uint32_t)gb, lane);
     if (lane < M) {
-      s_top[k * M + lane] = tlo;
-      s_bot[k * M + lane] = blo;
+      s_top[k * M + lane] = REV ? __brev(tlo) : tlo;
+      s_bot[k * M + lane] = REV ? __brev(blo) : blo;
       if (s_cnt) atomicAdd(&s_cnt[lane], (uint32_t)(__popc(tlo) + __popc(blo)));
     }
     if (M > 32) {
       const uint32_t thi = transpose32((uint32_t)(gt >> 32), lane), bhi = transpose32((uint32_t)(gb >> 32), lane);
-      s_top[k * M + 32 + lane] = thi;
-      s_bot[k * M + 32 + lane] = bhi;
+      s_top[k * M + 32 + lane] = REV ? __brev(thi) : thi;
+      s_bot[k * M + 32 + lane] = REV ? __brev(bhi) : bhi;
       if (s_cnt) atomicAdd(&s_cnt[32 + lane], (uint32_t)(__popc(thi) + __popc(bhi)));
     }
   }
