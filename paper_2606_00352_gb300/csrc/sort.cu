@@ -208,6 +208,43 @@ __device__ __forceinline__ int radix_bits(uint32_t kmin, uint32_t kmax) {
   return span ? 32 - __clz(span) : 0;
 }
 
+// Loads the n <= NT * IPT pairs at kg / vg into a shared-memory region of
+// ceil(n / NT) * NT slots (padding: key and value 0xffffffff) and folds
+// the keys into kmin / kmax.  Every global load of a thread is issued
+// before the first store in groups of G rows, so a segment's load costs a
+// memory latency per group instead of one per item row (G is held to what
+// the tier's 64 registers allow without spills).
+template <int NT, int IPT, int G>
+__device__ __forceinline__ void load_region(const uint32_t* __restrict__ kg, const uint32_t* __restrict__ vg, int n,
+                                            uint32_t* ks, uint32_t* vs, uint32_t& kmin, uint32_t& kmax) {
+  const int used = ((n + NT - 1) / NT) * NT;
+  for (int i0 = 0; i0 < IPT; i0 += G) {
+    if ((int)threadIdx.x + i0 * NT >= used) break;
+    uint32_t k[G], v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int j = threadIdx.x + (i0 + i) * NT;
+      k[i] = v[i] = 0xffffffffu;
+      if (j < n) {
+        k[i] = __ldcg(kg + j);
+        v[i] = __ldcg(vg + j);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int j = threadIdx.x + (i0 + i) * NT;
+      if (j < used) {
+        ks[j] = k[i];
+        vs[j] = v[i];
+      }
+      if (j < n) {
+        kmin = min(kmin, k[i]);
+        kmax = max(kmax, k[i]);
+      }
+    }
+  }
+}
+
 // Next entry of a tier's segment list for this CTA (dynamic claiming: the
 // segments differ in size, so CTAs take the next one when they are done).
 __device__ __forceinline__ uint32_t claim_segment(FrameCounters* fc, int tier, uint32_t* s_claim) {
@@ -235,19 +272,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a
     const uint32_t seg = list[idx];
     const uint32_t start = a.seg_off[seg];
     const int n = (int)(a.seg_off[seg + 1] - start);
-    const int used = ((n + NT - 1) / NT) * NT;
     uint32_t kmin = 0xffffffffu, kmax = 0;
-    for (int j = tid; j < used; j += NT) {
-      uint32_t k = 0xffffffffu, v = 0xffffffffu;
-      if (j < n) {
-        k = a.keys[start + j];
-        v = a.vals[start + j];
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
-      }
-      s.keys[j] = k;
-      s.vals[j] = v;
-    }
+    load_region<NT, IPT, 4>(a.keys + start, a.vals + start, n, s.keys, s.vals, kmin, kmax);
     block_min_max<NT>(kmin, kmax, s.red);
     sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_bits(kmin, kmax), s.rank, s.red, &s_long_run,
                          &a.fc->sort_resorts);
@@ -290,30 +316,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_merge_sort(Sort
     const uint32_t start = a.seg_off[seg];
     const int n = (int)(a.seg_off[seg + 1] - start);
     const int hA = (n + 1) / 2, hB = n - hA;
-    const int usedA = ((hA + NT - 1) / NT) * NT, usedB = ((hB + NT - 1) / NT) * NT;
     uint32_t kmin = 0xffffffffu, kmax = 0;
-    for (int j = tid; j < usedA; j += NT) {
-      uint32_t k = 0xffffffffu, v = 0xffffffffu;
-      if (j < hA) {
-        k = a.keys[start + j];
-        v = a.vals[start + j];
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
-      }
-      s.keys[j] = k;
-      s.vals[j] = v;
-    }
-    for (int j = tid; j < usedB; j += NT) {
-      uint32_t k = 0xffffffffu, v = 0xffffffffu;
-      if (j < hB) {
-        k = a.keys[start + hA + j];
-        v = a.vals[start + hA + j];
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
-      }
-      s.keys[H + j] = k;
-      s.vals[H + j] = v;
-    }
+    load_region<NT, IPT, 2>(a.keys + start, a.vals + start, hA, s.keys, s.vals, kmin, kmax);
+    load_region<NT, IPT, 2>(a.keys + start + hA, a.vals + start + hA, hB, s.keys + H, s.vals + H, kmin, kmax);
     block_min_max<NT>(kmin, kmax, s.red);
     const int bits = radix_bits(kmin, kmax);
     // one inlined copy of the region sort serves both halves
