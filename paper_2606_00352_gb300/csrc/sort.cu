@@ -285,6 +285,167 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a
   }
 }
 
+// ------------------------------------------------------------ bucket tiers
+// Segments of up to NT * IPT pairs in one CTA, all in shared memory: the
+// pairs are held in registers (slot i of thread t: element t + i * NT),
+// counted into 2^BBITS buckets by the top BBITS bits of (key - min key)
+// (16-bit counters, two per word, shared-memory atomics), the bucket
+// counts scanned into offsets, and the pairs scattered to their buckets
+// (atomic cursors: any order inside a bucket).  With at least two buckets
+// per pair, a bucket holds a few pairs, and one thread per run of equal
+// buckets puts the run in (key, id) order by insertion, so the order is
+// exactly (key, id) whatever the scatter's order.  A region with a run of
+// more than TIE_RUN_MAX pairs (keys packed into few buckets, or many equal
+// keys) is sorted again by a bitonic network over (key, id) instead:
+// O(n log^2 n) with no register arrays, linear in the number of stages.
+template <int NT, int IPT, int BBITS>
+struct BucketSortSmem {
+  uint32_t keys[NT * IPT];
+  uint32_t vals[NT * IPT];
+  uint32_t cnt[(1 << BBITS) / 2];  // bucket b: bits 16 (b & 1) .. of word b / 2
+  uint32_t red[2][NT / 32];
+  uint32_t scan[33];
+};
+
+// Bitonic sort of the n pairs of a shared-memory region by (key, id), the
+// region padded to the next power of two (at most `cap`) with the largest
+// pair.
+template <int NT>
+__device__ __forceinline__ void bitonic_region(uint32_t* keys, uint32_t* vals, int n, int cap) {
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  if (n2 > cap) n2 = cap;
+  for (int j = n + (int)threadIdx.x; j < n2; j += NT) keys[j] = vals[j] = 0xffffffffu;
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < n2 / 2; i += NT) {
+        const int lo = ((i & ~(jj - 1)) << 1) | (i & (jj - 1)), hi = lo + jj;
+        const uint32_t ka = keys[lo], va = vals[lo], kb = keys[hi], vb = vals[hi];
+        const bool up = (lo & k) == 0;
+        if (pair_less(kb, vb, ka, va) == up) {
+          keys[lo] = kb;
+          vals[lo] = vb;
+          keys[hi] = ka;
+          vals[hi] = va;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int NT, int IPT, int BBITS>
+__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs a, int tier) {
+  constexpr int B = 1 << BBITS, W = B / 2, CW = W / NT;  // words of counters per thread
+  static_assert(W % NT == 0, "counter words must divide evenly over the threads");
+  static_assert(NT * IPT <= 65535, "16-bit bucket counters");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BucketSortSmem<NT, IPT, BBITS>& s = *reinterpret_cast<BucketSortSmem<NT, IPT, BBITS>*>(smem_raw);
+  __shared__ uint32_t s_claim;
+  __shared__ int s_long_run;
+  if (read_status(a.fc)) return;
+  const uint32_t count = a.fc->tier_count[tier];
+  const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
+  const int tid = threadIdx.x;
+  for (uint32_t idx = claim_segment(a.fc, tier, &s_claim); idx < count;
+       idx = claim_segment(a.fc, tier, &s_claim)) {
+    const uint32_t seg = list[idx];
+    const uint32_t start = a.seg_off[seg];
+    const int n = (int)(a.seg_off[seg + 1] - start);
+    uint32_t k[IPT], v[IPT];
+    uint32_t kmin = 0xffffffffu, kmax = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int j = tid + i * NT;
+      k[i] = v[i] = 0xffffffffu;
+      if (j < n) {
+        k[i] = __ldcg(a.keys + start + j);
+        v[i] = __ldcg(a.vals + start + j);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+      if (tid + i * NT < n) {
+        kmin = min(kmin, k[i]);
+        kmax = max(kmax, k[i]);
+      }
+#pragma unroll
+    for (int q = 0; q < CW; ++q) s.cnt[tid * CW + q] = 0;
+    block_min_max<NT>(kmin, kmax, s.red);  // its barriers also order the clearing
+    const int bits = radix_bits(kmin, kmax);
+    const int lo = bits > BBITS ? bits - BBITS : 0;
+    // bucket counts
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+      if (tid + i * NT < n) {
+        const uint32_t d = (k[i] - kmin) >> lo;
+        atomicAdd(&s.cnt[d >> 1], (d & 1u) ? 0x10000u : 1u);
+      }
+    __syncthreads();
+    // bucket offsets: thread t scans the words [t * CW, (t + 1) * CW)
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+      const uint32_t w = s.cnt[tid * CW + q];
+      sum += (w & 0xffffu) + (w >> 16);
+    }
+    uint32_t run = block_excl_scan(sum, s.scan, (uint32_t*)nullptr);
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+      const uint32_t w = s.cnt[tid * CW + q], c0 = w & 0xffffu;
+      s.cnt[tid * CW + q] = run | ((run + c0) << 16);
+      run += c0 + (w >> 16);
+    }
+    __syncthreads();
+    // scatter to the buckets
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+      if (tid + i * NT < n) {
+        const uint32_t d = (k[i] - kmin) >> lo;
+        const uint32_t old = atomicAdd(&s.cnt[d >> 1], (d & 1u) ? 0x10000u : 1u);
+        const uint32_t pos = (d & 1u) ? old >> 16 : old & 0xffffu;
+        s.keys[pos] = k[i];
+        s.vals[pos] = v[i];
+      }
+    if (tid == 0) s_long_run = 0;
+    __syncthreads();
+    // runs of equal buckets in (key, id) order
+    for (int j = tid; j < n; j += NT) {
+      const uint32_t hk = (s.keys[j] - kmin) >> lo;
+      if ((j == 0 || ((s.keys[j - 1] - kmin) >> lo) != hk) && j + 1 < n && ((s.keys[j + 1] - kmin) >> lo) == hk) {
+        int e = j + 1;
+        while (e < n && e - j <= TIE_RUN_MAX && ((s.keys[e] - kmin) >> lo) == hk) ++e;
+        if (e - j > TIE_RUN_MAX) {
+          s_long_run = 1;
+          continue;
+        }
+        for (int i = j + 1; i < e; ++i) {
+          const uint32_t kk = s.keys[i], vv = s.vals[i];
+          int q = i - 1;
+          while (q >= j && pair_less(kk, vv, s.keys[q], s.vals[q])) {
+            s.keys[q + 1] = s.keys[q];
+            s.vals[q + 1] = s.vals[q];
+            --q;
+          }
+          s.keys[q + 1] = kk;
+          s.vals[q + 1] = vv;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_long_run) {
+      if (tid == 0) atomicAdd(&a.fc->sort_resorts, 1u);
+      bitonic_region<NT>(s.keys, s.vals, n, NT * IPT);
+    }
+    for (int j = tid; j < n; j += NT) {
+      a.keys[start + j] = s.keys[j];
+      a.vals[start + j] = s.vals[j];
+    }
+    __syncthreads();
+  }
+}
+
 // Segments of 1K..16K pairs: the two halves are sorted in their own
 // shared-memory regions of NT * IPT slots (sort_region), then merged by the
 // merge path straight into the output: thread t finds, by binary search on
@@ -542,12 +703,13 @@ static int num_sms() {
   return g_sms;
 }
 
-template <int NT, int IPT>
-static cudaError_t launch_tier(const SortArgs& a, int tier, int blocks_per_sm, cudaStream_t st) {
-  size_t sm = sizeof(BlockSortSmem<NT, IPT>);
-  cudaError_t e = cudaFuncSetAttribute(k_block_sort<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <int NT, int IPT, int BBITS>
+static cudaError_t launch_bucket_tier(const SortArgs& a, int tier, int blocks_per_sm, cudaStream_t st) {
+  size_t sm = sizeof(BucketSortSmem<NT, IPT, BBITS>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_bucket_sort<NT, IPT, BBITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_block_sort<NT, IPT><<<num_sms() * blocks_per_sm, NT, sm, st>>>(a, tier);
+  k_bucket_sort<NT, IPT, BBITS><<<num_sms() * blocks_per_sm, NT, sm, st>>>(a, tier);
   note_launch();
   return cudaGetLastError();
 }
@@ -658,9 +820,9 @@ static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaS
   // the largest tiers first, each on its own stream when s1..s3 differ from
   // st: their tails overlap
   if ((e = launch_merge_tier<1024, 8>(a, 3, 1, s3)) != cudaSuccess) return e;
-  if ((e = launch_merge_tier<512, 8>(a, 2, 2, s2)) != cudaSuccess) return e;
-  if ((e = launch_merge_tier<256, 8>(a, 1, 4, s1)) != cudaSuccess) return e;
-  if ((e = launch_tier<128, 8>(a, 0, 8, st)) != cudaSuccess) return e;
+  if ((e = launch_bucket_tier<512, 16, 14>(a, 2, 2, s2)) != cudaSuccess) return e;
+  if ((e = launch_bucket_tier<256, 16, 13>(a, 1, 4, s1)) != cudaSuccess) return e;
+  if ((e = launch_bucket_tier<128, 8, 11>(a, 0, 8, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   // the partition zeroed the big segments' histograms
   return launch_onesweep_by_val_key(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist, 0, false, a.lookback,
