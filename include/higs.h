@@ -203,8 +203,8 @@ typedef struct {
   int64_t n_replays;      /* merge replays (exact termination across batches) */
   int64_t raster_evals;   /* (gaussian, pixel) evaluations in the rasteriser */
   int32_t status;         /* device status word (hg_status) */
-  int32_t sort_resorts;   /* shared-memory sort regions sorted again over every key bit
-                           * (a run of more than 32 pairs with equal high key bits) */
+  int32_t sort_resorts;   /* shared-memory sort segments sorted again by the bitonic
+                           * network (a run of more than 32 pairs in one bucket) */
   float ms_project, ms_partition, ms_sort, ms_raster, ms_merge, ms_total;
   /* with HG_FLAG_PROFILE: SM clock cycles summed over processing units of
    * [0] record gather, [1] tile masks + queue, [2] chain wait, and over warps

@@ -57,7 +57,7 @@ struct FrameCounters {
   uint32_t os_claim[8];
   uint32_t tier_claim[6];  // next list entry of each SMEM sort tier (dynamic claiming)
   uint32_t timeout_where;
-  uint32_t sort_resorts;   // shared-memory sort regions sorted again (a long run after the high-bit passes)
+  uint32_t sort_resorts;   // shared-memory sort segments sorted again (a long run in one bucket)
   unsigned long long replays;
   unsigned long long raster_evals;
   // HG_FLAG_PROFILE: the intrinsic per-pixel work of the frame (support

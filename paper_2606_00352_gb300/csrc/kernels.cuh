@@ -61,10 +61,10 @@ struct PartitionArgs {
 };
 
 // Sort tiers: segment-size limits handled by one CTA in shared memory.
-constexpr int TIER0_MAX = 1024;    // 128 threads x 8
-constexpr int TIER1_MAX = 4096;    // two halves of 256 threads x 8, then a merge
-constexpr int TIER2_MAX = 8192;    // two halves of 512 threads x 8, then a merge
-constexpr int TIER3_MAX = 16384;   // two halves of 1024 threads x 8, then a merge
+constexpr int TIER0_MAX = 1024;    // 128 threads x 8 pairs, 2^12 buckets
+constexpr int TIER1_MAX = 4096;    // 256 threads x 16, 2^13 buckets
+constexpr int TIER2_MAX = 8192;    // 512 threads x 16, 2^14 buckets
+constexpr int TIER3_MAX = 16384;   // 1024 threads x 16, 2^15 buckets
 // tiers: <= 1K, <= 4K, <= 8K, <= 16K (shared memory), onesweep, empty / one pair
 constexpr int N_TIERS = 6;
 constexpr int TIER_OS = 4, TIER_NONE = 5;

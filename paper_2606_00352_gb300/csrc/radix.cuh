@@ -1,5 +1,5 @@
-// Stable block-wide radix ranking (8-bit digits) used by the segmented sort
-// tiers and by the onesweep passes.
+// Stable block-wide radix ranking (8-bit digits) used by the onesweep passes
+// of the segmented sort.
 //
 // Items are held warp-striped: item slot i of lane l in warp w is element
 // w * 32 * IPT + i * 32 + l of the block's range, so ranking slot by slot and
@@ -89,96 +89,6 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[IPT], uint32_t 
   for (int i = 0; i < IPT; ++i) {
     const uint32_t d = dig[i];
     pos[i] = d < 256 ? s.digit_start[d] + s.hist[warp][d] + rk[i] : 0xffffffffu;
-  }
-}
-
-// Shared memory of block_rank_rows: per-warp counters for digits of up to
-// 9 bits ([warp][digit], row stride 1 << bits).
-// digit_start / digit_count are indexed by pad(d) = d + d / 32, so that warp
-// 0's scan, lane l reading digits [l * per, (l + 1) * per) in step, touches
-// 32 distinct banks for per = 8 and 16.
-template <int NT>
-struct RowRankSmem {
-  uint32_t hist[(NT / 32) * 512];
-  uint32_t digit_start[512 + 16];
-  uint32_t digit_count[512 + 16];
-};
-__device__ __forceinline__ int rank_pad(int d) { return d + (d >> 5); }
-
-// Lanes holding the same digit as this lane: eight ballots, a ninth for
-// 9-bit digits (wide, warp-uniform).
-__device__ __forceinline__ uint32_t digit_peers89(uint32_t d, bool wide) {
-  uint32_t peers = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < 9; ++b) {
-    if (b == 8 && !wide) break;
-    const bool bit = (d >> b) & 1u;
-    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
-
-// Stable block-wide ranking of 8-bit (wide false) or 9-bit (wide true)
-// digits over the first `rows` item slots of every thread (rows <= IPT, the
-// same in every warp; every digit below 1 << bits).  Warp w holds elements
-// [w * 32 * rows, (w + 1) * 32 * rows), slot i of lane l being element
-// w * 32 * rows + i * 32 + l.  On return pos[i] is the item's position in
-// the block sorted stably by digit.
-template <int NT, int IPT>
-__device__ __forceinline__ void block_rank_rows(const uint32_t (&dig)[IPT], uint32_t (&pos)[IPT], RowRankSmem<NT>& s,
-                                                int rows, bool wide) {
-  constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int bins = wide ? 512 : 256;
-  uint32_t* hw = s.hist + warp * bins;
-  for (int j = lane; j < bins; j += 32) hw[j] = 0;
-  __syncwarp();
-  const uint32_t lt = lanemask_lt();
-  uint32_t rk[IPT];
-#pragma unroll
-  for (int i = 0; i < IPT; ++i) {
-    if (i >= rows) break;
-    const uint32_t d = dig[i];
-    const uint32_t peers = digit_peers89(d, wide);
-    const uint32_t leader = __ffs(peers) - 1;
-    const uint32_t base = hw[d];
-    __syncwarp();
-    if (lane == (int)leader) hw[d] = base + __popc(peers);
-    __syncwarp();
-    rk[i] = base + __popc(peers & lt);
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < bins; d += NT) {
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      const uint32_t c = s.hist[w * bins + d];
-      s.hist[w * bins + d] = run;
-      run += c;
-    }
-    s.digit_count[rank_pad(d)] = run;
-  }
-  __syncthreads();
-  // exclusive scan of the digit totals by warp 0 (8 or 16 per lane)
-  if (warp == 0) {
-    const int per = bins / 32;
-    uint32_t sum = 0;
-    for (int k = 0; k < per; ++k) sum += s.digit_count[rank_pad(lane * per + k)];
-    uint32_t run = warp_incl_scan(sum) - sum;
-    for (int k = 0; k < per; ++k) {
-      const int q = rank_pad(lane * per + k);
-      const uint32_t c = s.digit_count[q];
-      s.digit_start[q] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < IPT; ++i) {
-    if (i >= rows) break;
-    const uint32_t d = dig[i];
-    pos[i] = s.digit_start[rank_pad((int)d)] + hw[d] + rk[i];
   }
 }
 

@@ -1,25 +1,21 @@
 // Segmented depth sort (Sec. 3.3, 4.4).  Every (view, macro-tile) segment of
 // (32-bit depth key, gaussian id) pairs is sorted ascending by (key, id):
-//   * segments of <= 1K pairs: one CTA of 128 threads sorts the segment in
-//     shared memory, over the top 16 bits of (key - min key) (two 8-bit
-//     passes), then puts the short runs of equal high bits in (key, id)
-//     order by insertion;
-//   * segments of 1K..4K, 4K..8K and 8K..16K pairs: one CTA (256, 512 or
-//     1,024 threads) sorts the two halves in shared memory the same way and
-//     merges them (merge path) into the output; the smaller CTAs fit more
-//     segments per SM than one CTA over the whole segment would;
+//   * segments of <= 1K, <= 4K, <= 8K and <= 16K pairs: one CTA of 128, 256,
+//     512 or 1,024 threads sorts the segment in shared memory with one
+//     counting scatter into 2^12, 2^13, 2^14 or 2^15 buckets (at least two
+//     per pair) by the top bits of (key - min key), then puts each run of
+//     pairs that share a bucket in (key, id) order by insertion, one thread
+//     per run; this also breaks key ties by id (the fill pass writes a
+//     segment in a data-dependent order).  A segment with a run of more
+//     than 32 pairs is sorted again by a bitonic network over (key, id), so
+//     the cost stays bounded whatever the keys.  The smaller CTAs fit more
+//     segments per SM;
 //   * larger segments (> 16K): a segment-local onesweep (one kernel per 8-bit
 //     digit pass, decoupled look-back across the segment's tiles, tiles
 //     claimed in order through an atomic counter so every awaited
 //     predecessor is running), preceded by one histogram kernel for all
 //     digits.  Its passes are stable, so it sorts by the id's four digits
 //     first and then by the key's: (key, id) order with no fix-up.
-// The tiers of 512 and 1,024 threads sort the top 18 bits (two 9-bit
-// passes).  The run fix-up also breaks key ties by id (the fill pass writes
-// a segment in a data-dependent order).  A region with a run of more than
-// 32 equal high parts is sorted again over every key bit, and one with more
-// than 32 equal keys by id and then by key (stable passes), so the cost
-// stays linear in the segment size whatever the keys.
 #include <mutex>
 #include <string>
 #include <utility>
@@ -33,149 +29,12 @@ namespace hg {
 namespace {
 
 // ------------------------------------------------------------ tier sorts
-template <int NT, int IPT>
-struct BlockSortSmem {
-  uint32_t keys[NT * IPT];
-  uint32_t vals[NT * IPT];
-  RowRankSmem<NT> rank;
-  uint32_t red[2][NT / 32];
-};
-
-// LSD radix passes over bits [lo, bits) of (x - xmin), x = keys[e]
-// (by_val false) or vals[e] (by_val true), of the n pairs of a shared-memory
-// region, moving both arrays: the region's pairs are spread evenly over the
-// warps (rows = ceil(n / NT) item slots per thread; slots [n, rows * NT) must
-// hold key and value 0xffffffff and get the largest digit, so padding always
-// ranks after the real pairs).  In CTAs of 512 threads or more a span that
-// 9-bit digits cover in fewer passes than 8-bit ones (9, 17-18, 25-27 bits)
-// takes 9-bit passes; otherwise ceil(span / 8) 8-bit passes (the 9-bit
-// passes' 512 counters per warp cost more than the pass they save in the
-// small tiers).  Every pass is stable.
-template <int NT, int IPT>
-__device__ __forceinline__ void radix_region(uint32_t* keys, uint32_t* vals, int n, uint32_t xmin, int lo, int bits,
-                                             bool by_val, RowRankSmem<NT>& rank) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rows = (n + NT - 1) / NT;  // <= IPT
-  const int span = bits - lo;
-  const bool wide = NT >= 512 && span > 8 && (span + 8) / 9 < (span + 7) / 8;
-  const int dbits = wide ? 9 : 8, passes = wide ? (span + 8) / 9 : (span + 7) / 8;
-  const uint32_t dmask = wide ? 0x1ffu : 0xffu;
-  for (int pass = 0; pass < passes; ++pass) {
-    const int shift = lo + dbits * pass;
-    uint32_t k[IPT], v[IPT], d[IPT], p[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      if (i >= rows) break;
-      const int e = warp * 32 * rows + i * 32 + lane;
-      k[i] = keys[e];
-      v[i] = vals[e];
-      d[i] = e < n ? (((by_val ? v[i] : k[i]) - xmin) >> shift) & dmask : dmask;
-    }
-    // every thread has read its items before the ranking's first barrier,
-    // so the scatter needs no barrier of its own before it
-    block_rank_rows<NT, IPT>(d, p, rank, rows, wide);
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      if (i >= rows) break;
-      keys[p[i]] = k[i];
-      vals[p[i]] = v[i];
-    }
-    __syncthreads();
-  }
-}
-
-template <int NT>
-__device__ __forceinline__ void block_min_max(uint32_t& mn, uint32_t& mx, uint32_t (*red)[NT / 32]);
-__device__ __forceinline__ int radix_bits(uint32_t kmin, uint32_t kmax);
-
 // Longest run of pairs one thread puts in order by insertion after the
-// radix passes.
+// bucket scatter.
 constexpr int TIE_RUN_MAX = 32;
 
 __device__ __forceinline__ bool pair_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
   return ka < kb || (ka == kb && va < vb);
-}
-
-// Sorts the n pairs of a shared-memory region ascending by (key, id) (the
-// padding rule of radix_region applies).  The radix passes cover only the
-// high bits of the span (key - kmin): its top 16 bits (18 in CTAs of 512
-// threads or more, two 9-bit passes), which leaves a segment's pairs in runs
-// of equal high parts that are short (2^16 and more buckets for at most
-// 16K pairs); one thread per run then insertion-sorts the run by
-// (key, id), which also breaks key ties by id.  If a run is longer than
-// TIE_RUN_MAX the region is sorted again over all key bits and the runs,
-// now of equal keys, are fixed up the same way; if one of those is still
-// longer, the region is sorted from scratch by id and then by key with
-// stable passes.  The cost stays linear in the region size for any keys
-// (at most 2 + 4 + 8 passes), and the order is exactly (key, id).
-template <int NT, int IPT>
-__device__ __forceinline__ void sort_region(uint32_t* keys, uint32_t* vals, int n, uint32_t kmin, int bits,
-                                            RowRankSmem<NT>& rank, uint32_t (*red)[NT / 32], int* long_run,
-                                            uint32_t* resorts) {
-  const int tid = threadIdx.x;
-  constexpr int HIGH = NT >= 512 ? 18 : 16;
-  // stage 0: key passes over the high bits; stage 1: key passes over every
-  // bit; stage 2: id passes; stage 3: key passes (one inlined copy of the
-  // pass loop and of the run fix-up serves every stage)
-  int lo = bits > HIGH ? bits - HIGH : 0;
-  int stage = 0;
-  uint32_t xmin = kmin;
-  int xbits = bits;
-  for (;;) {
-    radix_region<NT, IPT>(keys, vals, n, xmin, lo, xbits, stage == 2, rank);
-    if (stage == 3) break;
-    if (stage == 2) {
-      stage = 3;
-      xmin = kmin;
-      xbits = bits;
-      continue;
-    }
-    // runs of equal (key - kmin) >> lo: insertion by (key, id)
-    if (tid == 0) *long_run = 0;
-    __syncthreads();
-    const int sh = lo;
-    for (int j = tid; j < n; j += NT) {
-      const uint32_t hk = (keys[j] - kmin) >> sh;
-      if ((j == 0 || ((keys[j - 1] - kmin) >> sh) != hk) && j + 1 < n && ((keys[j + 1] - kmin) >> sh) == hk) {
-        int e = j + 1;
-        while (e < n && e - j <= TIE_RUN_MAX && ((keys[e] - kmin) >> sh) == hk) ++e;
-        if (e - j > TIE_RUN_MAX) {
-          *long_run = 1;
-          continue;
-        }
-        for (int i = j + 1; i < e; ++i) {
-          const uint32_t k = keys[i], v = vals[i];
-          int q = i - 1;
-          while (q >= j && pair_less(k, v, keys[q], vals[q])) {
-            keys[q + 1] = keys[q];
-            vals[q + 1] = vals[q];
-            --q;
-          }
-          keys[q + 1] = k;
-          vals[q + 1] = v;
-        }
-      }
-    }
-    __syncthreads();
-    if (!*long_run) break;
-    if (tid == 0 && resorts) atomicAdd(resorts, 1u);
-    if (lo > 0) {
-      // a long run of equal high parts: every key bit, then the equal-key runs
-      lo = 0;
-      stage = 1;
-      continue;
-    }
-    // a long run of equal keys: by id, then by key
-    uint32_t vmn = 0xffffffffu, vmx = 0;
-    for (int j = tid; j < n; j += NT) {
-      vmn = min(vmn, vals[j]);
-      vmx = max(vmx, vals[j]);
-    }
-    block_min_max<NT>(vmn, vmx, red);
-    xmin = vmn;
-    xbits = radix_bits(vmn, vmx);
-    stage = 2;
-  }
 }
 
 // Block-wide min and max of one value per thread (red: [2][NT / 32]).
@@ -208,81 +67,12 @@ __device__ __forceinline__ int radix_bits(uint32_t kmin, uint32_t kmax) {
   return span ? 32 - __clz(span) : 0;
 }
 
-// Loads the n <= NT * IPT pairs at kg / vg into a shared-memory region of
-// ceil(n / NT) * NT slots (padding: key and value 0xffffffff) and folds
-// the keys into kmin / kmax.  Every global load of a thread is issued
-// before the first store in groups of G rows, so a segment's load costs a
-// memory latency per group instead of one per item row (G is held to what
-// the tier's 64 registers allow without spills).
-template <int NT, int IPT, int G>
-__device__ __forceinline__ void load_region(const uint32_t* __restrict__ kg, const uint32_t* __restrict__ vg, int n,
-                                            uint32_t* ks, uint32_t* vs, uint32_t& kmin, uint32_t& kmax) {
-  const int used = ((n + NT - 1) / NT) * NT;
-  for (int i0 = 0; i0 < IPT; i0 += G) {
-    if ((int)threadIdx.x + i0 * NT >= used) break;
-    uint32_t k[G], v[G];
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-      const int j = threadIdx.x + (i0 + i) * NT;
-      k[i] = v[i] = 0xffffffffu;
-      if (j < n) {
-        k[i] = __ldcg(kg + j);
-        v[i] = __ldcg(vg + j);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-      const int j = threadIdx.x + (i0 + i) * NT;
-      if (j < used) {
-        ks[j] = k[i];
-        vs[j] = v[i];
-      }
-      if (j < n) {
-        kmin = min(kmin, k[i]);
-        kmax = max(kmax, k[i]);
-      }
-    }
-  }
-}
-
 // Next entry of a tier's segment list for this CTA (dynamic claiming: the
 // segments differ in size, so CTAs take the next one when they are done).
 __device__ __forceinline__ uint32_t claim_segment(FrameCounters* fc, int tier, uint32_t* s_claim) {
   if (threadIdx.x == 0) *s_claim = atomicAdd(&fc->tier_claim[tier], 1u);
   __syncthreads();
   return *s_claim;
-}
-
-// One CTA per segment (claimed from the tier's list): the segment is loaded
-// into shared memory, sorted there (sort_region) and written back.
-template <int NT, int IPT>
-__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_sort(SortArgs a, int tier) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  BlockSortSmem<NT, IPT>& s = *reinterpret_cast<BlockSortSmem<NT, IPT>*>(smem_raw);
-  __shared__ uint32_t s_claim;
-  __shared__ int s_long_run;
-  if (read_status(a.fc)) return;
-  const uint32_t count = a.fc->tier_count[tier];
-  const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
-  const int tid = threadIdx.x;
-  // every thread reads the claim before the body's first barrier, and the
-  // next claim is written only after the barrier that ends the body
-  for (uint32_t idx = claim_segment(a.fc, tier, &s_claim); idx < count;
-       idx = claim_segment(a.fc, tier, &s_claim)) {
-    const uint32_t seg = list[idx];
-    const uint32_t start = a.seg_off[seg];
-    const int n = (int)(a.seg_off[seg + 1] - start);
-    uint32_t kmin = 0xffffffffu, kmax = 0;
-    load_region<NT, IPT, 4>(a.keys + start, a.vals + start, n, s.keys, s.vals, kmin, kmax);
-    block_min_max<NT>(kmin, kmax, s.red);
-    sort_region<NT, IPT>(s.keys, s.vals, n, kmin, radix_bits(kmin, kmax), s.rank, s.red, &s_long_run,
-                         &a.fc->sort_resorts);
-    for (int j = tid; j < n; j += NT) {
-      a.keys[start + j] = s.keys[j];
-      a.vals[start + j] = s.vals[j];
-    }
-    __syncthreads();
-  }
 }
 
 // ------------------------------------------------------------ bucket tiers
@@ -441,71 +231,6 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs 
     for (int j = tid; j < n; j += NT) {
       a.keys[start + j] = s.keys[j];
       a.vals[start + j] = s.vals[j];
-    }
-    __syncthreads();
-  }
-}
-
-// Segments of 1K..16K pairs: the two halves are sorted in their own
-// shared-memory regions of NT * IPT slots (sort_region), then merged by the
-// merge path straight into the output: thread t finds, by binary search on
-// its output diagonal, how many of its first outputs come from each half
-// and merges its run of ceil(n / NT) outputs.  Pairs of a segment are
-// distinct gaussians, so (key, id) is a strict order.
-template <int NT, int IPT>
-struct MergeSortSmem {
-  uint32_t keys[2 * NT * IPT];
-  uint32_t vals[2 * NT * IPT];
-  RowRankSmem<NT> rank;
-  uint32_t red[2][NT / 32];
-};
-
-template <int NT, int IPT>
-__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_block_merge_sort(SortArgs a, int tier) {
-  constexpr int H = NT * IPT;  // one half's region
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MergeSortSmem<NT, IPT>& s = *reinterpret_cast<MergeSortSmem<NT, IPT>*>(smem_raw);
-  __shared__ uint32_t s_claim;
-  __shared__ int s_long_run;
-  if (read_status(a.fc)) return;
-  const uint32_t count = a.fc->tier_count[tier];
-  const uint32_t* list = a.tier_list + (size_t)tier * a.n_seg;
-  const int tid = threadIdx.x;
-  for (uint32_t idx = claim_segment(a.fc, tier, &s_claim); idx < count;
-       idx = claim_segment(a.fc, tier, &s_claim)) {
-    const uint32_t seg = list[idx];
-    const uint32_t start = a.seg_off[seg];
-    const int n = (int)(a.seg_off[seg + 1] - start);
-    const int hA = (n + 1) / 2, hB = n - hA;
-    uint32_t kmin = 0xffffffffu, kmax = 0;
-    load_region<NT, IPT, 2>(a.keys + start, a.vals + start, hA, s.keys, s.vals, kmin, kmax);
-    load_region<NT, IPT, 2>(a.keys + start + hA, a.vals + start + hA, hB, s.keys + H, s.vals + H, kmin, kmax);
-    block_min_max<NT>(kmin, kmax, s.red);
-    const int bits = radix_bits(kmin, kmax);
-    // one inlined copy of the region sort serves both halves
-    for (int h = 0; h < 2; ++h)
-      sort_region<NT, IPT>(s.keys + h * H, s.vals + h * H, h ? hB : hA, kmin, bits, s.rank, s.red, &s_long_run,
-                           &a.fc->sort_resorts);
-    const uint32_t *ka = s.keys, *va = s.vals, *kb = s.keys + H, *vb = s.vals + H;
-    const int per = (n + NT - 1) / NT;
-    const int d0 = min(n, tid * per), d1 = min(n, d0 + per);
-    // i = number of A pairs among the first d0 outputs
-    int lo = max(0, d0 - hB), hi = min(d0, hA);
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (pair_less(kb[d0 - mid - 1], vb[d0 - mid - 1], ka[mid], va[mid]))
-        hi = mid;
-      else
-        lo = mid + 1;
-    }
-    int ia = lo, ib = d0 - lo;
-    for (int d = d0; d < d1; ++d) {
-      const bool takeA = ib >= hB || (ia < hA && pair_less(ka[ia], va[ia], kb[ib], vb[ib]));
-      const uint32_t k = takeA ? ka[ia] : kb[ib], v = takeA ? va[ia] : vb[ib];
-      ia += takeA;
-      ib += !takeA;
-      a.keys[start + d] = k;
-      a.vals[start + d] = v;
     }
     __syncthreads();
   }
@@ -803,26 +528,15 @@ static cudaError_t launch_onesweep_by_val_key(const OsTileView& tv, uint32_t* ke
   return cudaSuccess;
 }
 
-template <int NT, int IPT>
-static cudaError_t launch_merge_tier(const SortArgs& a, int tier, int blocks_per_sm, cudaStream_t st) {
-  size_t sm = sizeof(MergeSortSmem<NT, IPT>);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_block_merge_sort<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_block_merge_sort<NT, IPT><<<num_sms() * blocks_per_sm, NT, sm, st>>>(a, tier);
-  note_launch();
-  return cudaGetLastError();
-}
-
 static cudaError_t launch_sort_kernels(const SortArgs& a, cudaStream_t st, cudaStream_t s1, cudaStream_t s2,
                                        cudaStream_t s3) {
   cudaError_t e;
   // the largest tiers first, each on its own stream when s1..s3 differ from
   // st: their tails overlap
-  if ((e = launch_merge_tier<1024, 8>(a, 3, 1, s3)) != cudaSuccess) return e;
+  if ((e = launch_bucket_tier<1024, 16, 15>(a, 3, 1, s3)) != cudaSuccess) return e;
   if ((e = launch_bucket_tier<512, 16, 14>(a, 2, 2, s2)) != cudaSuccess) return e;
   if ((e = launch_bucket_tier<256, 16, 13>(a, 1, 4, s1)) != cudaSuccess) return e;
-  if ((e = launch_bucket_tier<128, 8, 11>(a, 0, 8, st)) != cudaSuccess) return e;
+  if ((e = launch_bucket_tier<128, 8, 12>(a, 0, 8, st)) != cudaSuccess) return e;
   OsTileView tv{a.big_tiles, &a.fc->n_big_tiles, a.seg_hist, a.seg_off, a.big_segs, a.big_tile_first};
   // the partition zeroed the big segments' histograms
   return launch_onesweep_by_val_key(tv, a.keys, a.vals, a.keys_alt, a.vals_alt, a.seg_hist, 0, false, a.lookback,

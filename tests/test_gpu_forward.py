@@ -225,16 +225,15 @@ def test_discrete_stages_all_tiers(lib, ctx):
     pr = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if k != "n"}
     pr["n"] = len(pr["radius"])
     st = _gate(lib, ctx, [pr], [cam])
-    # <= 1K, <= 4K, <= 8K, <= 16K (halves + merge) and onesweep
+    # <= 1K, <= 4K, <= 8K, <= 16K (bucket sorts in shared memory) and onesweep
     assert all(st["seg_by_tier"][t] > 0 for t in range(5))
 
 
 @pytest.mark.parametrize("octaves,bits", [(2, 24), (3, 25), (5, 26), (9, 27), (17, 28)])
 def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
-    """Depth keys spanning 24 to 28 bits in every shared-memory tier (the
-    tiers of 512 and 1,024 threads sort the top 18 bits of the span with
-    9-bit digits, the smaller tiers the top 16 with 8-bit ones, and fix up
-    the runs of equal high bits), with ties."""
+    """Depth keys spanning 24 to 28 bits in every shared-memory tier (each
+    tier scatters a segment into buckets by the top 12 to 15 bits of the
+    span and fixes up the runs of pairs that share a bucket), with ties."""
     cam = scenes.look_at((3, 0, 0), width=512, height=96)
     g = np.random.default_rng(100 + octaves)
     parts = []
@@ -258,10 +257,10 @@ def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
 def test_discrete_stages_dense_key_runs(lib, ctx):
     """Keys spanning 25 bits with nearly all of them packed into a few
     thousand consecutive float values (about four pairs per value): the
-    shared-memory tiers' passes over the high key bits leave runs of more
-    than 32 pairs with equal high bits, so every tier sorts such a segment
-    again over every key bit and breaks the ties by id (sort_resorts > 0);
-    the order is still exactly the oracle's."""
+    shared-memory tiers' buckets over the top bits of the span leave runs of
+    more than 32 pairs in one bucket, so every tier sorts such a segment
+    again with the bitonic network over (key, id) (sort_resorts > 0); the
+    order is still exactly the oracle's."""
     cam = scenes.look_at((3, 0, 0), width=512, height=96)
     g = np.random.default_rng(77)
     base = int(np.float32(2.5).view(np.uint32))
