@@ -254,6 +254,31 @@ def test_discrete_stages_key_spans(lib, ctx, octaves, bits):
     assert span.bit_length() == bits
 
 
+def test_discrete_stages_tier_boundary_sizes(lib, ctx):
+    """Segments of exactly 2, 1,024 / 1,025, 4,096 / 4,097, 8,192 / 8,193
+    and 16,384 / 16,385 pairs (each tier's largest segment and the smallest
+    of the next, the last one in the onesweep), one 64x32 macro cell each,
+    depth keys spanning 25 bits with ties: bit-exact pairs and order."""
+    sizes = (2, 1024, 1025, 4096, 4097, 8192, 8193, 16384, 16385)
+    cam = scenes.look_at((3, 0, 0), width=64 * len(sizes), height=32)
+    g = np.random.default_rng(31)
+    parts = []
+    for c, n in enumerate(sizes):
+        p = _synthetic_records(n, 64, 32, max(2, n // 3), seed=int(g.integers(1 << 30)), rad_max=1,
+                               depth_range=(1.0, 8.0))
+        # centres at least 2 px inside the cell: the 3-sigma rectangle (radius 1) stays in it
+        p["mean2d"] = np.stack([g.uniform(2.5, 61.5, n) + 64 * c, g.uniform(2.5, 29.5, n)], 1)
+        p["radius"][:] = 1
+        k = p["depth_key"]
+        k[:2] = np.float32(1.0).view(np.uint32), np.float32(8.0 * (1 - 2 ** -20)).view(np.uint32)
+        parts.append(p)
+    pr = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if k != "n"}
+    pr["n"] = len(pr["radius"])
+    st = _gate(lib, ctx, [pr], [cam])
+    assert st["max_segment"] == 16385
+    assert st["seg_by_tier"][:5] == [2, 2, 2, 2, 1]
+
+
 def test_discrete_stages_dense_key_runs(lib, ctx):
     """Keys spanning 25 bits with nearly all of them packed into a few
     thousand consecutive float values (about four pairs per value): the
