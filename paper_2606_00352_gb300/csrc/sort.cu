@@ -200,27 +200,60 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs 
       }
     if (tid == 0) s_long_run = 0;
     __syncthreads();
-    // runs of equal buckets in (key, id) order
-    for (int j = tid; j < n; j += NT) {
-      const uint32_t hk = (s.keys[j] - kmin) >> lo;
-      if ((j == 0 || ((s.keys[j - 1] - kmin) >> lo) != hk) && j + 1 < n && ((s.keys[j + 1] - kmin) >> lo) == hk) {
-        int e = j + 1;
-        while (e < n && e - j <= TIE_RUN_MAX && ((s.keys[e] - kmin) >> lo) == hk) ++e;
-        if (e - j > TIE_RUN_MAX) {
-          s_long_run = 1;
-          continue;
+    // runs of pairs that share a bucket, in (key, id) order.  The counters
+    // now hold each bucket's end, so a pair's run is [end of the bucket
+    // before, end of its bucket).  Warp w takes the pairs from the first
+    // run start at or after w * n / NW to the first at or after
+    // (w + 1) * n / NW, 32 positions at a time, cut back to the last run
+    // that ends inside them: every lane ranks its pair against the pairs of
+    // its own run (shuffles, as many steps as the chunk's longest run) and
+    // writes it to its place in the chunk, which no other warp touches.
+    {
+      const int lane = tid & 31, warp = tid >> 5;
+      constexpr int NW = NT / 32;
+      auto bucket_end = [&](uint32_t b) -> int {
+        const uint32_t w = s.cnt[b >> 1];
+        return (int)((b & 1u) ? w >> 16 : w & 0xffffu);
+      };
+      auto run_start_from = [&](int pos) -> int {  // first run start at or after pos
+        if (pos <= 0 || pos >= n) return pos <= 0 ? 0 : n;
+        const uint32_t b = (s.keys[pos] - kmin) >> lo;
+        const int rs = b ? bucket_end(b - 1) : 0;
+        return rs == pos ? pos : bucket_end(b);
+      };
+      const int c_end = run_start_from((int)(((long long)(warp + 1) * n) / NW));
+      for (int c = run_start_from((int)(((long long)warp * n) / NW)); c < c_end;) {
+        const int p = c + lane;
+        uint32_t k = 0, v = 0;
+        int rs = 0, re = 0x7fffffff;
+        if (p < c_end) {
+          k = s.keys[p];
+          v = s.vals[p];
+          const uint32_t b = (k - kmin) >> lo;
+          rs = b ? bucket_end(b - 1) : 0;
+          re = bucket_end(b);
         }
-        for (int i = j + 1; i < e; ++i) {
-          const uint32_t kk = s.keys[i], vv = s.vals[i];
-          int q = i - 1;
-          while (q >= j && pair_less(kk, vv, s.keys[q], s.vals[q])) {
-            s.keys[q + 1] = s.keys[q];
-            s.vals[q + 1] = s.vals[q];
-            --q;
-          }
-          s.keys[q + 1] = kk;
-          s.vals[q + 1] = vv;
+        const bool fits = re <= c + 32;  // runs ending inside the chunk (a prefix of the lanes)
+        const int len = __popc(__ballot_sync(0xffffffffu, fits));
+        if (len == 0) {  // a run of more than 32 pairs starts at c
+          if (lane == 0) s_long_run = 1;
+          break;
         }
+        const int rl = fits ? re - rs : 0, off = rs - c;
+        const int steps = __reduce_max_sync(0xffffffffu, (unsigned)rl);
+        int rank = 0;
+        for (int d = 0; d < steps; ++d) {
+          const int src = (off + d) & 31;
+          const uint32_t kd = __shfl_sync(0xffffffffu, k, src), vd = __shfl_sync(0xffffffffu, v, src);
+          if (d < rl) rank += pair_less(kd, vd, k, v);
+        }
+        __syncwarp();
+        if (fits && rl > 1) {
+          s.keys[rs + rank] = k;
+          s.vals[rs + rank] = v;
+        }
+        __syncwarp();
+        c += len;
       }
     }
     __syncthreads();
