@@ -4,9 +4,9 @@
 //     512 or 1,024 threads sorts the segment in shared memory with one
 //     counting scatter into 2^12, 2^13, 2^14 or 2^15 buckets (at least two
 //     per pair) by the top bits of (key - min key), then puts each run of
-//     pairs that share a bucket in (key, id) order by insertion, one thread
-//     per run; this also breaks key ties by id (the fill pass writes a
-//     segment in a data-dependent order).  A segment with a run of more
+//     pairs that share a bucket in (key, id) order, the warps ranking the
+//     pairs of whole runs by shuffles; this also breaks key ties by id (the
+//     fill pass writes a segment in a data-dependent order).  A segment with a run of more
 //     than 32 pairs is sorted again by a bitonic network over (key, id), so
 //     the cost stays bounded whatever the keys.  The smaller CTAs fit more
 //     segments per SM;
@@ -29,10 +29,6 @@ namespace hg {
 namespace {
 
 // ------------------------------------------------------------ tier sorts
-// Longest run of pairs one thread puts in order by insertion after the
-// bucket scatter.
-constexpr int TIE_RUN_MAX = 32;
-
 __device__ __forceinline__ bool pair_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
   return ka < kb || (ka == kb && va < vb);
 }
@@ -82,11 +78,11 @@ __device__ __forceinline__ uint32_t claim_segment(FrameCounters* fc, int tier, u
 // (16-bit counters, two per word, shared-memory atomics), the bucket
 // counts scanned into offsets, and the pairs scattered to their buckets
 // (atomic cursors: any order inside a bucket).  With at least two buckets
-// per pair, a bucket holds a few pairs, and one thread per run of equal
-// buckets puts the run in (key, id) order by insertion, so the order is
-// exactly (key, id) whatever the scatter's order.  A region with a run of
-// more than TIE_RUN_MAX pairs (keys packed into few buckets, or many equal
-// keys) is sorted again by a bitonic network over (key, id) instead:
+// per pair, a bucket holds a few pairs, and the warps put every run of
+// pairs that share a bucket in (key, id) order, so the order is exactly
+// (key, id) whatever the scatter's order.  A segment with a run of more
+// than 32 pairs (keys packed into few buckets, or many equal keys) is
+// sorted again by a bitonic network over (key, id) instead:
 // O(n log^2 n) with no register arrays, linear in the number of stages.
 template <int NT, int IPT, int BBITS>
 struct BucketSortSmem {
