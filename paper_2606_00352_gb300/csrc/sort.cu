@@ -84,11 +84,16 @@ __device__ __forceinline__ uint32_t claim_segment(FrameCounters* fc, int tier, u
 // than 32 pairs (keys packed into few buckets, or many equal keys) is
 // sorted again by a bitonic network over (key, id) instead:
 // O(n log^2 n) with no register arrays, linear in the number of stages.
+// Shared-memory index of counter word w: one pad word after every 16, so
+// the 16 words a thread scans start 17 words after its neighbour's (no two
+// lanes on one bank).
+__device__ __forceinline__ uint32_t cnt_word(uint32_t w) { return w + (w >> 4); }
+
 template <int NT, int IPT, int BBITS>
 struct BucketSortSmem {
   uint32_t keys[NT * IPT];
   uint32_t vals[NT * IPT];
-  uint32_t cnt[(1 << BBITS) / 2];  // bucket b: bits 16 (b & 1) .. of word b / 2
+  uint32_t cnt[(1 << BBITS) / 2 + (1 << BBITS) / 32];  // bucket b: bits 16 (b & 1) .. of word cnt_word(b / 2)
   uint32_t red[2][NT / 32];
   uint32_t scan[33];
 };
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs 
         kmax = max(kmax, k[i]);
       }
 #pragma unroll
-    for (int q = 0; q < CW; ++q) s.cnt[tid * CW + q] = 0;
+    for (int q = 0; q < CW + CW / 16; ++q) s.cnt[tid + q * NT] = 0;
     block_min_max<NT>(kmin, kmax, s.red);  // its barriers also order the clearing
     const int bits = radix_bits(kmin, kmax);
     const int lo = bits > BBITS ? bits - BBITS : 0;
@@ -166,21 +171,21 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs 
     for (int i = 0; i < IPT; ++i)
       if (tid + i * NT < n) {
         const uint32_t d = (k[i] - kmin) >> lo;
-        atomicAdd(&s.cnt[d >> 1], (d & 1u) ? 0x10000u : 1u);
+        atomicAdd(&s.cnt[cnt_word(d >> 1)], (d & 1u) ? 0x10000u : 1u);
       }
     __syncthreads();
     // bucket offsets: thread t scans the words [t * CW, (t + 1) * CW)
     uint32_t sum = 0;
 #pragma unroll
     for (int q = 0; q < CW; ++q) {
-      const uint32_t w = s.cnt[tid * CW + q];
+      const uint32_t w = s.cnt[cnt_word(tid * CW + q)];
       sum += (w & 0xffffu) + (w >> 16);
     }
     uint32_t run = block_excl_scan(sum, s.scan, (uint32_t*)nullptr);
 #pragma unroll
     for (int q = 0; q < CW; ++q) {
-      const uint32_t w = s.cnt[tid * CW + q], c0 = w & 0xffffu;
-      s.cnt[tid * CW + q] = run | ((run + c0) << 16);
+      const uint32_t w = s.cnt[cnt_word(tid * CW + q)], c0 = w & 0xffffu;
+      s.cnt[cnt_word(tid * CW + q)] = run | ((run + c0) << 16);
       run += c0 + (w >> 16);
     }
     __syncthreads();
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs 
     for (int i = 0; i < IPT; ++i)
       if (tid + i * NT < n) {
         const uint32_t d = (k[i] - kmin) >> lo;
-        const uint32_t old = atomicAdd(&s.cnt[d >> 1], (d & 1u) ? 0x10000u : 1u);
+        const uint32_t old = atomicAdd(&s.cnt[cnt_word(d >> 1)], (d & 1u) ? 0x10000u : 1u);
         const uint32_t pos = (d & 1u) ? old >> 16 : old & 0xffffu;
         s.keys[pos] = k[i];
         s.vals[pos] = v[i];
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs 
       const int lane = tid & 31, warp = tid >> 5;
       constexpr int NW = NT / 32;
       auto bucket_end = [&](uint32_t b) -> int {
-        const uint32_t w = s.cnt[b >> 1];
+        const uint32_t w = s.cnt[cnt_word(b >> 1)];
         return (int)((b & 1u) ? w >> 16 : w & 0xffffu);
       };
       auto run_start_from = [&](int pos) -> int {  // first run start at or after pos
