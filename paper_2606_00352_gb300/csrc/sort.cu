@@ -129,7 +129,7 @@ __device__ __forceinline__ void bitonic_region(uint32_t* keys, uint32_t* vals, i
 template <int NT, int IPT, int BBITS>
 __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_bucket_sort(SortArgs a, int tier) {
   constexpr int B = 1 << BBITS, W = B / 2, CW = W / NT;  // words of counters per thread
-  static_assert(W % NT == 0, "counter words must divide evenly over the threads");
+  static_assert(W % NT == 0 && CW % 16 == 0, "counter words (and their pad words) must divide evenly over the threads");
   static_assert(NT * IPT <= 65535, "16-bit bucket counters");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BucketSortSmem<NT, IPT, BBITS>& s = *reinterpret_cast<BucketSortSmem<NT, IPT, BBITS>*>(smem_raw);
