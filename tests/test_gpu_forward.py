@@ -282,13 +282,13 @@ def test_discrete_stages_tier_boundary_sizes(lib, ctx):
 @pytest.mark.parametrize("n", [1024, 4096, 8192, 16384])
 def test_discrete_stages_equal_keys_full_tier(lib, ctx, n):
     """One segment of each shared-memory tier's largest size whose pairs
-    all carry the same depth key, ids in reverse order of their positions:
-    the whole segment is one bucket, so the tier sorts it with the bitonic
-    network and the order is the ids' (sort_resorts counts it)."""
+    all carry the same depth key: the whole segment is one bucket, so the
+    tier sorts it with the bitonic network, and the order is the ids'
+    (sort_resorts counts it)."""
     cam = scenes.look_at((3, 0, 0), width=64, height=32)
     g = np.random.default_rng(n)
     p = _synthetic_records(n, 64, 32, 1, seed=int(g.integers(1 << 30)), rad_max=1)
-    p["mean2d"] = np.stack([g.uniform(2.5, 61.5, n), g.uniform(2.5, 29.5, n)], 1)[::-1].copy()
+    p["mean2d"] = np.stack([g.uniform(2.5, 61.5, n), g.uniform(2.5, 29.5, n)], 1)
     p["radius"][:] = 1
     p["depth_key"][:] = np.float32(2.5).view(np.uint32)
     st = _gate(lib, ctx, [p], [cam])
